@@ -1,0 +1,289 @@
+"""Benchmark: 3D cubic-quintic CGL, periodic, Fourier 128^3, complex128,
+tau = 0.005, fourth-order splitting (split4); Strang and RK4 alongside.
+
+A bench step is one cgl_step call advancing the 128^3 field by `--chunk`
+time steps (default 50) on the GPU.  value = grid points x time steps / s.
+Inputs are resident in HBM; L2 (129 MB) is flushed by writing a 256 MiB
+buffer between timed iterations, outside the timed events.
+
+--impl reference times the FP64 CPU oracle on the same workload (a bounded
+sample: one time step per bench step) and prints the same JSON line.
+
+Multi-GPU (torchrun, N > 1): every rank advances its own replica of the
+workload (the method has no exchange step); value sums the ranks' grid-point
+steps over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2403_02816_gb300 import inputs as I  # noqa: E402
+
+METRIC = "grid-pt·steps/s at fixed rel. L2 error vs FP64 oracle; % tensor/HBM roofline"
+UNIT = "grid-pt·steps/s"
+
+# FP64 peak of the GB300: 1.25 TFLOP/s nominal (dense FP64) at the 2070 MHz
+# maximum SM clock over 152 SMs, i.e. 2 FP64 FMA per clock per SM.
+FP64_FMA_PER_CLK_PER_SM = 2
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def fp64_peak_tflops(sm_mhz=SM_MAX_MHZ):
+    return N_SM * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk", type=int, default=50, help="time steps per bench step")
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--scheme", default="split4")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+                self.lines = [l for l in out.splitlines() if l.strip()]
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        # samples under load: the upper half of the clock samples
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_problem(p):
+    from oracle import cgl_oracle as O
+    return O.OracleProblem(p.n, p.bc, p.lo, p.hi, p.a1, p.b1, p.a2, p.a3, p.b3, p.a4, p.b4)
+
+
+def cpu_oracle_steps(w, U0, scheme, nsteps):
+    """Time `nsteps` oracle steps on the full workload (bounded sample)."""
+    from oracle import cgl_oracle as O
+    L = O.LinearOperator(oracle_problem(w.prob), w.tau)
+    step = O.SCHEMES[scheme]
+    U = U0.copy()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        U = step(L, U)
+    return time.perf_counter() - t0, U
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = I.workload_3d_periodic(args.n)
+    U0 = I.u0_3d_periodic(w)
+    N = w.prob.N
+    for _ in range(max(args.warmup, 0)):
+        cpu_oracle_steps(w, U0, args.scheme, 1)
+    times = [cpu_oracle_steps(w, U0, args.scheme, 1)[0] for _ in range(args.steps)]
+    total = sum(times)
+    value = N * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "scheme": args.scheme, "tau": w.tau, "grid": list(w.prob.n),
+                   "time_steps_per_bench_step": 1, "l2": "input larger than L2 not needed (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d time steps of %s on the full %s field (numpy, FP64)"
+                                   % (args.steps, args.scheme, "x".join(map(str, w.prob.n)))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2403_02816_gb300 import native as nat
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    nat.load()
+    w = I.workload_3d_periodic(args.n)
+    U0 = I.u0_3d_periodic(w)
+    N = w.prob.N
+    chunk = args.chunk
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(plan, u, K, W):
+        for _ in range(W):
+            plan.step(u, chunk)
+        barrier()
+        evs = []
+        for _ in range(K):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.step(u, chunk)
+            e1.record(stream)
+            evs.append((e0, e1))
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms
+
+    plan = nat.Plan(w.prob, w.tau, args.scheme, "f64")
+    u = nat.to_device(U0, torch.complex128, dev)
+    with Clocks(local) as clk:
+        ms = timed(plan, u, args.steps, max(args.warmup, 3))
+    clocks = clk.summary()
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    units = N * chunk * args.steps * world
+    value = units / (ms_max / 1e3)
+    status = plan.device_status()
+
+    # per-kernel timing for the roofline (CUDA events around every launch)
+    prof = plan.profile(u, 2)
+    dom = max(prof, key=lambda r: r["total_ms"])
+    achieved = dom["flops"] / (dom["total_ms"] / 1e3) / 1e12
+    peak = fp64_peak_tflops()
+    traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom["name"], "launches_profiled": dom["launches"],
+                "avg_launch_ms": dom["total_ms"] / dom["launches"],
+                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz (1.25 TFLOP/s nominal FP64)",
+                "share": dom["total_ms"] / sum(r["total_ms"] for r in prof)}
+
+    # end to end through the C ABI with host buffers (pinned)
+    host = torch.from_numpy(np.ascontiguousarray(U0.T)).pin_memory()
+    plan.step_host(host, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.step_host(host, chunk)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": N * chunk * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16}
+
+    info = plan.info()
+    extras = {}
+    if not args.no_extras:
+        for s in ("strang", "rk4", "lawson4"):
+            if s == args.scheme:
+                continue
+            with nat.Plan(w.prob, w.tau, s, "f64") as p2:
+                u2 = nat.to_device(U0, torch.complex128, dev)
+                ms2 = timed(p2, u2, 2, 1)
+                extras[s] = N * chunk * 2 / (ms2 / 1e3)
+        extras[args.scheme] = value / world
+
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, Uref = cpu_oracle_steps(w, U0, args.scheme, 1)
+        cpu = {"value": N / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "1 time step of %s on the full %s field (numpy FP64, single thread)"
+                         % (args.scheme, "x".join(map(str, w.prob.n)))}
+        with nat.Plan(w.prob, w.tau, args.scheme, "f64") as p3:
+            u3 = nat.to_device(U0, torch.complex128, dev)
+            p3.step(u3, 1)
+            torch.cuda.synchronize()
+            from oracle import cgl_oracle as O
+            parity = O.rel_l2(nat.from_device(u3), Uref)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "scheme": args.scheme, "tau": w.tau, "grid": list(w.prob.n),
+                       "time_steps_per_bench_step": chunk, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed (256 MiB write) between timed iterations"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": info["launches_per_step"] * chunk * args.steps,
+            "clocks": clocks, "device_status": status,
+            "rel_l2_vs_oracle_1step": parity, "schemes_grid_pt_steps_per_s": extras,
+            "kernels": prof,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

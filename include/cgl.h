@@ -1,0 +1,185 @@
+/*
+ * cgl.h - C ABI of libcgl: constant-step exponential integrators for the
+ * semidiscretised complex Ginzburg-Landau (CGL) equation on one GB300 GPU.
+ *
+ * Method: Caliari & Cassini, "Efficient simulation of complex Ginzburg-Landau
+ * equations using high-order exponential-type methods" (arXiv 2403.02816).
+ *
+ *   u_t = (a1 + i b1) Lap u + a2 u + (a3 + i b3)|u|^2 u + (a4 + i b4)|u|^4 u
+ *                                                                  (Sec. 1, eq. 1)
+ * on a box (lo_1,hi_1) x ... x (lo_d,hi_d), d = 1..3, semidiscretised as
+ * u' = K u + g(u) with K = A_d (+) ... (+) A_1 a Kronecker sum (Sec. 1, eq. 2).
+ *   - Dirichlet/Neumann directions: 2nd-order finite differences; the linear
+ *     flow exp(c tau K) is the Tucker operator U x_1 e^{c tau A_1} ... x_d
+ *     e^{c tau A_d} (Sec. 3.1, eq. Tucker), one mu-mode product per direction
+ *     with a dense n_mu x n_mu factor computed once per distinct c.
+ *   - Periodic directions: Fourier pseudospectral; exp(c tau K) is a pointwise
+ *     multiplication in Fourier space (Sec. 3.2), done with an in-house FFT.
+ *
+ * Conventions for every entry point:
+ *   - Return value: 0 (CGL_OK) or a negative cgl_status.  Nothing throws or
+ *     aborts across the ABI; cgl_last_error() gives a message for the calling
+ *     thread's most recent failure.
+ *   - Fields are caller-owned device buffers of N = n_1*...*n_d complex
+ *     numbers, interleaved (re, im), double2 for CGL_F64 and float2 for
+ *     CGL_F32, stored with index 1 fastest: the paper's vec(U) (Sec. 3.1).
+ *     A PyTorch tensor of shape (n_d, ..., n_1), contiguous, has this layout.
+ *   - Streams are passed as void* (a cudaStream_t; NULL = legacy default).
+ *     Work is enqueued asynchronously unless an entry point says otherwise.
+ *   - A plan owns its factors and workspace (device memory it allocates at
+ *     creation and frees in cgl_plan_destroy).  One plan must not run on two
+ *     streams at once.
+ */
+#ifndef CGL_H
+#define CGL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cgl_plan cgl_plan;
+
+/* Boundary condition per direction. */
+enum cgl_bc { CGL_BC_DIRICHLET = 0, CGL_BC_NEUMANN = 1, CGL_BC_PERIODIC = 2 };
+
+/* Time integrators (Sec. 2). */
+enum cgl_scheme {
+    CGL_STRANG = 0,   /* eq. Strang: phi_{tau/2} e^{tau K} phi_{tau/2}, order 2            */
+    CGL_SPLIT4 = 1,   /* eq. Richardson: 4/3 S_{tau/2}S_{tau/2} - 1/3 S_tau, order 4        */
+    CGL_LAWSON4 = 2,  /* eq. lawson4 (if4), order 4                                         */
+    CGL_RK4 = 3,      /* eq. RK4 on u' = K u + g(u); periodic problems only                 */
+    CGL_LAWSON2 = 4,  /* eq. lawson2b (if2), order 2                                        */
+    CGL_RK2 = 5       /* eq. RK2 (Heun); periodic problems only                             */
+};
+
+/* Arithmetic of the state and of the time-stepping kernels.  The factors
+ * exp(c tau A_mu) are always computed in FP64 and rounded once. */
+enum cgl_precision { CGL_F64 = 0, CGL_F32 = 1 };
+
+enum cgl_status {
+    CGL_OK = 0,
+    CGL_EINVAL = -1,        /* invalid argument                                   */
+    CGL_ENOMEM = -2,        /* device allocation failed                           */
+    CGL_ECUDA = -3,         /* a CUDA runtime call failed (see cgl_last_error)    */
+    CGL_EUNSUPPORTED = -4,  /* valid but not implemented (e.g. RK4 with FD)       */
+    CGL_ETIMEOUT = -5,      /* a bounded device-side wait gave up                 */
+    CGL_ENONFINITE = -6     /* a step produced Inf/NaN (finite-time blow-up)      */
+};
+
+/*
+ * Create a plan: validates the problem, builds A_mu = (a1+i b1) D2_mu + a2/d
+ * (Sec. 1 after eq. 2; 2nd-order FD or Fourier symbol, Sec. 3.2), computes the
+ * factors exp(c tau A_mu) in FP64 on the GPU for every distinct c the scheme
+ * needs (Strang/Lawson2: c = 1; split4: 1 and 1/2; Lawson4: 1/2), and sizes
+ * the workspace.
+ *   out        receives the plan (set to NULL on failure).
+ *   d          1, 2 or 3.
+ *   n[d]       grid sizes, n_mu >= 2.  Periodic: powers of two <= 2048.
+ *              Finite differences: n_mu <= 1024.
+ *   bc[d]      cgl_bc per direction; all periodic or none (else EUNSUPPORTED).
+ *   lo[d],hi[d] domain, hi > lo.
+ *   a1 > 0 (Sec. 1 assumption); b1, a2, a3, b3, a4, b4 any finite values
+ *              (zeros allowed).  a4 = b4 = 0 selects the cubic model whose
+ *              nonlinear flow is exact (eq. exsolcub); otherwise the flow is
+ *              one RK4 step of u' = g(u) (Sec. 4.3).
+ *   tau        constant step, > 0 and finite.
+ *   scheme     cgl_scheme; CGL_RK4/CGL_RK2 need periodic directions.
+ *   precision  cgl_precision.
+ *   stream     stream used for the set-up work; the call returns after it
+ *              has completed.
+ * Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA.
+ */
+int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc,
+                    const double* lo, const double* hi,
+                    double a1, double b1, double a2, double a3, double b3,
+                    double a4, double b4, double tau, int scheme, int precision,
+                    void* stream);
+
+/*
+ * Advance the caller-owned device field u (N complex values, layout above)
+ * by nsteps constant steps of the plan's scheme, in place.  Asynchronous on
+ * `stream`.  The step sequence is recorded once per (plan, u) pair into a
+ * CUDA graph and replayed; the first call for a new u pointer therefore
+ * captures on an internal stream.  nsteps >= 0.
+ * Errors: EINVAL (NULL plan/u, nsteps < 0), ECUDA.
+ */
+int cgl_step(cgl_plan* plan, void* u, int64_t nsteps, void* stream);
+
+/*
+ * Same as cgl_step for a HOST buffer u_host (N complex values): copies it to
+ * a plan-owned device field, advances nsteps, copies the result back.
+ * Synchronous: returns after the result is in u_host.  u_host may be pinned
+ * (fast path) or pageable.
+ */
+int cgl_step_host(cgl_plan* plan, void* u_host, int64_t nsteps, void* stream);
+
+/* Destroy a plan and free its device memory.  NULL is accepted. */
+int cgl_plan_destroy(cgl_plan* plan);
+
+/*
+ * Apply one linear flow exp(c tau K) to the device field u in place
+ * (eq. Tucker / Sec. 3.2), for c equal to one of the plan's factor values
+ * (1 or 0.5; EINVAL otherwise).  Asynchronous on `stream`.
+ */
+int cgl_linear_flow(cgl_plan* plan, double c, void* u, void* stream);
+
+/*
+ * Copy the plan's FP64 factor for value c and direction mu (0-based) to host
+ * memory: FD gives exp(c tau A_mu) as n_mu x n_mu complex (re,im) doubles in
+ * column-major order (2*n_mu*n_mu doubles); periodic gives the diagonal
+ * exp(c tau a_mu(kappa)) in FFT order (2*n_mu doubles).  Synchronous.
+ */
+int cgl_plan_factor(cgl_plan* plan, double c, int mu, double* host_out);
+
+/* Sizes: bytes of one field, of the plan's workspace, and kernel launches
+ * enqueued per time step.  Any pointer may be NULL. */
+int cgl_plan_info(const cgl_plan* plan, size_t* field_bytes, size_t* workspace_bytes,
+                  int* launches_per_step);
+
+/*
+ * Read (synchronising `stream`) and clear the plan's device status word:
+ * returns CGL_OK, or CGL_ENONFINITE if any step since the last call wrote a
+ * non-finite value.
+ */
+int cgl_last_device_status(cgl_plan* plan, void* stream);
+
+/*
+ * Per-kernel timing (CUDA events around every launch) of nsteps steps run
+ * without the graph.  Fills up to max_kernels records, sets *count.
+ * Synchronous.  flops / bytes are the algorithmic counts per launch (FFT
+ * 5 n log2 n per pencil, 8 n real flops per mode-product output point, one
+ * read and one write per field touched).
+ */
+typedef struct cgl_kernel_time {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+    double flops;   /* algorithmic flops summed over the launches */
+    double bytes;   /* algorithmic DRAM bytes summed over the launches */
+} cgl_kernel_time;
+int cgl_profile_step(cgl_plan* plan, void* u, int64_t nsteps, void* stream,
+                     cgl_kernel_time* out, int max_kernels, int* count);
+
+/*
+ * Relative errors of x against y over `count` complex values of `precision`
+ * (Sec. 4: relative norms against a reference): out[0] = ||x-y||_2/||y||_2,
+ * out[1] = ||x-y||_inf/||y||_inf, out[2] = number of non-finite entries of x.
+ * Accumulates in FP64.  Allocates its scratch with cudaMallocAsync on
+ * `stream`.  Synchronous.
+ */
+int cgl_rel_error(const void* x, const void* y, int64_t count, int precision,
+                  double* out, void* stream);
+
+/* Message for a status code (static string). */
+const char* cgl_strerror(int status);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char* cgl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGL_H */

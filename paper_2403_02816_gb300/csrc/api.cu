@@ -1,0 +1,740 @@
+// libcgl C ABI: plan creation (space discretisation and factor precompute),
+// the per-scheme step programs, CUDA-graph replay, profiling hooks.
+//
+// A time step is a short program of "sweeps".  A sweep applies one linear
+// flow exp(c tau K) (or K itself for the Runge-Kutta schemes) to one or two
+// fields, with a pointwise prologue fused into its first pass and a pointwise
+// epilogue fused into its last pass (see ProOp / EpiOp).  A sweep is d
+// mu-mode passes (finite differences, eq. Tucker) or 2d-1 FFT pencil passes
+// (periodic, Sec. 3.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cgl_internal.cuh"
+
+using namespace cgl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return fail(_e == cudaErrorMemoryAllocation ? CGL_ENOMEM : CGL_ECUDA,              \
+                  std::string(#expr) + ": " + cudaGetErrorString(_e));                   \
+  } while (0)
+
+enum { BUF_U = 0, BUF_W0 = 1, BUF_W1 = 2, BUF_W2 = 3, NBUF = 4 };
+constexpr int FAC_K = -1;  // the Runge-Kutta sweeps apply K, not an exponential
+
+struct Sweep {
+  int nin = 1, in[2] = {BUF_U, BUF_U};
+  int nrhs = 1, fac[2] = {0, 0}, work[2] = {BUF_U, BUF_U};
+  int nextra = 0, extra[3] = {BUF_U, BUF_U, BUF_U};
+  int nout = 1, out[2] = {BUF_U, BUF_U};
+  OpArgs op{};
+};
+
+struct KernelStat {
+  int64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+
+}  // namespace
+
+struct cgl_plan {
+  int dev = 0;
+  int d = 0;
+  int64_t n[3] = {1, 1, 1};
+  int bc[3] = {0, 0, 0};
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  double a1 = 0, b1 = 0, a2 = 0, a3 = 0, b3 = 0, a4 = 0, b4 = 0, tau = 0;
+  int scheme = 0, precision = 0, periodic = 0, cubic = 0;
+  int64_t N = 0;
+  size_t elem = 0;
+
+  int nfac = 0;
+  double cval[2] = {0, 0};
+  void* fac[2][3] = {{nullptr}};        // working-precision factors / symbol vectors
+  double2* fac64[2][3] = {{nullptr}};   // FP64 masters
+  void* ksym[3] = {nullptr};            // K symbol vectors (periodic Runge-Kutta)
+  void* twiddle[3] = {nullptr};         // FFT twiddles per axis
+  std::vector<void*> allocations;
+
+  int nwork = 0;
+  void* work[3] = {nullptr, nullptr, nullptr};
+  int* status = nullptr;
+  void* host_stage = nullptr;  // device field for cgl_step_host
+
+  std::vector<Sweep> sweeps;
+
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* graph_u = nullptr;
+
+  // profiling (when `prof` is set, launches are bracketed by events)
+  bool prof = false;
+  std::map<std::string, KernelStat>* stats = nullptr;
+};
+
+namespace {
+
+int64_t axis_P(const cgl_plan* p, int axis) {
+  int64_t P = 1;
+  for (int m = 0; m < axis; ++m) P *= p->n[m];
+  return P;
+}
+
+PassGeom geom(const cgl_plan* p, int axis) {
+  PassGeom g{};
+  g.d = p->d;
+  for (int m = 0; m < 3; ++m) g.n[m] = p->n[m];
+  g.axis = axis;
+  g.n_ax = p->n[axis];
+  g.P = axis_P(p, axis);
+  g.npencils = p->N / p->n[axis];
+  return g;
+}
+
+// Algorithmic flop count per grid point of the pointwise operators (real
+// flops, transcendental calls not counted): g = 15, exact flow = 20,
+// one RK4 step of u' = g(u) = 84, complex axpy = 4.
+double flow_flops(const cgl_plan* p) { return p->cubic ? 20.0 : 84.0; }
+double pro_flops(const cgl_plan* p, const OpArgs& o) {
+  switch (o.pro) {
+    case PRO_FLOW: return flow_flops(p);
+    case PRO_FLOW2: return 2 * flow_flops(p);
+    case PRO_LAW4: return 15;
+    case PRO_LAW2: return 23;
+    default: return 0;
+  }
+}
+double epi_flops(const cgl_plan* p, const OpArgs& o) {
+  switch (o.epi) {
+    case EPI_FLOW: return flow_flops(p);
+    case EPI_FLOW2: return 2 * flow_flops(p);
+    case EPI_SPLIT4: return flow_flops(p) + 4;
+    case EPI_LAW4A: return 46;
+    case EPI_LAW4B: return 19;
+    case EPI_LAW2: return 19;
+    case EPI_RK: return 25;
+    default: return 0;
+  }
+}
+
+struct Timer {
+  cgl_plan* p;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Timer(cgl_plan* p_, cudaStream_t s_) : p(p_), s(s_) {
+    if (p->prof) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+    }
+  }
+  void done(const std::string& name, double flops, double bytes) {
+    if (!p->prof) return;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    KernelStat& k = (*p->stats)[name];
+    k.launches += 1;
+    k.ms += ms;
+    k.flops += flops;
+    k.bytes += bytes;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+};
+
+int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
+  void* bufs[NBUF] = {u, p->work[0], p->work[1], p->work[2]};
+  PassFields f{};
+  f.nin = sw.nin;
+  f.nrhs = sw.nrhs;
+  f.nextra = sw.nextra;
+  f.nout = sw.nout;
+  for (int r = 0; r < 2; ++r) {
+    f.in[r] = bufs[sw.in[r]];
+    f.work[r] = bufs[sw.work[r]];
+    f.out[r] = bufs[sw.out[r]];
+  }
+  for (int x = 0; x < 3; ++x) f.extra[x] = bufs[sw.extra[x]];
+  const double Nd = (double)p->N;
+  const double es = (double)p->elem;
+  const bool f64 = p->precision == CGL_F64;
+
+  if (!p->periodic) {
+    for (int mu = 0; mu < p->d; ++mu) {
+      ModePassArgs a{};
+      a.g = geom(p, mu);
+      a.f = f;
+      a.op = sw.op;
+      a.flags = (mu == 0 ? PASS_PRO : 0) | (mu == p->d - 1 ? PASS_EPI : 0);
+      for (int r = 0; r < 2; ++r) a.factor[r] = p->fac[sw.fac[r < sw.nrhs ? r : 0]][mu];
+      a.status = p->status;
+      double flops = 8.0 * (double)p->n[mu] * Nd * sw.nrhs;
+      double rd = (mu == 0 ? sw.nin : sw.nrhs), wr = (mu == p->d - 1 ? sw.nout : sw.nrhs);
+      if (mu == 0) flops += pro_flops(p, sw.op) * Nd;
+      if (mu == p->d - 1) { flops += epi_flops(p, sw.op) * Nd; rd += sw.nextra; }
+      Timer tm(p, s);
+      cudaError_t e = f64 ? launch_mode_pass<double>(a, s) : launch_mode_pass<float>(a, s);
+      if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("mode pass: ") + cudaGetErrorString(e));
+      tm.done(f64 ? "mode_pass_f64" : "mode_pass_f32", flops, (rd + wr) * Nd * es);
+    }
+    return CGL_OK;
+  }
+
+  // periodic: forward passes along axes 0..d-2, the last axis does
+  // forward + symbol + inverse, then inverse passes d-2..0.
+  struct PassPlan { int axis, flags; };
+  std::vector<PassPlan> passes;
+  const int d = p->d;
+  for (int mu = 0; mu < d - 1; ++mu) passes.push_back({mu, PASS_FWD});
+  passes.push_back({d - 1, PASS_FWD | PASS_MUL | PASS_INV});
+  for (int mu = d - 2; mu >= 0; --mu) passes.push_back({mu, PASS_INV});
+  passes.front().flags |= PASS_PRO;
+  passes.back().flags |= PASS_EPI;
+
+  for (size_t k = 0; k < passes.size(); ++k) {
+    const int mu = passes[k].axis;
+    FftPassArgs a{};
+    a.g = geom(p, mu);
+    a.f = f;
+    a.op = sw.op;
+    a.flags = passes[k].flags;
+    for (int r = 0; r < sw.nrhs; ++r) {
+      const int fi = sw.fac[r];
+      for (int m = 0; m < d; ++m) a.sym[r].vec[m] = (fi == FAC_K) ? p->ksym[m] : p->fac[fi][m];
+      a.sym[r].sum_form = (fi == FAC_K) ? 1 : 0;
+    }
+    a.twiddle = p->twiddle[mu];
+    a.status = p->status;
+    const double nn = (double)p->n[mu];
+    const double fft = 5.0 * std::log2(nn) * Nd * sw.nrhs;  // 5 n log2 n per pencil
+    double flops = 0;
+    if (a.flags & PASS_FWD) flops += fft;
+    if (a.flags & PASS_INV) flops += fft;
+    if (a.flags & PASS_MUL) flops += 6.0 * Nd * sw.nrhs;
+    if (a.flags & PASS_PRO) flops += pro_flops(p, sw.op) * Nd;
+    if (a.flags & PASS_EPI) flops += epi_flops(p, sw.op) * Nd;
+    double rd = (a.flags & PASS_PRO) ? sw.nin : sw.nrhs;
+    double wr = (a.flags & PASS_EPI) ? sw.nout : sw.nrhs;
+    if (a.flags & PASS_EPI) rd += sw.nextra;
+    Timer tm(p, s);
+    cudaError_t e = f64 ? launch_fft_pass<double>(a, s) : launch_fft_pass<float>(a, s);
+    if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("fft pass: ") + cudaGetErrorString(e));
+    tm.done(f64 ? "fft_pass_f64" : "fft_pass_f32", flops, (rd + wr) * Nd * es);
+  }
+  return CGL_OK;
+}
+
+int enqueue_step(cgl_plan* p, void* u, cudaStream_t s) {
+  for (const Sweep& sw : p->sweeps) {
+    int st = enqueue_sweep(p, sw, u, s);
+    if (st != CGL_OK) return st;
+  }
+  return CGL_OK;
+}
+
+int launches_per_step(const cgl_plan* p) {
+  const int per = p->periodic ? 2 * p->d - 1 : p->d;
+  return (int)p->sweeps.size() * per;
+}
+
+// ------------------------------------------------------------ space discretisation
+
+// 2nd-order FD d^2/dx^2 (the workloads' discretisation; the paper prints the
+// 4th-order matrices of Sec. 4.1.1/4.2): Dirichlet on n interior nodes,
+// h = L/(n+1), tridiag(1,-2,1)/h^2; Neumann on n nodes including both ends,
+// h = L/(n-1), ghost reflection giving rows (-2, 2) and (2, -2).
+// A = (a1 + i b1) D2 + (a2/d) I, n x n complex, column-major.
+std::vector<double2> fd_direction_matrix(const cgl_plan* p, int mu) {
+  const int n = (int)p->n[mu];
+  const double L = p->hi[mu] - p->lo[mu];
+  const double h = (p->bc[mu] == CGL_BC_DIRICHLET) ? L / (n + 1) : L / (n - 1);
+  const double ih2 = 1.0 / (h * h);
+  std::vector<double2> A((size_t)n * n, make_double2(0.0, 0.0));
+  auto put = [&](int i, int j, double v) {
+    A[(size_t)i + (size_t)j * n].x += p->a1 * v * ih2;
+    A[(size_t)i + (size_t)j * n].y += p->b1 * v * ih2;
+  };
+  for (int i = 0; i < n; ++i) {
+    put(i, i, -2.0);
+    if (i > 0) put(i, i - 1, (p->bc[mu] == CGL_BC_NEUMANN && i == n - 1) ? 2.0 : 1.0);
+    if (i < n - 1) put(i, i + 1, (p->bc[mu] == CGL_BC_NEUMANN && i == 0) ? 2.0 : 1.0);
+    A[(size_t)i + (size_t)i * n].x += p->a2 / p->d;
+  }
+  return A;
+}
+
+double norm1(const std::vector<double2>& A, int n) {
+  double best = 0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += std::hypot(A[(size_t)i + (size_t)j * n].x, A[(size_t)i + (size_t)j * n].y);
+    best = std::max(best, s);
+  }
+  return best;
+}
+
+int dev_alloc(cgl_plan* p, void** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return fail(CGL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  p->allocations.push_back(*ptr);
+  return CGL_OK;
+}
+
+// Copy an FP64 vector to a working-precision buffer.
+int make_working(cgl_plan* p, const double2* src64, int64_t count, void** dst, cudaStream_t s) {
+  if (p->precision == CGL_F64) {
+    *dst = (void*)src64;
+    return CGL_OK;
+  }
+  int st = dev_alloc(p, dst, count * sizeof(float2));
+  if (st) return st;
+  CUDA_TRY(convert_f64_to_f32(src64, (float2*)*dst, count, s));
+  return CGL_OK;
+}
+
+int build_factors(cgl_plan* p, cudaStream_t s) {
+  // FD: exp(c tau A_mu) per distinct c and direction, shared between
+  // directions with identical (n, bc, lo, hi).
+  int st;
+  if (!p->periodic) {
+    int64_t nmax = 0;
+    for (int m = 0; m < p->d; ++m) nmax = std::max(nmax, p->n[m]);
+    double2 *dA = nullptr, *dW = nullptr;
+    if ((st = dev_alloc(p, (void**)&dA, nmax * nmax * sizeof(double2)))) return st;
+    if ((st = dev_alloc(p, (void**)&dW, 3 * nmax * nmax * sizeof(double2)))) return st;
+    for (int c = 0; c < p->nfac; ++c) {
+      for (int mu = 0; mu < p->d; ++mu) {
+        int same = -1;
+        for (int nu = 0; nu < mu; ++nu)
+          if (p->n[nu] == p->n[mu] && p->bc[nu] == p->bc[mu] && p->lo[nu] == p->lo[mu] && p->hi[nu] == p->hi[mu])
+            same = nu;
+        if (same >= 0) {
+          p->fac64[c][mu] = p->fac64[c][same];
+          p->fac[c][mu] = p->fac[c][same];
+          continue;
+        }
+        const int n = (int)p->n[mu];
+        std::vector<double2> A = fd_direction_matrix(p, mu);
+        CUDA_TRY(cudaMemcpyAsync(dA, A.data(), A.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+        if ((st = dev_alloc(p, (void**)&p->fac64[c][mu], (size_t)n * n * sizeof(double2)))) return st;
+        CUDA_TRY(expm_device(dA, p->cval[c] * p->tau, n, p->fac64[c][mu], dW, norm1(A, n), s));
+        if ((st = make_working(p, p->fac64[c][mu], (int64_t)n * n, &p->fac[c][mu], s))) return st;
+        // the host copy of A must stay alive until the upload has completed
+        CUDA_TRY(cudaStreamSynchronize(s));
+      }
+    }
+    return CGL_OK;
+  }
+  // periodic: per-direction symbol vectors; the inverse FFT's 1/n_mu is
+  // folded into each factor of the product form, 1/N into each term of
+  // the sum form.
+  for (int mu = 0; mu < p->d; ++mu) {
+    const int n = (int)p->n[mu];
+    const double L = p->hi[mu] - p->lo[mu];
+    for (int c = 0; c < p->nfac; ++c) {
+      if ((st = dev_alloc(p, (void**)&p->fac64[c][mu], n * sizeof(double2)))) return st;
+      CUDA_TRY(periodic_symbol_device(p->fac64[c][mu], n, L, p->cval[c] * p->tau, p->a1, p->b1, p->a2 / p->d,
+                                      1.0 / n, 0, s));
+      if ((st = make_working(p, p->fac64[c][mu], n, &p->fac[c][mu], s))) return st;
+    }
+    if (p->scheme == CGL_RK4 || p->scheme == CGL_RK2) {
+      double2* k64 = nullptr;
+      if ((st = dev_alloc(p, (void**)&k64, n * sizeof(double2)))) return st;
+      CUDA_TRY(periodic_symbol_device(k64, n, L, 0.0, p->a1, p->b1, p->a2 / p->d, 1.0 / (double)p->N, 1, s));
+      if ((st = make_working(p, k64, n, &p->ksym[mu], s))) return st;
+    }
+    double2* tw64 = nullptr;
+    if ((st = dev_alloc(p, (void**)&tw64, n * sizeof(double2)))) return st;
+    CUDA_TRY(twiddle_device(tw64, n, s));
+    if ((st = make_working(p, tw64, n, &p->twiddle[mu], s))) return st;
+  }
+  return CGL_OK;
+}
+
+void build_program(cgl_plan* p) {
+  const double tau = p->tau;
+  NlParams nl{p->a3, p->b3, p->a4, p->b4, p->cubic, tau};
+  auto base = [&]() {
+    Sweep s;
+    s.op.nl = nl;
+    return s;
+  };
+  p->sweeps.clear();
+  switch (p->scheme) {
+    case CGL_STRANG: {  // eq. Strang
+      Sweep s = base();
+      s.op.pro = PRO_FLOW; s.op.t0 = tau / 2;
+      s.op.epi = EPI_FLOW; s.op.te = tau / 2;
+      s.fac[0] = 0;
+      p->sweeps.push_back(s);
+      break;
+    }
+    case CGL_SPLIT4: {  // eq. Richardson; factor 0: c = 1, factor 1: c = 1/2
+      Sweep s1 = base();
+      s1.op.pro = PRO_FLOW2; s1.op.t0 = tau / 2; s1.op.t1 = tau / 4;
+      s1.nrhs = 2; s1.fac[0] = 0; s1.fac[1] = 1; s1.work[0] = BUF_W0; s1.work[1] = BUF_W1;
+      s1.op.epi = EPI_FLOW2; s1.op.te = tau / 2;
+      s1.nout = 2; s1.out[0] = BUF_W0; s1.out[1] = BUF_W1;  // u_{n2}, v
+      Sweep s2 = base();
+      s2.in[0] = BUF_W1; s2.fac[0] = 1; s2.work[0] = BUF_W1;
+      s2.op.epi = EPI_SPLIT4; s2.op.te = tau / 4;
+      s2.nextra = 1; s2.extra[0] = BUF_W0;
+      s2.out[0] = BUF_U;
+      p->sweeps.push_back(s1);
+      p->sweeps.push_back(s2);
+      break;
+    }
+    case CGL_LAWSON4: {  // eq. lawson4 with E = exp(tau K/2), factor 0: c = 1/2
+      Sweep s1 = base();
+      s1.op.pro = PRO_LAW4;
+      s1.nrhs = 2; s1.work[0] = BUF_W0; s1.work[1] = BUF_W1;
+      s1.op.epi = EPI_LAW4A;
+      s1.nout = 2; s1.out[0] = BUF_W0; s1.out[1] = BUF_W1;  // p, w
+      Sweep s2 = base();
+      s2.nin = 2; s2.in[0] = BUF_W0; s2.in[1] = BUF_W1;
+      s2.nrhs = 2; s2.work[0] = BUF_W0; s2.work[1] = BUF_W1;
+      s2.op.epi = EPI_LAW4B;
+      s2.out[0] = BUF_U;
+      p->sweeps.push_back(s1);
+      p->sweeps.push_back(s2);
+      break;
+    }
+    case CGL_LAWSON2: {  // eq. lawson2b, factor 0: c = 1
+      Sweep s = base();
+      s.op.pro = PRO_LAW2;
+      s.nrhs = 2; s.work[0] = BUF_W0; s.work[1] = BUF_W1;
+      s.op.epi = EPI_LAW2;
+      s.out[0] = BUF_U;
+      p->sweeps.push_back(s);
+      break;
+    }
+    case CGL_RK4:
+    case CGL_RK2: {  // eq. RK4 / eq. RK2: stage s computes K x_s with x_1 = u
+      const int stages = p->scheme == CGL_RK4 ? 4 : 2;
+      for (int st = 1; st <= stages; ++st) {
+        Sweep s = base();
+        s.in[0] = (st == 1) ? BUF_U : BUF_W1;  // x_s
+        s.fac[0] = FAC_K;
+        s.work[0] = BUF_W0;
+        s.op.epi = EPI_RK; s.op.rk_scheme = stages; s.op.rk_stage = st;
+        s.nextra = 3; s.extra[0] = s.in[0]; s.extra[1] = BUF_U; s.extra[2] = BUF_W2;
+        if (st < stages) { s.nout = 2; s.out[0] = BUF_W1; s.out[1] = BUF_W2; }
+        else { s.nout = 1; s.out[0] = BUF_U; }
+        p->sweeps.push_back(s);
+      }
+      break;
+    }
+  }
+}
+
+bool finite_all(std::initializer_list<double> v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+// Kernel attributes are set once per process and device, before any capture.
+cudaError_t prepare_kernels(int dev) {
+  static bool done[64] = {false};
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  cudaError_t e;
+  if ((e = prepare_fft_pass<double>()) != cudaSuccess) return e;
+  if ((e = prepare_fft_pass<float>()) != cudaSuccess) return e;
+  if ((e = prepare_mode_pass<double>()) != cudaSuccess) return e;
+  if ((e = prepare_mode_pass<float>()) != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return cudaSuccess;
+}
+
+int ensure_graph(cgl_plan* p, void* u) {
+  if (p->exec && p->graph_u == u) return CGL_OK;
+  if (p->exec) {
+    cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+  }
+  CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+  int st = enqueue_step(p, u, p->cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
+  if (st != CGL_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&p->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    p->exec = nullptr;
+    return fail(CGL_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  p->graph_u = u;
+  return CGL_OK;
+}
+
+void free_plan(cgl_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  for (void* a : p->allocations) cudaFree(a);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cgl_strerror(int status) {
+  switch (status) {
+    case CGL_OK: return "ok";
+    case CGL_EINVAL: return "invalid argument";
+    case CGL_ENOMEM: return "device allocation failed";
+    case CGL_ECUDA: return "CUDA runtime error";
+    case CGL_EUNSUPPORTED: return "unsupported configuration";
+    case CGL_ETIMEOUT: return "device-side wait timed out";
+    case CGL_ENONFINITE: return "non-finite value produced";
+    default: return "unknown status";
+  }
+}
+
+const char* cgl_last_error(void) { return g_last_error.c_str(); }
+
+int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
+                    double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
+                    int scheme, int precision, void* stream) {
+  g_last_error.clear();
+  if (!out) return fail(CGL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > 3) return fail(CGL_EINVAL, "d must be 1, 2 or 3");
+  if (!n || !bc || !lo || !hi) return fail(CGL_EINVAL, "n, bc, lo, hi must be non-NULL");
+  if (!finite_all({a1, b1, a2, a3, b3, a4, b4, tau})) return fail(CGL_EINVAL, "parameters must be finite");
+  if (!(a1 > 0)) return fail(CGL_EINVAL, "alpha1 must be positive");
+  if (!(tau > 0)) return fail(CGL_EINVAL, "tau must be positive");
+  if (scheme < CGL_STRANG || scheme > CGL_RK2) return fail(CGL_EINVAL, "unknown scheme");
+  if (precision != CGL_F64 && precision != CGL_F32) return fail(CGL_EINVAL, "unknown precision");
+  int nper = 0;
+  for (int m = 0; m < d; ++m) {
+    if (bc[m] < CGL_BC_DIRICHLET || bc[m] > CGL_BC_PERIODIC) return fail(CGL_EINVAL, "unknown boundary condition");
+    if (n[m] < 2) return fail(CGL_EINVAL, "n_mu must be >= 2");
+    if (!std::isfinite(lo[m]) || !std::isfinite(hi[m]) || !(hi[m] > lo[m]))
+      return fail(CGL_EINVAL, "domain must satisfy lo < hi (finite)");
+    nper += bc[m] == CGL_BC_PERIODIC;
+  }
+  if (nper != 0 && nper != d)
+    return fail(CGL_EUNSUPPORTED, "mixing periodic and finite-difference directions is not supported");
+  const bool periodic = nper == d;
+  for (int m = 0; m < d; ++m) {
+    if (periodic && ((n[m] & (n[m] - 1)) != 0 || n[m] > 2048))
+      return fail(CGL_EUNSUPPORTED, "periodic sizes must be powers of two <= 2048");
+    if (!periodic && n[m] > 1024) return fail(CGL_EUNSUPPORTED, "finite-difference sizes must be <= 1024");
+  }
+  if (!periodic && (scheme == CGL_RK4 || scheme == CGL_RK2))
+    return fail(CGL_EUNSUPPORTED, "Runge-Kutta schemes need periodic directions");
+
+  cgl_plan* p = new cgl_plan();
+  cudaGetDevice(&p->dev);
+  p->d = d;
+  p->N = 1;
+  for (int m = 0; m < d; ++m) {
+    p->n[m] = n[m];
+    p->bc[m] = bc[m];
+    p->lo[m] = lo[m];
+    p->hi[m] = hi[m];
+    p->N *= n[m];
+  }
+  p->a1 = a1; p->b1 = b1; p->a2 = a2; p->a3 = a3; p->b3 = b3; p->a4 = a4; p->b4 = b4;
+  p->tau = tau;
+  p->scheme = scheme;
+  p->precision = precision;
+  p->periodic = periodic;
+  p->cubic = (a4 == 0.0 && b4 == 0.0);
+  p->elem = precision == CGL_F64 ? sizeof(double2) : sizeof(float2);
+  switch (scheme) {
+    case CGL_STRANG:
+    case CGL_LAWSON2: p->nfac = 1; p->cval[0] = 1.0; break;
+    case CGL_SPLIT4: p->nfac = 2; p->cval[0] = 1.0; p->cval[1] = 0.5; break;
+    case CGL_LAWSON4: p->nfac = 1; p->cval[0] = 0.5; break;
+    default: p->nfac = 0;
+  }
+  switch (scheme) {
+    case CGL_STRANG: p->nwork = 0; break;
+    case CGL_RK4:
+    case CGL_RK2: p->nwork = 3; break;
+    default: p->nwork = 2;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = CGL_OK;
+  cudaError_t e = prepare_kernels(p->dev);
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(CGL_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  }
+  e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("stream create: ") + cudaGetErrorString(e));
+  if (!st) st = dev_alloc(p, (void**)&p->status, sizeof(int));
+  if (!st && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) st = fail(CGL_ECUDA, "memset status");
+  for (int w = 0; !st && w < p->nwork; ++w) st = dev_alloc(p, &p->work[w], p->N * p->elem);
+  if (!st) st = build_factors(p, s);
+  if (!st) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("plan set-up: ") + cudaGetErrorString(e));
+  }
+  if (st) {
+    free_plan(p);
+    return st;
+  }
+  build_program(p);
+  *out = p;
+  return CGL_OK;
+}
+
+int cgl_plan_destroy(cgl_plan* p) {
+  if (!p) return CGL_OK;
+  cudaSetDevice(p->dev);
+  free_plan(p);
+  return CGL_OK;
+}
+
+int cgl_step(cgl_plan* p, void* u, int64_t nsteps, void* stream) {
+  if (!p || !u) return fail(CGL_EINVAL, "plan and u must be non-NULL");
+  if (nsteps < 0) return fail(CGL_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return CGL_OK;
+  CUDA_TRY(cudaSetDevice(p->dev));
+  int st = ensure_graph(p, u);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int64_t k = 0; k < nsteps; ++k) CUDA_TRY(cudaGraphLaunch(p->exec, s));
+  return CGL_OK;
+}
+
+int cgl_step_host(cgl_plan* p, void* u_host, int64_t nsteps, void* stream) {
+  if (!p || !u_host) return fail(CGL_EINVAL, "plan and u_host must be non-NULL");
+  if (nsteps < 0) return fail(CGL_EINVAL, "nsteps must be >= 0");
+  CUDA_TRY(cudaSetDevice(p->dev));
+  if (!p->host_stage) {
+    int st = dev_alloc(p, &p->host_stage, p->N * p->elem);
+    if (st) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = p->N * p->elem;
+  CUDA_TRY(cudaMemcpyAsync(p->host_stage, u_host, bytes, cudaMemcpyHostToDevice, s));
+  int st = cgl_step(p, p->host_stage, nsteps, stream);
+  if (st) return st;
+  CUDA_TRY(cudaMemcpyAsync(u_host, p->host_stage, bytes, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return CGL_OK;
+}
+
+int cgl_linear_flow(cgl_plan* p, double c, void* u, void* stream) {
+  if (!p || !u) return fail(CGL_EINVAL, "plan and u must be non-NULL");
+  int idx = -1;
+  for (int k = 0; k < p->nfac; ++k)
+    if (p->cval[k] == c) idx = k;
+  if (idx < 0) return fail(CGL_EINVAL, "c is not one of the plan's factor values");
+  CUDA_TRY(cudaSetDevice(p->dev));
+  Sweep s;
+  s.op.nl = NlParams{p->a3, p->b3, p->a4, p->b4, p->cubic, p->tau};
+  s.fac[0] = idx;
+  return enqueue_sweep(p, s, u, (cudaStream_t)stream);
+}
+
+int cgl_plan_factor(cgl_plan* p, double c, int mu, double* host_out) {
+  if (!p || !host_out) return fail(CGL_EINVAL, "plan and host_out must be non-NULL");
+  if (mu < 0 || mu >= p->d) return fail(CGL_EINVAL, "mu out of range");
+  int idx = -1;
+  for (int k = 0; k < p->nfac; ++k)
+    if (p->cval[k] == c) idx = k;
+  if (idx < 0) return fail(CGL_EINVAL, "c is not one of the plan's factor values");
+  CUDA_TRY(cudaSetDevice(p->dev));
+  const size_t count = p->periodic ? (size_t)p->n[mu] : (size_t)p->n[mu] * p->n[mu];
+  CUDA_TRY(cudaMemcpy(host_out, p->fac64[idx][mu], count * sizeof(double2), cudaMemcpyDeviceToHost));
+  return CGL_OK;
+}
+
+int cgl_plan_info(const cgl_plan* p, size_t* field_bytes, size_t* workspace_bytes, int* launches) {
+  if (!p) return fail(CGL_EINVAL, "plan is NULL");
+  if (field_bytes) *field_bytes = p->N * p->elem;
+  if (workspace_bytes) *workspace_bytes = (size_t)p->nwork * p->N * p->elem;
+  if (launches) *launches = launches_per_step(p);
+  return CGL_OK;
+}
+
+int cgl_last_device_status(cgl_plan* p, void* stream) {
+  if (!p) return fail(CGL_EINVAL, "plan is NULL");
+  CUDA_TRY(cudaSetDevice(p->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return (h & 1) ? CGL_ENONFINITE : CGL_OK;
+}
+
+int cgl_profile_step(cgl_plan* p, void* u, int64_t nsteps, void* stream, cgl_kernel_time* out, int max_kernels,
+                     int* count) {
+  if (!p || !u || !count || (max_kernels > 0 && !out)) return fail(CGL_EINVAL, "NULL argument");
+  CUDA_TRY(cudaSetDevice(p->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::map<std::string, KernelStat> stats;
+  p->prof = true;
+  p->stats = &stats;
+  int st = CGL_OK;
+  for (int64_t k = 0; k < nsteps && st == CGL_OK; ++k) st = enqueue_step(p, u, s);
+  p->prof = false;
+  p->stats = nullptr;
+  if (st) return st;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int c = 0;
+  for (auto& kv : stats) {
+    if (c >= max_kernels) break;
+    std::memset(out[c].name, 0, sizeof(out[c].name));
+    std::strncpy(out[c].name, kv.first.c_str(), sizeof(out[c].name) - 1);
+    out[c].launches = kv.second.launches;
+    out[c].total_ms = kv.second.ms;
+    out[c].flops = kv.second.flops;
+    out[c].bytes = kv.second.bytes;
+    ++c;
+  }
+  *count = c;
+  return CGL_OK;
+}
+
+int cgl_rel_error(const void* x, const void* y, int64_t count, int precision, double* out, void* stream) {
+  if (!x || !y || !out) return fail(CGL_EINVAL, "NULL argument");
+  if (count <= 0) return fail(CGL_EINVAL, "count must be positive");
+  if (precision != CGL_F64 && precision != CGL_F32) return fail(CGL_EINVAL, "unknown precision");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = rel_error_blocks(count);
+  double* scratch = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&scratch, (5 * (size_t)nb + 3) * sizeof(double), s));
+  cudaError_t e = rel_error_device(x, y, count, precision, scratch, nb, out, s);
+  cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("rel_error: ") + cudaGetErrorString(e));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return CGL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,301 @@
+// Internal declarations shared by the libcgl translation units.
+//
+// Layout: a field is N complex values (T2 = double2 or float2), index 1
+// fastest (the paper's vec(U), Sec. 3.1).  A "pass" works on pencils/fibers
+// along one axis mu: pencil b in [0, N/n_mu) has its element j at
+//   (b % P) + P*j + P*n_mu*(b / P),   P = n_1*...*n_{mu-1}.
+// Each CTA owns whole pencils, so every pass may run in place.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cgl.h"
+
+namespace cgl {
+
+constexpr int kMaxRhs = 2;
+constexpr int kMaxExtra = 3;
+
+// ---------------------------------------------------------------- complex
+
+template <class T> struct C2;
+template <> struct C2<double> { using type = double2; };
+template <> struct C2<float> { using type = float2; };
+
+template <class T2> __host__ __device__ __forceinline__ T2 mk(decltype(T2{}.x) re, decltype(T2{}.x) im) {
+  T2 r; r.x = re; r.y = im; return r;
+}
+template <class T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk<T2>(a.x + b.x, a.y + b.y); }
+template <class T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk<T2>(a.x - b.x, a.y - b.y); }
+template <class T2, class T> __device__ __forceinline__ T2 cscale(T2 a, T s) { return mk<T2>(a.x * s, a.y * s); }
+template <class T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  return mk<T2>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+template <class T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {
+  return mk<T2>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// a + s*b  (s real)
+template <class T2, class T> __device__ __forceinline__ T2 caxpy(T2 a, T s, T2 b) {
+  return mk<T2>(fma(s, b.x, a.x), fma(s, b.y, a.y));
+}
+
+// ---------------------------------------------------------------- operators
+
+// Prologue: maps the pass inputs (1 or 2 fields) to the fields transformed by
+// the linear flow.  Epilogue: maps the transformed fields and extra inputs to
+// the outputs.  Both are pointwise and evaluated once per grid point.
+enum ProOp : int {
+  PRO_NONE = 0,    // z_r = in_r
+  PRO_FLOW = 1,    // z0 = phi_{t0}(in0)                              (Strang)
+  PRO_FLOW2 = 2,   // z0 = phi_{t0}(in0), z1 = phi_{t1}(in0)           (split4, first sweep)
+  PRO_LAW4 = 3,    // z0 = in0, z1 = g(in0)                            (Lawson4, first sweep)
+  PRO_LAW2 = 4     // z0 = in0 + tau g(in0), z1 = in0 + tau/2 g(in0)   (Lawson2)
+};
+enum EpiOp : int {
+  EPI_NONE = 0,    // out_r = y_r
+  EPI_FLOW = 1,    // out0 = phi_t(y0)                                 (Strang)
+  EPI_FLOW2 = 2,   // out0 = phi_t(y0), out1 = phi_t(y1)               (split4, first sweep)
+  EPI_SPLIT4 = 3,  // out0 = 4/3 phi_t(y0) - 1/3 e0                    (split4, second sweep)
+  EPI_LAW4A = 4,   // (a, b) -> (p, w)                                 (Lawson4, first sweep)
+  EPI_LAW4B = 5,   // (q, r) -> r + tau/6 g(q)                         (Lawson4, second sweep)
+  EPI_LAW2 = 6,    // (v, w) -> w + tau/2 g(v)                         (Lawson2)
+  EPI_RK = 7       // Runge-Kutta stage, see rk_stage()
+};
+
+// Nonlinear model parameters (eq. 1) and the per-pass operator constants.
+struct NlParams {
+  double a3, b3, a4, b4;
+  int cubic;       // a4 = b4 = 0: exact flow (eq. exsolcub); else one RK4 step
+  double tau;
+};
+
+struct OpArgs {
+  int pro, epi;
+  double t0, t1;   // prologue flow times
+  double te;       // epilogue flow time
+  int rk_scheme;   // 4 or 2 (EPI_RK)
+  int rk_stage;    // 1-based stage (EPI_RK)
+  NlParams nl;
+};
+
+// g(u) = (a3 + i b3)|u|^2 u + (a4 + i b4)|u|^4 u  (eq. 1)
+template <class T, class T2> __device__ __forceinline__ T2 nl_g(const NlParams& p, T2 u) {
+  const T rho = fma(u.x, u.x, u.y * u.y);
+  const T cr = rho * fma(T(p.a4), rho, T(p.a3));
+  const T ci = rho * fma(T(p.b4), rho, T(p.b3));
+  return mk<T2>(fma(cr, u.x, -ci * u.y), fma(cr, u.y, ci * u.x));
+}
+
+// Lambda(x) = -log|1-x|/x, Lambda(0) = 1; with it the exact flows read
+// u0 exp((a + i b) r t Lambda(k a r t)) (eq. exsolcub and its quintic
+// counterpart in Sec. 4.3), defined also for a = 0.
+template <class T> __device__ __forceinline__ T lambda_fn(T x) {
+  if (fabs(x) < T(1e-8)) return T(1) + x * (T(0.5) + x * (T(1) / T(3)));
+  const T lg = (x < T(1)) ? log1p(-x) : log(x - T(1));
+  return -lg / x;
+}
+
+// Exact flow of u' = (a + i b) rho^k u over time t, rho = |u|^2, k = 1 (cubic)
+// or 2 (quintic): |u|^{2k} obeys r' = 2k a r^{k+1}, giving
+// u(t) = u0 exp((a + i b) rho^k t Lambda(2k a rho^k t)).
+template <class T, class T2> __device__ __forceinline__ T2 exact_power_flow(T2 u, T a, T b, int k, T t) {
+  const T rho = fma(u.x, u.x, u.y * u.y);
+  const T rk = (k == 1) ? rho : rho * rho;
+  const T s = rk * t * lambda_fn<T>(T(2 * k) * a * rk * t);
+  const T m = exp(a * s);
+  T sn, cs;
+  sincos(b * s, &sn, &cs);
+  return mk<T2>(m * fma(u.x, cs, -u.y * sn), m * fma(u.x, sn, u.y * cs));
+}
+
+// phi_t: nonlinear flow of the splitting schemes (Sec. 2.1): exact for the
+// cubic model (eq. exsolcub); one RK4 step of u' = g(u) otherwise (Sec. 4.3).
+template <class T, class T2> __device__ __forceinline__ T2 nl_flow(const NlParams& p, T2 u, T t) {
+  if (p.cubic) return exact_power_flow<T, T2>(u, T(p.a3), T(p.b3), 1, t);
+  const T h = t * T(0.5);
+  const T2 k1 = nl_g<T, T2>(p, u);
+  const T2 k2 = nl_g<T, T2>(p, caxpy(u, h, k1));
+  const T2 k3 = nl_g<T, T2>(p, caxpy(u, h, k2));
+  const T2 k4 = nl_g<T, T2>(p, caxpy(u, t, k3));
+  const T2 s = cadd(cadd(k1, k4), cscale(cadd(k2, k3), T(2)));
+  return caxpy(u, t * (T(1) / T(6)), s);
+}
+
+template <class T, class T2>
+__device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2* z) {
+  switch (o.pro) {
+    case PRO_FLOW:
+      z[0] = nl_flow<T, T2>(o.nl, in[0], T(o.t0));
+      break;
+    case PRO_FLOW2:
+      z[0] = nl_flow<T, T2>(o.nl, in[0], T(o.t0));
+      z[1] = nl_flow<T, T2>(o.nl, in[0], T(o.t1));
+      break;
+    case PRO_LAW4:
+      z[0] = in[0];
+      z[1] = nl_g<T, T2>(o.nl, in[0]);
+      break;
+    case PRO_LAW2: {
+      const T2 gn = nl_g<T, T2>(o.nl, in[0]);
+      const T tau = T(o.nl.tau);
+      z[0] = caxpy(in[0], tau, gn);
+      z[1] = caxpy(in[0], tau * T(0.5), gn);
+      break;
+    }
+    default:
+      z[0] = in[0];
+      z[1] = in[1];
+  }
+}
+
+// Runge-Kutta stage epilogue on y = K x (eq. RK4 / eq. RK2):
+// extras e0 = x (stage argument), e1 = u_n, e2 = acc; outputs o0, o1.
+//   RK4 s=1..3: k = y + g(x); acc (+)= w_s k; x_next = u_n + c_{s+1} k  -> (x_next, acc)
+//   RK4 s=4   : u_{n+1} = u_n + tau/6 (acc + k)                        -> (u_{n+1})
+//   RK2 s=1   : acc = k; x_next = u_n + tau k ; s=2: u_n + tau/2 (acc + k)
+template <class T, class T2>
+__device__ __forceinline__ int rk_stage(const OpArgs& o, T2 y, const T2* e, T2* out) {
+  const T tau = T(o.nl.tau);
+  const T2 k = cadd(y, nl_g<T, T2>(o.nl, e[0]));
+  if (o.rk_scheme == 4) {
+    switch (o.rk_stage) {
+      case 1: out[1] = k; out[0] = caxpy(e[1], tau * T(0.5), k); return 2;
+      case 2: out[1] = caxpy(e[2], T(2), k); out[0] = caxpy(e[1], tau * T(0.5), k); return 2;
+      case 3: out[1] = caxpy(e[2], T(2), k); out[0] = caxpy(e[1], tau, k); return 2;
+      default: out[0] = caxpy(e[1], tau * (T(1) / T(6)), cadd(e[2], k)); return 1;
+    }
+  }
+  if (o.rk_stage == 1) { out[1] = k; out[0] = caxpy(e[1], tau, k); return 2; }
+  out[0] = caxpy(e[1], tau * T(0.5), cadd(e[2], k));
+  return 1;
+}
+
+// Returns the number of outputs written.
+template <class T, class T2>
+__device__ __forceinline__ int apply_epilogue(const OpArgs& o, const T2* y, const T2* e, T2* out) {
+  const T tau = T(o.nl.tau);
+  switch (o.epi) {
+    case EPI_FLOW:
+      out[0] = nl_flow<T, T2>(o.nl, y[0], T(o.te));
+      return 1;
+    case EPI_FLOW2:
+      out[0] = nl_flow<T, T2>(o.nl, y[0], T(o.te));
+      out[1] = nl_flow<T, T2>(o.nl, y[1], T(o.te));
+      return 2;
+    case EPI_SPLIT4: {
+      const T2 f = nl_flow<T, T2>(o.nl, y[0], T(o.te));
+      out[0] = mk<T2>(fma(T(4) / T(3), f.x, -(T(1) / T(3)) * e[0].x),
+                      fma(T(4) / T(3), f.y, -(T(1) / T(3)) * e[0].y));
+      return 1;
+    }
+    case EPI_LAW4A: {
+      // a = E u, b = E g(u) with E = exp(tau K / 2); Lawson4 (eq. lawson4)
+      // rewritten with E^2 = exp(tau K):  u2 = a + tau/2 b, u3 = a + tau/2 g(u2),
+      // p = a + tau g(u3) (so u4 = E p), w = a + tau/6 b + tau/3 (g(u2)+g(u3))
+      // (so u_{n+1} = E w + tau/6 g(E p)).
+      const T2 a = y[0], b = y[1];
+      const T2 g2 = nl_g<T, T2>(o.nl, caxpy(a, tau * T(0.5), b));
+      const T2 g3 = nl_g<T, T2>(o.nl, caxpy(a, tau * T(0.5), g2));
+      out[0] = caxpy(a, tau, g3);
+      out[1] = caxpy(caxpy(a, tau * (T(1) / T(6)), b), tau * (T(1) / T(3)), cadd(g2, g3));
+      return 2;
+    }
+    case EPI_LAW4B:
+      out[0] = caxpy(y[1], tau * (T(1) / T(6)), nl_g<T, T2>(o.nl, y[0]));
+      return 1;
+    case EPI_LAW2:
+      out[0] = caxpy(y[1], tau * T(0.5), nl_g<T, T2>(o.nl, y[0]));
+      return 1;
+    case EPI_RK:
+      return rk_stage<T, T2>(o, y[0], e, out);
+    default:
+      out[0] = y[0];
+      out[1] = y[1];
+      return 2;
+  }
+}
+
+__device__ __forceinline__ bool finite2(double2 v) { return isfinite(v.x) && isfinite(v.y); }
+__device__ __forceinline__ bool finite2(float2 v) { return isfinite(v.x) && isfinite(v.y); }
+
+// ---------------------------------------------------------------- passes
+
+// Field pointers of one pass (any may alias, see the layout note above).
+struct PassFields {
+  void* in[kMaxRhs];       // prologue inputs (first pass of a sweep)
+  void* work[kMaxRhs];     // fields transformed by the linear flow
+  void* extra[kMaxExtra];  // epilogue extra inputs (last pass)
+  void* out[kMaxRhs];      // epilogue outputs (last pass)
+  int nin, nrhs, nextra, nout;
+};
+
+// One pass over the pencils of axis `axis`.
+struct PassGeom {
+  int d;
+  int64_t n[3];
+  int axis;
+  int64_t n_ax;      // pencil length
+  int64_t P;         // element stride along the axis
+  int64_t npencils;  // N / n_ax
+};
+
+enum PassFlags : int {
+  PASS_PRO = 1,   // read `in`, apply prologue
+  PASS_FWD = 2,   // forward FFT along the axis (periodic)
+  PASS_MUL = 4,   // multiply by the separable Fourier symbol (last axis)
+  PASS_INV = 8,   // inverse FFT along the axis (periodic)
+  PASS_EPI = 16   // apply epilogue, write `out`
+};
+
+// Fourier symbol of one right-hand side: product form (exp(c tau K), the
+// tensor E of Sec. 3.2 with the inverse-FFT 1/N folded in) or sum form (K).
+struct Symbol {
+  const void* vec[3];  // per-axis vectors in FFT order (T2)
+  int sum_form;        // 0: prod_mu vec_mu[k_mu]   1: sum_mu vec_mu[k_mu]
+};
+
+struct FftPassArgs {
+  PassGeom g;
+  PassFields f;
+  OpArgs op;
+  int flags;
+  Symbol sym[kMaxRhs];
+  const void* twiddle;  // T2[n_ax]: exp(-2 pi i m / n_ax)
+  int* status;          // device status word (bit 0: non-finite output)
+};
+
+struct ModePassArgs {
+  PassGeom g;
+  PassFields f;
+  OpArgs op;
+  int flags;                     // PASS_PRO / PASS_EPI
+  const void* factor[kMaxRhs];   // n x n column-major T2 per rhs
+  int* status;
+};
+
+// Launchers (return cudaError_t of the launch).
+template <class T> cudaError_t launch_fft_pass(const FftPassArgs& a, cudaStream_t s);
+template <class T> cudaError_t launch_mode_pass(const ModePassArgs& a, cudaStream_t s);
+template <class T> cudaError_t prepare_fft_pass();
+template <class T> cudaError_t prepare_mode_pass();
+
+// expm.cu: FP64 complex n x n exponential of (scale * A) on the device.
+// dA: n x n column-major double2 (device); dOut: same layout.  work: 3*n*n double2.
+cudaError_t expm_device(const double2* dA, double scale, int n, double2* dOut, double2* work,
+                        double norm1, cudaStream_t s);
+// Periodic symbols: vec[k] = exp(c*tau*(alpha*(-kappa_k^2) + beta)) * post  (sum_form = 0)
+//                   vec[k] = (alpha*(-kappa_k^2) + beta) * post              (sum_form = 1)
+cudaError_t periodic_symbol_device(double2* dOut, int n, double L, double ctau, double ar,
+                                   double ai, double beta, double post, int sum_form,
+                                   cudaStream_t s);
+cudaError_t twiddle_device(double2* dOut, int n, cudaStream_t s);
+cudaError_t convert_f64_to_f32(const double2* src, float2* dst, int64_t count, cudaStream_t s);
+
+// norms.cu
+cudaError_t rel_error_device(const void* x, const void* y, int64_t count, int precision,
+                             double* d_partial, int nblocks, double* h_out, cudaStream_t s);
+int rel_error_blocks(int64_t count);
+
+}  // namespace cgl

@@ -1,0 +1,206 @@
+// mu-mode product pass (Sec. 3.1): V = U x_mu F, i.e. for every fiber along
+// axis mu, v_i = sum_j F_{ij} u_j with the dense n x n complex factor
+// F = exp(c tau A_mu).  A chain of d passes is the Tucker operator
+// (eq. Tucker).  SIMT kernel for FP64 (parity path) and FP32.
+//
+// A CTA owns `tb` whole fibers of every right-hand side: it loads them into
+// shared memory (applying the sweep's prologue on the first pass), then each
+// thread accumulates a 4-wide register block of outputs for both right-hand
+// sides and applies the sweep's epilogue before storing.  Two thread
+// mappings keep global accesses coalesced:
+//   mode 1 (P == 1, fibers contiguous): consecutive threads take consecutive
+//     rows i (F read column-major, coalesced); block = 4 fibers.
+//   other modes (P > 1, fibers strided): consecutive threads take consecutive
+//     fibers t (outputs of one row i are adjacent in memory); block = 4 rows,
+//     whose factor entries are a broadcast load.
+#include <algorithm>
+
+#include "cgl_internal.cuh"
+
+namespace cgl {
+
+constexpr int kModeThreads = 256;
+constexpr int kModeMaxSmem = 96 * 1024;
+
+template <class T2> __device__ __forceinline__ T2 ldm(const void* base, int64_t off) {
+  return reinterpret_cast<const T2*>(base)[off];
+}
+
+// acc += f * z
+template <class T2> __device__ __forceinline__ void cmac(T2& acc, T2 f, T2 z) {
+  acc.x = fma(f.x, z.x, acc.x);
+  acc.x = fma(-f.y, z.y, acc.x);
+  acc.y = fma(f.x, z.y, acc.y);
+  acc.y = fma(f.y, z.x, acc.y);
+}
+
+template <class T>
+__device__ __forceinline__ void finish_point(const ModePassArgs& a, typename C2<T>::type* y, int64_t off,
+                                             bool& bad) {
+  using T2 = typename C2<T>::type;
+  if (a.flags & PASS_EPI) {
+    T2 ex[kMaxExtra], o[2];
+    for (int x = 0; x < a.f.nextra; ++x) ex[x] = ldm<T2>(a.f.extra[x], off);
+    const int no = apply_epilogue<T, T2>(a.op, y, ex, o);
+    for (int x = 0; x < no && x < a.f.nout; ++x) {
+      reinterpret_cast<T2*>(a.f.out[x])[off] = o[x];
+      bad |= !finite2(o[x]);
+    }
+  } else {
+    reinterpret_cast<T2*>(a.f.work[0])[off] = y[0];
+    if (a.f.nrhs > 1) reinterpret_cast<T2*>(a.f.work[1])[off] = y[1];
+  }
+}
+
+template <class T, int NRHS>
+__global__ void __launch_bounds__(kModeThreads) mode_pass_kernel(const ModePassArgs a, int tbmax) {
+  using T2 = typename C2<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = (int)a.g.n_ax;
+  const int pitch = n + 1;
+  const int64_t P = a.g.P;
+  const int64_t b0 = (int64_t)blockIdx.x * tbmax;
+  const int tb = (int)min((int64_t)tbmax, a.g.npencils - b0);
+
+  T2* Z0 = reinterpret_cast<T2*>(smem_raw);
+  T2* Z1 = Z0 + tbmax * pitch;
+  int64_t* pbase = reinterpret_cast<int64_t*>(Z0 + NRHS * tbmax * pitch);
+
+  for (int t = threadIdx.x; t < tb; t += kModeThreads) {
+    const int64_t b = b0 + t;
+    pbase[t] = (b % P) + P * (int64_t)n * (b / P);
+  }
+  __syncthreads();
+
+  // ---- load (+ prologue)
+  const int cnt = tb * n;
+  for (int e = threadIdx.x; e < cnt; e += kModeThreads) {
+    int t, j;
+    if (P == 1) { t = e / n; j = e - t * n; }
+    else { j = e / tb; t = e - j * tb; }
+    const int64_t off = pbase[t] + P * j;
+    T2 z[2];
+    if (a.flags & PASS_PRO) {
+      T2 in[2];
+      in[0] = ldm<T2>(a.f.in[0], off);
+      in[1] = a.f.nin > 1 ? ldm<T2>(a.f.in[1], off) : in[0];
+      apply_prologue<T, T2>(a.op, in, z);
+    } else {
+      z[0] = ldm<T2>(a.f.work[0], off);
+      if (NRHS > 1) z[1] = ldm<T2>(a.f.work[1], off);
+    }
+    Z0[t * pitch + j] = z[0];
+    if (NRHS > 1) Z1[t * pitch + j] = z[1];
+  }
+  __syncthreads();
+
+  const T2* F0 = reinterpret_cast<const T2*>(a.factor[0]);
+  const T2* F1 = reinterpret_cast<const T2*>(a.factor[NRHS > 1 ? 1 : 0]);
+  bool bad = false;
+
+  if (P == 1) {
+    // rows i fast, 4 fibers per thread
+    const int tgroups = (tb + 3) / 4;
+    const int items = n * tgroups;
+    for (int w = threadIdx.x; w < items; w += kModeThreads) {
+      const int tg = w / n;
+      const int i = w - tg * n;
+      const int t0 = tg * 4;
+      T2 acc0[4], acc1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { acc0[u] = mk<T2>(0, 0); acc1[u] = mk<T2>(0, 0); }
+      const int tlim = min(4, tb - t0);
+      for (int j = 0; j < n; ++j) {
+        const T2 f0 = F0[i + (int64_t)j * n];
+        const T2 f1 = NRHS > 1 ? F1[i + (int64_t)j * n] : f0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u < tlim) {
+            cmac(acc0[u], f0, Z0[(t0 + u) * pitch + j]);
+            if (NRHS > 1) cmac(acc1[u], f1, Z1[(t0 + u) * pitch + j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u < tlim) {
+          T2 y[2] = {acc0[u], acc1[u]};
+          finish_point<T>(a, y, pbase[t0 + u] + i, bad);
+        }
+      }
+    }
+  } else {
+    // fibers t fast, 4 rows per thread
+    const int igroups = (n + 3) / 4;
+    const int items = tb * igroups;
+    for (int w = threadIdx.x; w < items; w += kModeThreads) {
+      const int ig = w / tb;
+      const int t = w - ig * tb;
+      const int i0 = ig * 4;
+      const int ilim = min(4, n - i0);
+      T2 acc0[4], acc1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { acc0[u] = mk<T2>(0, 0); acc1[u] = mk<T2>(0, 0); }
+      for (int j = 0; j < n; ++j) {
+        const T2 z0 = Z0[t * pitch + j];
+        const T2 z1 = NRHS > 1 ? Z1[t * pitch + j] : z0;
+        const T2* c0 = F0 + i0 + (int64_t)j * n;
+        const T2* c1 = F1 + i0 + (int64_t)j * n;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u < ilim) {
+            cmac(acc0[u], c0[u], z0);
+            if (NRHS > 1) cmac(acc1[u], c1[u], z1);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u < ilim) {
+          T2 y[2] = {acc0[u], acc1[u]};
+          finish_point<T>(a, y, pbase[t] + P * (i0 + u), bad);
+        }
+      }
+    }
+  }
+  if (bad && a.status) atomicOr(a.status, 1);
+}
+
+static int mode_tb(int n, int nrhs, size_t elem, int64_t npencils) {
+  const size_t per = (size_t)(n + 1) * elem * nrhs + sizeof(int64_t);
+  int tb = (int)std::min<size_t>(16, kModeMaxSmem / per);
+  tb = std::max(tb, 1);
+  return (int)std::min<int64_t>(tb, npencils);
+}
+
+template <class T> cudaError_t launch_mode_pass(const ModePassArgs& a, cudaStream_t s) {
+  using T2 = typename C2<T>::type;
+  const int n = (int)a.g.n_ax;
+  const int nrhs = a.f.nrhs;
+  const int tb = mode_tb(n, nrhs, sizeof(T2), a.g.npencils);
+  const int64_t grid = (a.g.npencils + tb - 1) / tb;
+  const size_t smem = (size_t)tb * (n + 1) * sizeof(T2) * nrhs + (size_t)tb * sizeof(int64_t);
+  if (nrhs > 1)
+    mode_pass_kernel<T, 2><<<(unsigned)grid, kModeThreads, smem, s>>>(a, tb);
+  else
+    mode_pass_kernel<T, 1><<<(unsigned)grid, kModeThreads, smem, s>>>(a, tb);
+  return cudaGetLastError();
+}
+
+// Opt in to large dynamic shared memory; called at plan creation, outside any
+// stream capture.
+template <class T> cudaError_t prepare_mode_pass() {
+  cudaError_t e = cudaFuncSetAttribute(mode_pass_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kModeMaxSmem + 4096);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(mode_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kModeMaxSmem + 4096);
+}
+
+template cudaError_t prepare_mode_pass<double>();
+template cudaError_t prepare_mode_pass<float>();
+
+template cudaError_t launch_mode_pass<double>(const ModePassArgs&, cudaStream_t);
+template cudaError_t launch_mode_pass<float>(const ModePassArgs&, cudaStream_t);
+
+}  // namespace cgl

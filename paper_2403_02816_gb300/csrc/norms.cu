@@ -1,0 +1,105 @@
+// Relative error norms (Sec. 4 measures relative errors against a reference
+// solution): ||x-y||_2/||y||_2 and ||x-y||_inf/||y||_inf, FP64 accumulation,
+// plus a count of non-finite entries of x (the blow-ups the paper's tables
+// mark with a cross).  Two launches: per-block partials, then one block
+// folds them.
+#include <algorithm>
+
+#include "cgl_internal.cuh"
+
+namespace cgl {
+
+constexpr int kNormThreads = 256;
+constexpr int kNormMaxBlocks = 1024;
+constexpr int kNormFields = 5;  // sum|d|^2, sum|y|^2, max|d|, max|y|, nonfinite
+
+template <class T2>
+__global__ void __launch_bounds__(kNormThreads) rel_error_partial(const T2* __restrict__ x,
+                                                                  const T2* __restrict__ y, int64_t count,
+                                                                  double* partial) {
+  double sd = 0, sy = 0, md = 0, my = 0, nf = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T2 a = x[i], b = y[i];
+    const double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y;
+    const double d2 = dx * dx + dy * dy;
+    const double y2 = (double)b.x * (double)b.x + (double)b.y * (double)b.y;
+    if (!(isfinite((double)a.x) && isfinite((double)a.y))) { nf += 1; continue; }
+    sd += d2;
+    sy += y2;
+    md = fmax(md, d2);
+    my = fmax(my, y2);
+  }
+  __shared__ double red[kNormFields][kNormThreads / 32];
+  double v[kNormFields] = {sd, sy, md, my, nf};
+#pragma unroll
+  for (int f = 0; f < kNormFields; ++f) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, v[f], o);
+      v[f] = (f == 2 || f == 3) ? fmax(v[f], w) : v[f] + w;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int f = 0; f < kNormFields; ++f) red[f][warp] = v[f];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r[kNormFields] = {0, 0, 0, 0, 0};
+    for (int w = 0; w < kNormThreads / 32; ++w)
+      for (int f = 0; f < kNormFields; ++f)
+        r[f] = (f == 2 || f == 3) ? fmax(r[f], red[f][w]) : r[f] + red[f][w];
+    for (int f = 0; f < kNormFields; ++f) partial[f * gridDim.x + blockIdx.x] = r[f];
+  }
+}
+
+__global__ void rel_error_final(const double* partial, int nblocks, double* result) {
+  __shared__ double red[kNormFields][kNormThreads];
+  double v[kNormFields] = {0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int f = 0; f < kNormFields; ++f) {
+      const double w = partial[f * nblocks + b];
+      v[f] = (f == 2 || f == 3) ? fmax(v[f], w) : v[f] + w;
+    }
+  for (int f = 0; f < kNormFields; ++f) red[f][threadIdx.x] = v[f];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int f = 0; f < kNormFields; ++f) {
+        const double w = red[f][threadIdx.x + s];
+        red[f][threadIdx.x] = (f == 2 || f == 3) ? fmax(red[f][threadIdx.x], w) : red[f][threadIdx.x] + w;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double sd = red[0][0], sy = red[1][0], md = red[2][0], my = red[3][0];
+    result[0] = sy > 0 ? sqrt(sd / sy) : (sd > 0 ? INFINITY : 0.0);
+    result[1] = my > 0 ? sqrt(md / my) : (md > 0 ? INFINITY : 0.0);
+    result[2] = red[4][0];
+  }
+}
+
+int rel_error_blocks(int64_t count) {
+  const int64_t b = (count + kNormThreads - 1) / kNormThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, kNormMaxBlocks));
+}
+
+// d_partial: kNormFields * nblocks + 3 doubles of device scratch.
+cudaError_t rel_error_device(const void* x, const void* y, int64_t count, int precision, double* d_partial,
+                             int nblocks, double* h_out, cudaStream_t s) {
+  double* result = d_partial + kNormFields * nblocks;
+  if (precision == CGL_F64)
+    rel_error_partial<double2><<<nblocks, kNormThreads, 0, s>>>((const double2*)x, (const double2*)y, count,
+                                                                 d_partial);
+  else
+    rel_error_partial<float2><<<nblocks, kNormThreads, 0, s>>>((const float2*)x, (const float2*)y, count,
+                                                                d_partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  rel_error_final<<<1, kNormThreads, 0, s>>>(d_partial, nblocks, result);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(h_out, result, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  return cudaStreamSynchronize(s);
+}
+
+}  // namespace cgl

@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libcgl (include/cgl.h): argument marshalling only.
+
+Every step of the integrators runs in the library's CUDA kernels; there is no
+Python or CPU fallback.  Loading fails loudly when ``lib/libcgl.so`` has not
+been built (``__graft_entry__.build()`` or ``python -m
+paper_2403_02816_gb300.build``).
+
+Function names match the C ABI.  ``Plan`` wraps a plan handle for torch
+tensors: a field is a contiguous complex tensor of shape (n_d, ..., n_1)
+(so that n_1 runs fastest, the paper's vec order), complex128 for F64 plans
+and complex64 for F32 plans, on the current CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libcgl.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "cgl.h")
+
+CGL_BC_DIRICHLET, CGL_BC_NEUMANN, CGL_BC_PERIODIC = 0, 1, 2
+CGL_STRANG, CGL_SPLIT4, CGL_LAWSON4, CGL_RK4, CGL_LAWSON2, CGL_RK2 = 0, 1, 2, 3, 4, 5
+CGL_F64, CGL_F32 = 0, 1
+CGL_OK, CGL_EINVAL, CGL_ENOMEM, CGL_ECUDA, CGL_EUNSUPPORTED, CGL_ETIMEOUT, CGL_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+
+SCHEMES = {"strang": CGL_STRANG, "split4": CGL_SPLIT4, "lawson4": CGL_LAWSON4, "rk4": CGL_RK4,
+           "lawson2": CGL_LAWSON2, "rk2": CGL_RK2}
+PRECISIONS = {"f64": CGL_F64, "f32": CGL_F32}
+
+
+class CglError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__("%s failed: %s (%d): %s" % (where, _strerror(status), status, msg))
+        self.status = status
+
+
+class cgl_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load lib/libcgl.so (once) and declare the signatures of include/cgl.h."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libcgl.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, I64, D, VP, SZ = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
+                            ctypes.c_size_t)
+    sig = {
+        "cgl_plan_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(D),
+                                ctypes.POINTER(D), D, D, D, D, D, D, D, D, I, I, VP]),
+        "cgl_step": (I, [P, VP, I64, VP]),
+        "cgl_step_host": (I, [P, VP, I64, VP]),
+        "cgl_plan_destroy": (I, [P]),
+        "cgl_linear_flow": (I, [P, D, VP, VP]),
+        "cgl_plan_factor": (I, [P, D, I, ctypes.POINTER(D)]),
+        "cgl_plan_info": (I, [P, ctypes.POINTER(SZ), ctypes.POINTER(SZ), ctypes.POINTER(I)]),
+        "cgl_last_device_status": (I, [P, VP]),
+        "cgl_profile_step": (I, [P, VP, I64, VP, ctypes.POINTER(cgl_kernel_time), I, ctypes.POINTER(I)]),
+        "cgl_rel_error": (I, [VP, VP, I64, I, ctypes.POINTER(D), VP]),
+        "cgl_strerror": (ctypes.c_char_p, [I]),
+        "cgl_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list:
+    """Names of the functions include/cgl.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cgl_[a-z0-9_]+)\s*\(", text)))
+
+
+def _strerror(status: int) -> str:
+    try:
+        return load().cgl_strerror(status).decode()
+    except Exception:
+        return "status"
+
+
+def check(status: int, where: str):
+    if status != CGL_OK:
+        msg = load().cgl_last_error().decode()
+        raise CglError(status, where, msg)
+    return status
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def cgl_plan_create(d, n, bc, lo, hi, a1, b1, a2, a3, b3, a4, b4, tau, scheme, precision, stream=None):
+    lib = load()
+    h = ctypes.c_void_p()
+    arr = lambda t, v: (t * len(v))(*v)
+    st = lib.cgl_plan_create(ctypes.byref(h), int(d), arr(ctypes.c_int64, n), arr(ctypes.c_int, bc),
+                             arr(ctypes.c_double, lo), arr(ctypes.c_double, hi), a1, b1, a2, a3, b3, a4, b4,
+                             tau, int(scheme), int(precision), _stream_handle(stream))
+    return st, h
+
+
+def cgl_rel_error(x, y, precision, stream=None):
+    """Relative L2 and inf errors of device tensor x against y (FP64 accumulation)."""
+    out = (ctypes.c_double * 3)()
+    check(load().cgl_rel_error(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
+                               int(precision), out, _stream_handle(stream)), "cgl_rel_error")
+    return out[0], out[1], int(out[2])
+
+
+class Plan:
+    """A libcgl plan for one problem, step size, scheme and precision."""
+
+    def __init__(self, prob, tau: float, scheme: str, precision: str = "f64", stream=None):
+        self.prob = prob
+        self.scheme = scheme
+        self.precision = precision
+        self.prec = PRECISIONS[precision]
+        st, self.handle = cgl_plan_create(prob.d, prob.n, prob.bc, prob.lo, prob.hi, prob.a1, prob.b1, prob.a2,
+                                          prob.a3, prob.b3, prob.a4, prob.b4, tau, SCHEMES[scheme], self.prec,
+                                          stream)
+        check(st, "cgl_plan_create")
+
+    # torch helpers -------------------------------------------------------
+    @property
+    def shape(self):
+        return tuple(reversed(self.prob.n))
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.complex128 if self.prec == CGL_F64 else torch.complex64
+
+    def _field(self, u):
+        if not u.is_cuda or not u.is_contiguous() or u.dtype != self.dtype or u.numel() != self.prob.N:
+            raise ValueError("field must be a contiguous %s CUDA tensor with %d elements"
+                             % (self.dtype, self.prob.N))
+        return ctypes.c_void_p(u.data_ptr())
+
+    def step(self, u, nsteps: int, stream=None):
+        check(load().cgl_step(self.handle, self._field(u), int(nsteps), _stream_handle(stream)), "cgl_step")
+        return u
+
+    def step_host(self, u_host, nsteps: int, stream=None):
+        """u_host: a CPU tensor (pinned or pageable), advanced in place."""
+        if u_host.is_cuda or not u_host.is_contiguous() or u_host.dtype != self.dtype:
+            raise ValueError("u_host must be a contiguous CPU tensor of %s" % self.dtype)
+        check(load().cgl_step_host(self.handle, ctypes.c_void_p(u_host.data_ptr()), int(nsteps),
+                                   _stream_handle(stream)), "cgl_step_host")
+        return u_host
+
+    def linear_flow(self, u, c: float, stream=None):
+        check(load().cgl_linear_flow(self.handle, float(c), self._field(u), _stream_handle(stream)),
+              "cgl_linear_flow")
+        return u
+
+    def factor(self, c: float, mu: int):
+        import numpy as np
+        n = self.prob.n[mu]
+        count = n if self.prob.periodic else n * n
+        buf = (ctypes.c_double * (2 * count))()
+        check(load().cgl_plan_factor(self.handle, float(c), int(mu), buf), "cgl_plan_factor")
+        a = np.frombuffer(buf, dtype=np.complex128).copy()
+        return a if self.prob.periodic else a.reshape((n, n), order="F")
+
+    def info(self):
+        fb, wb, nl = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int()
+        check(load().cgl_plan_info(self.handle, ctypes.byref(fb), ctypes.byref(wb), ctypes.byref(nl)),
+              "cgl_plan_info")
+        return {"field_bytes": fb.value, "workspace_bytes": wb.value, "launches_per_step": nl.value}
+
+    def device_status(self, stream=None) -> int:
+        return load().cgl_last_device_status(self.handle, _stream_handle(stream))
+
+    def profile(self, u, nsteps: int, stream=None):
+        recs = (cgl_kernel_time * 16)()
+        cnt = ctypes.c_int()
+        check(load().cgl_profile_step(self.handle, self._field(u), int(nsteps), _stream_handle(stream), recs, 16,
+                                      ctypes.byref(cnt)), "cgl_profile_step")
+        return [{"name": r.name.decode(), "launches": r.launches, "total_ms": r.total_ms, "flops": r.flops,
+                 "bytes": r.bytes} for r in recs[:cnt.value]]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().cgl_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def to_device(U, dtype, device="cuda"):
+    """numpy array of shape (n_1..n_d) -> contiguous torch tensor (n_d..n_1)."""
+    import numpy as np
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(U.T))
+    return t.to(dtype).to(device).contiguous()
+
+
+def from_device(t):
+    """torch tensor (n_d..n_1) -> complex128 numpy array (n_1..n_d)."""
+    import torch
+    return t.to(torch.complex128).cpu().numpy().T.copy()

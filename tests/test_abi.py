@@ -1,0 +1,78 @@
+"""The C-ABI library loads and exports every symbol include/cgl.h declares;
+argument validation that happens before any CUDA call (no GPU needed)."""
+import ctypes
+
+import pytest
+
+from paper_2403_02816_gb300 import build as B
+from paper_2403_02816_gb300 import native as nat
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return nat.load()
+
+
+def test_header_declares_the_entry_points():
+    names = nat.header_functions()
+    for need in ["cgl_plan_create", "cgl_step", "cgl_plan_destroy", "cgl_step_host", "cgl_linear_flow",
+                 "cgl_rel_error", "cgl_strerror"]:
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in nat.header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror(lib):
+    assert lib.cgl_strerror(0) == b"ok"
+    assert lib.cgl_strerror(nat.CGL_EINVAL) == b"invalid argument"
+    assert lib.cgl_strerror(nat.CGL_ENONFINITE) == b"non-finite value produced"
+    assert lib.cgl_strerror(12345) == b"unknown status"
+
+
+def create(**kw):
+    base = dict(d=2, n=[8, 8], bc=[0, 0], lo=[-1.0, -1.0], hi=[1.0, 1.0], a1=1.0, b1=0.5, a2=1.0, a3=-1.0,
+                b3=1.2, a4=0.0, b4=0.0, tau=0.01, scheme=nat.CGL_STRANG, precision=nat.CGL_F64)
+    base.update(kw)
+    return nat.cgl_plan_create(base["d"], base["n"], base["bc"], base["lo"], base["hi"], base["a1"], base["b1"],
+                               base["a2"], base["a3"], base["b3"], base["a4"], base["b4"], base["tau"],
+                               base["scheme"], base["precision"], stream=0)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(d=0, n=[], bc=[], lo=[], hi=[]), nat.CGL_EINVAL),
+    (dict(d=4, n=[2] * 4, bc=[0] * 4, lo=[0.0] * 4, hi=[1.0] * 4), nat.CGL_EINVAL),
+    (dict(n=[1, 8]), nat.CGL_EINVAL),
+    (dict(a1=0.0), nat.CGL_EINVAL),
+    (dict(a1=-1.0), nat.CGL_EINVAL),
+    (dict(tau=0.0), nat.CGL_EINVAL),
+    (dict(tau=float("nan")), nat.CGL_EINVAL),
+    (dict(b3=float("inf")), nat.CGL_EINVAL),
+    (dict(lo=[1.0, -1.0]), nat.CGL_EINVAL),
+    (dict(bc=[0, 7]), nat.CGL_EINVAL),
+    (dict(scheme=99), nat.CGL_EINVAL),
+    (dict(precision=7), nat.CGL_EINVAL),
+    (dict(bc=[2, 0]), nat.CGL_EUNSUPPORTED),
+    (dict(bc=[2, 2], n=[8, 12]), nat.CGL_EUNSUPPORTED),
+    (dict(bc=[2, 2], n=[8, 4096]), nat.CGL_EUNSUPPORTED),
+    (dict(n=[8, 2048]), nat.CGL_EUNSUPPORTED),
+    (dict(scheme=nat.CGL_RK4), nat.CGL_EUNSUPPORTED),
+])
+def test_invalid_arguments_are_rejected_before_any_cuda_call(lib, kw, status):
+    st, h = create(**kw)
+    assert st == status
+    assert not h.value
+    assert lib.cgl_last_error() != b""
+
+
+def test_null_arguments(lib):
+    assert lib.cgl_plan_create(None, 2, None, None, None, None, 1, 0, 1, -1, 1, 0, 0, 0.1, 0, 0, None) \
+        == nat.CGL_EINVAL
+    assert lib.cgl_step(None, None, 1, None) == nat.CGL_EINVAL
+    assert lib.cgl_step_host(None, None, 1, None) == nat.CGL_EINVAL
+    assert lib.cgl_plan_destroy(None) == nat.CGL_OK
+    assert lib.cgl_rel_error(None, None, 4, 0, None, None) == nat.CGL_EINVAL
+    assert lib.cgl_plan_info(None, None, None, None) == nat.CGL_EINVAL

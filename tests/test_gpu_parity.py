@@ -1,0 +1,238 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (relative L2 over the whole field, also reported as rel. inf):
+  * FP64: 1e-11, the bound the workload statement sets for the FP64 path;
+    short runs land near 1e-14.
+  * FP32 (complex64 state, FP32 arithmetic): 2e-5 for the few-step cases
+    here: the FP32 unit roundoff is 6e-8 and each step applies O(10) rounded
+    operations per value plus a length-n sum per mode, so a handful of steps
+    stays below 1e-5 unless the dynamics amplify errors.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cgl_oracle as O
+from paper_2403_02816_gb300 import inputs as I
+from paper_2403_02816_gb300 import native as nat
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-11, "f32": 2e-5}
+DT = {"f64": torch.complex128, "f32": torch.complex64}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2403_02816_gb300 import build as B
+    B.build()
+    nat.load()
+    assert torch.cuda.is_available()
+
+
+def oprob(p):
+    return O.OracleProblem(p.n, p.bc, p.lo, p.hi, p.a1, p.b1, p.a2, p.a3, p.b3, p.a4, p.b4)
+
+
+def run_gpu(p, U0, tau, nsteps, scheme, prec="f64"):
+    with nat.Plan(p, tau, scheme, prec) as plan:
+        u = nat.to_device(U0, DT[prec])
+        plan.step(u, nsteps)
+        torch.cuda.synchronize()
+        assert plan.device_status() == nat.CGL_OK
+        return nat.from_device(u)
+
+
+def check(got, ref, prec, label=""):
+    e2 = O.rel_l2(got, ref)
+    einf = O.rel_inf(got, ref)
+    assert np.all(np.isfinite(got)), label
+    assert e2 <= TOL[prec], "%s rel L2 %.3e rel inf %.3e" % (label, e2, einf)
+    return e2
+
+
+def rand_problem(seed, n, bc, cubic=True, lo=-10.0, hi=10.0):
+    rng = np.random.default_rng(seed)
+    return I.random_problem(rng, n, bc, cubic=cubic, lo=lo, hi=hi), rng
+
+
+def smooth_data(p, rng, amp=0.5):
+    X = I.mesh(p)
+    r2 = sum(x * x for x in X)
+    L2 = max((h - l) for l, h in zip(p.lo, p.hi)) ** 2
+    return amp * (rng.standard_normal(p.n) + 1j * rng.standard_normal(p.n)) * np.exp(-8 * r2 / L2)
+
+
+# ------------------------------------------------------------ factors
+
+@pytest.mark.parametrize("n,bc", [((64, 64), (0, 0)), ((33, 17), (0, 1)), ((5, 256, 3), (1, 1, 0)),
+                                  ((2, 7), (1, 0))])
+def test_fd_factors_match_oracle_expm(n, bc):
+    p, _ = rand_problem(1, n, bc)
+    L = O.LinearOperator(oprob(p), 0.01)
+    for scheme, cs in [("split4", (1.0, 0.5)), ("lawson4", (0.5,))]:
+        with nat.Plan(p, 0.01, scheme) as plan:
+            for c in cs:
+                for mu in range(p.d):
+                    ref = L.factors(c)[mu]
+                    got = plan.factor(c, mu)
+                    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-13, (c, mu)
+
+
+def test_periodic_symbols_match_oracle():
+    p, _ = rand_problem(2, (16, 64, 8), (2, 2, 2))
+    L = O.LinearOperator(oprob(p), 0.02)
+    with nat.Plan(p, 0.02, "split4") as plan:
+        for c in (1.0, 0.5):
+            for mu in range(3):
+                # the library folds the inverse FFT's 1/n_mu into each factor
+                ref = L.factors(c)[mu] / p.n[mu]
+                np.testing.assert_allclose(plan.factor(c, mu), ref, rtol=1e-14, atol=1e-17)
+
+
+# ------------------------------------------------------------ linear flows
+
+@pytest.mark.parametrize("n,bc", [
+    ((64, 64), (0, 0)), ((33, 17), (0, 1)), ((7,), (1,)), ((2, 2), (0, 1)), ((48, 65, 3), (0, 1, 0)),
+    ((5, 6, 7), (1, 1, 1)), ((129, 20), (1, 0)), ((300, 4), (0, 0)),
+    ((8, 8), (2, 2)), ((2,), (2,)), ((1024,), (2,)), ((16, 32), (2, 2)), ((4, 2, 8), (2, 2, 2)),
+    ((64, 128), (2, 2)), ((2048, 4), (2, 2)), ((8, 4, 256), (2, 2, 2)),
+])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_linear_flow(n, bc, prec):
+    """exp(c tau K) u: Tucker operator (FD) or FFT-symbol-iFFT (periodic)."""
+    p, rng = rand_problem(3, n, bc)
+    tau = 0.013
+    U = rng.standard_normal(p.n) + 1j * rng.standard_normal(p.n)
+    L = O.LinearOperator(oprob(p), tau)
+    with nat.Plan(p, tau, "split4", prec) as plan:
+        for c in (1.0, 0.5):
+            u = nat.to_device(U, DT[prec])
+            plan.linear_flow(u, c)
+            check(nat.from_device(u), L.expK(U, c), prec, "c=%g" % c)
+
+
+# ------------------------------------------------------------ schemes
+
+SCHEME_CASES = [
+    # (n, bc, schemes)
+    ((24, 40), (0, 1), ("strang", "split4", "lawson4", "lawson2")),
+    ((9, 6, 11), (1, 0, 1), ("strang", "split4", "lawson4", "lawson2")),
+    ((37,), (0,), ("strang", "split4", "lawson4", "lawson2")),
+    ((32, 16), (2, 2), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2")),
+    ((8, 16, 4), (2, 2, 2), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2")),
+    ((64,), (2,), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2")),
+]
+
+
+@pytest.mark.parametrize("n,bc,schemes", SCHEME_CASES)
+@pytest.mark.parametrize("cubic", [True, False])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_schemes_match_oracle(n, bc, schemes, cubic, prec):
+    p, rng = rand_problem(4, n, bc, cubic=cubic)
+    U0 = smooth_data(p, rng, amp=0.8)
+    tau, nsteps = 0.004, 5
+    for s in schemes:
+        ref = O.integrate(oprob(p), U0, tau, nsteps, s)
+        got = run_gpu(p, U0, tau, nsteps, s, prec)
+        check(got, ref, prec, "%s cubic=%s" % (s, cubic))
+
+
+def test_plane_wave_orders_on_gpu():
+    """The GPU path reproduces the temporal orders on an exact plane wave."""
+    k = (1, -2)
+    a, a1, b1, a3, b3, a4, b4 = 0.8, 0.6, 0.9, -0.8, 1.1, -0.3, 0.4
+    k2 = sum(v * v for v in k)
+    a2 = a1 * k2 - a3 * a * a - a4 * a ** 4
+    w = b1 * k2 - b3 * a * a - b4 * a ** 4
+    p = I.Problem((8, 8), (2, 2), (-np.pi,) * 2, (np.pi,) * 2, a1, b1, a2, a3, b3, a4, b4)
+    U0 = I.plane_wave_data(p, k, a)
+    for s, order in [("strang", 2), ("split4", 4), ("lawson4", 4), ("rk4", 4), ("lawson2", 2), ("rk2", 2)]:
+        errs = [O.rel_l2(run_gpu(p, U0, 1.0 / m, m, s), U0 * np.exp(-1j * w)) for m in (40, 80)]
+        assert abs(O.observed_order(40, errs[0], 80, errs[1]) - order) < 0.1, (s, errs)
+
+
+# ------------------------------------------------------------ workloads
+
+def test_workload_2d_dirichlet_full_run():
+    """2D cubic Dirichlet 64x64, complex128, tau = 0.01, 200 steps of Strang
+    and of Lawson4 against the oracle: the FP64 parity workload."""
+    w = I.workload_2d_dirichlet()
+    U0 = I.u0_2d_dirichlet(w)
+    for s in w.schemes:
+        ref = O.integrate(oprob(w.prob), U0, w.tau, w.nsteps, s)
+        got = run_gpu(w.prob, U0, w.tau, w.nsteps, s)
+        check(got, ref, "f64", s)
+
+
+@pytest.mark.parametrize("scheme", ["split4", "strang", "rk4"])
+def test_workload_3d_periodic_full_size(scheme):
+    """3D cubic-quintic periodic 128^3, complex128, tau = 0.005, in the launch
+    configuration the benchmark times; the oracle runs 2 steps at full size."""
+    w = I.workload_3d_periodic()
+    U0 = I.u0_3d_periodic(w)
+    ref = O.integrate(oprob(w.prob), U0, w.tau, 2, scheme)
+    got = run_gpu(w.prob, U0, w.tau, 2, scheme)
+    check(got, ref, "f64", scheme)
+
+
+def test_workload_3d_periodic_longer_run_small_grid():
+    """Same equation and parameters on 32^3 over 100 steps of every scheme."""
+    w = I.workload_3d_periodic(32)
+    U0 = I.u0_3d_periodic(w)
+    for s in ("split4", "strang", "rk4"):
+        ref = O.integrate(oprob(w.prob), U0, w.tau, 100, s)
+        got = run_gpu(w.prob, U0, w.tau, 100, s)
+        check(got, ref, "f64", s)
+
+
+# ------------------------------------------------------------ API behaviour
+
+def test_step_host_matches_device_step():
+    w = I.workload_2d_dirichlet(32)
+    U0 = I.u0_2d_dirichlet(w)
+    with nat.Plan(w.prob, w.tau, "lawson4") as plan:
+        u = nat.to_device(U0, torch.complex128)
+        plan.step(u, 7)
+        h = torch.from_numpy(np.ascontiguousarray(U0.T)).pin_memory()
+        plan.step_host(h, 7)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(h.numpy(), u.cpu().numpy())
+
+
+def test_graph_follows_new_field_pointer_and_zero_steps():
+    w = I.workload_2d_dirichlet(16)
+    U0 = I.u0_2d_dirichlet(w)
+    with nat.Plan(w.prob, w.tau, "strang") as plan:
+        a = nat.to_device(U0, torch.complex128)
+        b = nat.to_device(U0, torch.complex128)
+        plan.step(a, 3)
+        plan.step(b, 0)
+        np.testing.assert_array_equal(nat.from_device(b), U0)
+        plan.step(b, 3)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(nat.from_device(a), nat.from_device(b))
+
+
+def test_nonfinite_status_is_reported():
+    p = I.Problem((16, 16), (2, 2), (-1.0, -1.0), (1.0, 1.0), 1.0, 0.5, 1.0, -1.0, 1.2, -0.1, 0.1)
+    U0 = np.full(p.n, 1e90 + 0j)
+    with nat.Plan(p, 0.01, "strang") as plan:
+        u = nat.to_device(U0, torch.complex128)
+        plan.step(u, 1)
+        assert plan.device_status() == nat.CGL_ENONFINITE
+        assert plan.device_status() == nat.CGL_OK  # cleared by the read
+
+
+def test_rel_error_kernel():
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(1000) + 1j * rng.standard_normal(1000)
+    y = x + 1e-3 * (rng.standard_normal(1000) + 1j * rng.standard_normal(1000))
+    tx, ty = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    e2, einf, nf = nat.cgl_rel_error(tx, ty, nat.CGL_F64)
+    assert e2 == pytest.approx(O.rel_l2(x, y), rel=1e-12)
+    assert einf == pytest.approx(O.rel_inf(x, y), rel=1e-12)
+    assert nf == 0
+    x[3] = np.nan
+    e2, einf, nf = nat.cgl_rel_error(torch.from_numpy(x).cuda(), ty, nat.CGL_F64)
+    assert nf == 1
