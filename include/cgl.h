@@ -173,6 +173,37 @@ int cgl_profile_step(cgl_plan* plan, void* u, int64_t nsteps, void* stream,
 int cgl_rel_error(const void* x, const void* y, int64_t count, int precision,
                   double* out, void* stream);
 
+/*
+ * Allocation-free variant of cgl_rel_error (the paper has no counterpart:
+ * this entry point exists for callers of the library, not for the method).
+ *
+ * Who needs it: callers that must not allocate device memory at the point
+ * where they check an error norm -- code whose device memory is entirely
+ * owned by another allocator (a framework's caching allocator or a fixed
+ * memory budget handed out at start-up), and monitoring loops that cannot
+ * afford the device-wide synchronisation cudaFree implies.  cgl_rel_error
+ * allocates its scratch on every call; this variant calls no cudaMalloc,
+ * cudaMallocAsync, cudaFree or allocating library routine.
+ *
+ * Scratch: a file-scope static __device__ array of 164 KiB (per-block
+ * partial sums) that every GPU loading the library holds until the process
+ * exits.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents; every slot a call reads is written by that same
+ * call first, so nothing needs clearing.  Calls that overlap on the GPU
+ * (concurrent streams, or threads sharing a device) race on the array:
+ * serialise them.
+ *
+ * Arguments and results are those of cgl_rel_error.  count must satisfy
+ * 1 <= count <= CGL_REL_ERROR_NOALLOC_MAX_COUNT (2^28 complex values, e.g.
+ * a 512^3 field is 2^27); larger counts return CGL_EINVAL before any work is
+ * enqueued.  Synchronous on `stream`.  Errors: EINVAL, ECUDA.
+ */
+#define CGL_REL_ERROR_NOALLOC_MAX_COUNT 268435456LL
+int cgl_rel_error_noalloc(const void* x, const void* y, int64_t count, int precision,
+                          double* out, void* stream);
+
 /* Message for a status code (static string). */
 const char* cgl_strerror(int status);
 

@@ -103,3 +103,117 @@ cudaError_t rel_error_device(const void* x, const void* y, int64_t count, int pr
 }
 
 }  // namespace cgl
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the error norms (cgl_rel_error_noalloc).
+//
+// Same arithmetic as rel_error_device, but its per-block partial sums live in
+// the file-scope device array below instead of a cudaMallocAsync buffer, so a
+// call performs no device allocation of any kind.  Each block of the variant
+// reduces one fixed chunk of kStaticChunk values, so the array's capacity
+// (kStaticMaxBlocks partial records) bounds the accepted count at
+// kStaticMaxBlocks * kStaticChunk values; larger counts are rejected.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace cgl {
+
+constexpr int kStaticChunk = 65536;     // values reduced by one block
+constexpr int kStaticMaxBlocks = 4096;  // partial records the array holds
+static_assert((int64_t)kStaticChunk * kStaticMaxBlocks == CGL_REL_ERROR_NOALLOC_MAX_COUNT,
+              "header limit must match the scratch capacity");
+
+// Scratch shared by every call on a device: kNormFields partials per block,
+// then 3 result slots.  164 KiB, resident on each GPU that loads the library
+// until the process exits.
+static __device__ __align__(256) double g_norm_scratch[kNormFields * kStaticMaxBlocks + 3];
+
+template <class T2>
+__global__ void __launch_bounds__(kNormThreads) rel_error_partial_chunked(const T2* __restrict__ x,
+                                                                          const T2* __restrict__ y,
+                                                                          int64_t count, double* partial) {
+  double sd = 0, sy = 0, md = 0, my = 0, nf = 0;
+  const int64_t beg = (int64_t)blockIdx.x * kStaticChunk;
+  const int64_t end = min(count, beg + kStaticChunk);
+  for (int64_t i = beg + threadIdx.x; i < end; i += kNormThreads) {
+    const T2 a = x[i], b = y[i];
+    const double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y;
+    const double d2 = dx * dx + dy * dy;
+    const double y2 = (double)b.x * (double)b.x + (double)b.y * (double)b.y;
+    if (!(isfinite((double)a.x) && isfinite((double)a.y))) { nf += 1; continue; }
+    sd += d2;
+    sy += y2;
+    md = fmax(md, d2);
+    my = fmax(my, y2);
+  }
+  __shared__ double red[kNormFields][kNormThreads / 32];
+  double v[kNormFields] = {sd, sy, md, my, nf};
+#pragma unroll
+  for (int f = 0; f < kNormFields; ++f) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, v[f], o);
+      v[f] = (f == 2 || f == 3) ? fmax(v[f], w) : v[f] + w;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int f = 0; f < kNormFields; ++f) red[f][warp] = v[f];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r[kNormFields] = {0, 0, 0, 0, 0};
+    for (int w = 0; w < kNormThreads / 32; ++w)
+      for (int f = 0; f < kNormFields; ++f)
+        r[f] = (f == 2 || f == 3) ? fmax(r[f], red[f][w]) : r[f] + red[f][w];
+    for (int f = 0; f < kNormFields; ++f) partial[f * gridDim.x + blockIdx.x] = r[f];
+  }
+}
+
+// Device address of g_norm_scratch, looked up once per device with that
+// device current.  In host code the array's name is only a host-side shadow,
+// never a device pointer, so kernels get the address found here.
+static std::mutex g_scratch_mutex;
+static double* g_scratch_ptr[64] = {nullptr};
+
+static cudaError_t static_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_norm_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace cgl
+
+extern "C" int cgl_rel_error_noalloc(const void* x, const void* y, int64_t count, int precision, double* out,
+                                     void* stream) {
+  using namespace cgl;
+  if (!x || !y || !out || count <= 0 || count > CGL_REL_ERROR_NOALLOC_MAX_COUNT) return CGL_EINVAL;
+  if (precision != CGL_F64 && precision != CGL_F32) return CGL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* partial = nullptr;
+  if (static_scratch(&partial) != cudaSuccess) return CGL_ECUDA;
+  const int nblocks = (int)((count + kStaticChunk - 1) / kStaticChunk);
+  double* result = partial + kNormFields * nblocks;
+  if (precision == CGL_F64)
+    rel_error_partial_chunked<double2><<<nblocks, kNormThreads, 0, s>>>((const double2*)x, (const double2*)y,
+                                                                        count, partial);
+  else
+    rel_error_partial_chunked<float2><<<nblocks, kNormThreads, 0, s>>>((const float2*)x, (const float2*)y,
+                                                                       count, partial);
+  if (cudaGetLastError() != cudaSuccess) return CGL_ECUDA;
+  rel_error_final<<<1, kNormThreads, 0, s>>>(partial, nblocks, result);
+  if (cudaGetLastError() != cudaSuccess) return CGL_ECUDA;
+  if (cudaMemcpyAsync(out, result, 3 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CGL_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CGL_ECUDA;
+  return CGL_OK;
+}

@@ -67,6 +67,7 @@ def load() -> ctypes.CDLL:
         "cgl_last_device_status": (I, [P, VP]),
         "cgl_profile_step": (I, [P, VP, I64, VP, ctypes.POINTER(cgl_kernel_time), I, ctypes.POINTER(I)]),
         "cgl_rel_error": (I, [VP, VP, I64, I, ctypes.POINTER(D), VP]),
+        "cgl_rel_error_noalloc": (I, [VP, VP, I64, I, ctypes.POINTER(D), VP]),
         "cgl_strerror": (ctypes.c_char_p, [I]),
         "cgl_last_error": (ctypes.c_char_p, []),
     }
