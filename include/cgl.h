@@ -56,8 +56,15 @@ enum cgl_scheme {
 };
 
 /* Arithmetic of the state and of the time-stepping kernels.  The factors
- * exp(c tau A_mu) are always computed in FP64 and rounded once. */
-enum cgl_precision { CGL_F64 = 0, CGL_F32 = 1 };
+ * exp(c tau A_mu) are always computed in FP64 and rounded once.
+ *   CGL_F64    complex128 state, FP64 kernels.
+ *   CGL_F32    complex64 state, FP32 kernels.
+ *   CGL_BF16X3 complex64 state; the mu-mode products run on the tensor cores
+ *              with each operand split into three BF16 parts and FP32
+ *              accumulation (about FP32 accuracy); pointwise work in FP32.
+ *              Finite differences only, every n_mu a multiple of 16 and
+ *              <= 256, and n_1 a multiple of 128 when d >= 2. */
+enum cgl_precision { CGL_F64 = 0, CGL_F32 = 1, CGL_BF16X3 = 2 };
 
 enum cgl_status {
     CGL_OK = 0,
@@ -145,6 +152,7 @@ int cgl_plan_info(const cgl_plan* plan, size_t* field_bytes, size_t* workspace_b
  * non-finite value.
  */
 int cgl_last_device_status(cgl_plan* plan, void* stream);
+/* (A bounded device-side wait that gave up is reported as CGL_ETIMEOUT.) */
 
 /*
  * Per-kernel timing (CUDA events around every launch) of nsteps steps run

@@ -82,6 +82,14 @@ struct cgl_plan {
 
   std::vector<Sweep> sweeps;
 
+  // BF16x3 tensor-core path: per-rhs BF16x3 state planes and FP32 output
+  // planes, per-(factor, mode) BF16x3 factor splits, and their TMA maps.
+  void* splits[2] = {nullptr, nullptr};
+  void* planes[2] = {nullptr, nullptr};
+  void* fsplit[2][3] = {{nullptr}};
+  alignas(64) unsigned char tmA[3][2][kTensorMapBytes];
+  alignas(64) unsigned char tmB[2][3][kTensorMapBytes];
+
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   void* graph_u = nullptr;
@@ -180,6 +188,48 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
   const double es = (double)p->elem;
   const bool f64 = p->precision == CGL_F64;
 
+  if (p->precision == CGL_BF16X3) {
+    // split prologue -> d tensor-core mode passes -> plane epilogue
+    {
+      Timer tm(p, s);
+      cudaError_t e = launch_split_prologue(f.in[0], f.in[1], sw.nin, sw.op, p->splits[0], p->splits[1], sw.nrhs,
+                                            p->N, s);
+      if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("split prologue: ") + cudaGetErrorString(e));
+      tm.done("split_prologue", pro_flops(p, sw.op) * Nd, (sw.nin * 8.0 + sw.nrhs * 12.0) * Nd);
+    }
+    for (int mu = 0; mu < p->d; ++mu) {
+      MmaLaunch L{};
+      L.n = (int)p->n[mu];
+      L.P = axis_P(p, mu);
+      L.Q = p->N / (L.P * p->n[mu]);
+      L.N = p->N;
+      L.nrhs = sw.nrhs;
+      for (int r = 0; r < 2; ++r) {
+        const int rr = r < sw.nrhs ? r : 0;
+        L.tmA[r] = p->tmA[mu][rr];
+        L.tmB[r] = p->tmB[sw.fac[rr]][mu];
+        L.out[r] = (mu == p->d - 1) ? p->planes[rr] : p->splits[rr];
+      }
+      L.out_fp32 = mu == p->d - 1;
+      L.status = p->status;
+      Timer tm(p, s);
+      cudaError_t e = launch_mma_pass(L, s);
+      if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("tensor-core mode pass: ") + cudaGetErrorString(e));
+      // issued tensor flops: 6 split products of a (2n x 2n) real GEMM per fiber
+      tm.done("mma_mode_bf16x3", 6.0 * 8.0 * (double)p->n[mu] * Nd * sw.nrhs,
+              (12.0 + (L.out_fp32 ? 8.0 : 12.0)) * Nd * sw.nrhs);
+    }
+    {
+      Timer tm(p, s);
+      void* ex[3] = {f.extra[0], f.extra[1], f.extra[2]};
+      cudaError_t e = launch_plane_epilogue(p->planes[0], p->planes[1], sw.nrhs, ex, sw.nextra, sw.op, f.out[0],
+                                            f.out[1], sw.nout, p->N, p->status, s);
+      if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("plane epilogue: ") + cudaGetErrorString(e));
+      tm.done("plane_epilogue", epi_flops(p, sw.op) * Nd, (sw.nrhs * 8.0 + (sw.nextra + sw.nout) * 8.0) * Nd);
+    }
+    return CGL_OK;
+  }
+
   if (!p->periodic) {
     for (int mu = 0; mu < p->d; ++mu) {
       ModePassArgs a{};
@@ -254,7 +304,8 @@ int enqueue_step(cgl_plan* p, void* u, cudaStream_t s) {
 }
 
 int launches_per_step(const cgl_plan* p) {
-  const int per = p->periodic ? 2 * p->d - 1 : p->d;
+  int per = p->periodic ? 2 * p->d - 1 : p->d;
+  if (p->precision == CGL_BF16X3) per = p->d + 2;  // split prologue + d mode passes + plane epilogue
   return (int)p->sweeps.size() * per;
 }
 
@@ -335,6 +386,8 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
         if (same >= 0) {
           p->fac64[c][mu] = p->fac64[c][same];
           p->fac[c][mu] = p->fac[c][same];
+          p->fsplit[c][mu] = p->fsplit[c][same];
+          std::memcpy(p->tmB[c][mu], p->tmB[c][same], kTensorMapBytes);
           continue;
         }
         const int n = (int)p->n[mu];
@@ -343,6 +396,11 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
         if ((st = dev_alloc(p, (void**)&p->fac64[c][mu], (size_t)n * n * sizeof(double2)))) return st;
         CUDA_TRY(expm_device(dA, p->cval[c] * p->tau, n, p->fac64[c][mu], dW, norm1(A, n), s));
         if ((st = make_working(p, p->fac64[c][mu], (int64_t)n * n, &p->fac[c][mu], s))) return st;
+        if (p->precision == CGL_BF16X3) {
+          if ((st = dev_alloc(p, &p->fsplit[c][mu], 3 * 4 * (size_t)n * n * 2))) return st;
+          CUDA_TRY(launch_factor_split(p->fac64[c][mu], n, p->fsplit[c][mu], s));
+          CUDA_TRY(make_factor_tmap(p->tmB[c][mu], p->fsplit[c][mu], n));
+        }
         // the host copy of A must stay alive until the upload has completed
         CUDA_TRY(cudaStreamSynchronize(s));
       }
@@ -466,6 +524,7 @@ cudaError_t prepare_kernels(int dev) {
   if ((e = prepare_fft_pass<float>()) != cudaSuccess) return e;
   if ((e = prepare_mode_pass<double>()) != cudaSuccess) return e;
   if ((e = prepare_mode_pass<float>()) != cudaSuccess) return e;
+  if ((e = prepare_mma_pass()) != cudaSuccess) return e;
   if (dev >= 0 && dev < 64) done[dev] = true;
   return cudaSuccess;
 }
@@ -534,7 +593,8 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, cons
   if (!(a1 > 0)) return fail(CGL_EINVAL, "alpha1 must be positive");
   if (!(tau > 0)) return fail(CGL_EINVAL, "tau must be positive");
   if (scheme < CGL_STRANG || scheme > CGL_RK2) return fail(CGL_EINVAL, "unknown scheme");
-  if (precision != CGL_F64 && precision != CGL_F32) return fail(CGL_EINVAL, "unknown precision");
+  if (precision != CGL_F64 && precision != CGL_F32 && precision != CGL_BF16X3)
+    return fail(CGL_EINVAL, "unknown precision");
   int nper = 0;
   for (int m = 0; m < d; ++m) {
     if (bc[m] < CGL_BC_DIRICHLET || bc[m] > CGL_BC_PERIODIC) return fail(CGL_EINVAL, "unknown boundary condition");
@@ -553,6 +613,13 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, cons
   }
   if (!periodic && (scheme == CGL_RK4 || scheme == CGL_RK2))
     return fail(CGL_EUNSUPPORTED, "Runge-Kutta schemes need periodic directions");
+  if (precision == CGL_BF16X3) {
+    if (periodic) return fail(CGL_EUNSUPPORTED, "BF16x3 applies to the finite-difference mode products only");
+    for (int m = 0; m < d; ++m)
+      if (n[m] % 16 != 0 || n[m] > 256)
+        return fail(CGL_EUNSUPPORTED, "BF16x3 needs every n_mu a multiple of 16 and <= 256");
+    if (d >= 2 && n[0] % 128 != 0) return fail(CGL_EUNSUPPORTED, "BF16x3 needs n_1 a multiple of 128 when d >= 2");
+  }
 
   cgl_plan* p = new cgl_plan();
   cudaGetDevice(&p->dev);
@@ -571,7 +638,7 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, cons
   p->precision = precision;
   p->periodic = periodic;
   p->cubic = (a4 == 0.0 && b4 == 0.0);
-  p->elem = precision == CGL_F64 ? sizeof(double2) : sizeof(float2);
+  p->elem = precision == CGL_F64 ? sizeof(double2) : sizeof(float2);  // F32 and BF16x3: complex64
   switch (scheme) {
     case CGL_STRANG:
     case CGL_LAWSON2: p->nfac = 1; p->cval[0] = 1.0; break;
@@ -597,6 +664,18 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, cons
   if (!st) st = dev_alloc(p, (void**)&p->status, sizeof(int));
   if (!st && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) st = fail(CGL_ECUDA, "memset status");
   for (int w = 0; !st && w < p->nwork; ++w) st = dev_alloc(p, &p->work[w], p->N * p->elem);
+  if (!st && precision == CGL_BF16X3) {
+    const int nr = scheme == CGL_STRANG ? 1 : 2;
+    for (int r = 0; !st && r < nr; ++r) {
+      st = dev_alloc(p, &p->splits[r], 12 * (size_t)p->N);
+      if (!st) st = dev_alloc(p, &p->planes[r], 8 * (size_t)p->N);
+      for (int mu = 0; !st && mu < d; ++mu) {
+        const int64_t P = axis_P(p, mu), Q = p->N / (P * p->n[mu]);
+        e = make_state_tmap(p->tmA[mu][r], p->splits[r], (int)p->n[mu], P, Q, p->N);
+        if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("tensor map: ") + cudaGetErrorString(e));
+      }
+    }
+  }
   if (!st) st = build_factors(p, s);
   if (!st) {
     e = cudaStreamSynchronize(s);
@@ -690,6 +769,7 @@ int cgl_last_device_status(cgl_plan* p, void* stream) {
   CUDA_TRY(cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (h & 2) return fail(CGL_ETIMEOUT, "a device-side wait timed out");
   return (h & 1) ? CGL_ENONFINITE : CGL_OK;
 }
 
@@ -725,6 +805,7 @@ int cgl_profile_step(cgl_plan* p, void* u, int64_t nsteps, void* stream, cgl_ker
 int cgl_rel_error(const void* x, const void* y, int64_t count, int precision, double* out, void* stream) {
   if (!x || !y || !out) return fail(CGL_EINVAL, "NULL argument");
   if (count <= 0) return fail(CGL_EINVAL, "count must be positive");
+  if (precision == CGL_BF16X3) precision = CGL_F32;  // complex64 state
   if (precision != CGL_F64 && precision != CGL_F32) return fail(CGL_EINVAL, "unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
   const int nb = rel_error_blocks(count);

@@ -293,6 +293,29 @@ cudaError_t periodic_symbol_device(double2* dOut, int n, double L, double ctau, 
 cudaError_t twiddle_device(double2* dOut, int n, cudaStream_t s);
 cudaError_t convert_f64_to_f32(const double2* src, float2* dst, int64_t count, cudaStream_t s);
 
+// mma_mode.cu: BF16x3 mu-mode product on tcgen05 (complex64 state).
+struct MmaLaunch {
+  int n;              // mode length
+  int64_t P, Q, N;    // faster / slower products, field size
+  int nrhs;
+  const void* tmA[kMaxRhs];  // CUtensorMap (128 bytes) of each rhs's BF16x3 planes
+  const void* tmB[kMaxRhs];  // CUtensorMap of each rhs's factor splits
+  int out_fp32;       // 1: FP32 planes, 0: BF16x3 planes
+  void* out[kMaxRhs];
+  int* status;
+};
+constexpr size_t kTensorMapBytes = 128;
+cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N);
+cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n);
+cudaError_t prepare_mma_pass();
+cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s);
+cudaError_t launch_split_prologue(const void* in0, const void* in1, int nin, const OpArgs& op, void* s0, void* s1,
+                                  int nrhs, int64_t N, cudaStream_t s);
+cudaError_t launch_plane_epilogue(const void* y0, const void* y1, int nrhs, void* const* extra, int nextra,
+                                  const OpArgs& op, void* o0, void* o1, int nout, int64_t N, int* status,
+                                  cudaStream_t s);
+cudaError_t launch_factor_split(const double2* F, int n, void* out, cudaStream_t s);
+
 // norms.cu
 cudaError_t rel_error_device(const void* x, const void* y, int64_t count, int precision,
                              double* d_partial, int nblocks, double* h_out, cudaStream_t s);

@@ -1,0 +1,527 @@
+// mu-mode product (Sec. 3.1, eq. Tucker) on the 5th-generation tensor cores:
+// BF16x3 split operands, FP32 accumulation in tensor memory.
+//
+// Complex contraction as a real GEMM.  For mode mu with fibers m (the other
+// coordinates) the product v = F u over each fiber is
+//   C[m, (c', i)] = sum_{(c, j)} A[m, (c, j)] B[(c, j), (c', i)],
+// c, c' in {re, im}, A[m, (c, j)] = component c of u at position j of fiber m,
+// B the real form of F: [[Fr, -Fi], [Fi, Fr]] laid out as N rows (c', i) of K
+// = 2n contiguous values.  The state is held as three BF16 planes per
+// component (x = h + m + l, h = bf16(x), m = bf16(x - h), l = bf16(x - h - m)),
+// the factor likewise (split once from FP64), and six products
+// (lh, hl, mm, mh, hm, hh; small terms first) accumulate in one FP32 TMEM
+// accumulator: about 24 significant bits, i.e. FP32 accuracy.
+//
+// Kernel shape: one CTA per tile of 128 fibers (TMEM lanes) x all 2n outputs
+// (TMEM columns, n <= 256); K advances 16 per pipeline stage, three stages,
+// filled by TMA (A: K-major for mode 1 whose fibers are contiguous, MN-major
+// for the other modes; B: K-major), consumed by tcgen05.mma issued by one
+// thread, freed by tcgen05.commit.  Every mbarrier wait is bounded: on
+// timeout the kernel sets bit 1 of the status word, skips its stores, waits
+// (bounded) for its own copies, frees its TMEM and returns.
+//
+// Each CTA owns whole fibers, so a pass may write its output over its input.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "cgl_internal.cuh"
+
+namespace cgl {
+
+constexpr int kMmaThreads = 128;
+constexpr int kMmaStages = 3;
+constexpr int kMmaM = 128;
+constexpr int kMmaK = 16;
+constexpr long long kSpinLimit = 1ll << 24;
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after kSpinLimit unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+      "%6}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem], kind::f16 (BF16 inputs, FP32 accumulator).
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on `bar` once every tcgen05 operation this thread issued has completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (16-byte units), the fixed 0b001 at bits 46-48, swizzle mode at
+// bits 61-63 (2 = 128-byte, 6 = 32-byte).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t swizzle) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(swizzle & 7) << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, A major-ness
+// (0 = K-major, 1 = MN-major), B K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(a_mn) << 15) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(m);
+  l = __float2bfloat16_rn(r2);
+}
+
+// ------------------------------------------------------------------ the GEMM pass
+
+struct MmaPassArgs {
+  int n;             // mode length (multiple of 16, <= 256)
+  int64_t P, Q;      // products of the faster / slower sizes
+  int a_mn;          // 1: A is MN-major (P > 1, P % 128 == 0); 0: K-major (mode 1)
+  int out_fp32;      // 1: FP32 planes (re, im); 0: BF16x3 planes (6)
+  void* out[kMaxRhs];
+  int64_t N;         // plane length (field size)
+  int64_t mtiles;    // tiles of 128 fibers
+  int tmem_cols;     // power of two >= 2n
+  int* status;
+};
+
+static __host__ __device__ constexpr uint32_t mma_stage_bytes(int n) {
+  return 3u * (kMmaM * kMmaK * 2u) + 3u * (2u * n * kMmaK * 2u);
+}
+
+__global__ void __launch_bounds__(kMmaThreads, 1)
+    mma_mode_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                    const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
+                    const MmaPassArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int n = a.n;
+  const int rhs = blockIdx.y;
+  const CUtensorMap* tmA = rhs ? &tmA1 : &tmA0;
+  const CUtensorMap* tmB = rhs ? &tmB1 : &tmB0;
+  const int nk = (2 * n) / kMmaK;
+  const uint32_t a_bytes = kMmaM * kMmaK * 2;
+  const uint32_t b_bytes = 2u * n * kMmaK * 2;
+  const uint32_t stage_bytes = mma_stage_bytes(n);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kMmaStages * stage_bytes);
+  uint64_t* empty = full + kMmaStages;
+  uint64_t* accum = empty + kMmaStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5;
+
+  // fiber tile coordinates
+  const int64_t tile = blockIdx.x;
+  int64_t q0 = 0, p0 = 0;
+  if (a.a_mn) {
+    const int64_t per_q = a.P / kMmaM;
+    q0 = tile / per_q;
+    p0 = (tile - q0 * per_q) * kMmaM;
+  } else {
+    q0 = tile * kMmaM;
+  }
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kMmaStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accum), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = idesc_bf16(kMmaM, n, a.a_mn);
+    auto issue_load = [&](int kb, int slot) {
+      uint8_t* st = base + slot * stage_bytes;
+      const uint32_t bar = smem_u32(&full[slot]);
+      mbar_expect_tx(bar, stage_bytes);
+      const int k0 = kb * kMmaK;
+      const int c = k0 / n, j0 = k0 - c * n;
+      for (int s = 0; s < 3; ++s) {
+        const uint32_t dA = smem_u32(st + s * a_bytes);
+        const int plane = s * 2 + c;
+        if (a.a_mn) {
+          tma_load_4d(dA, tmA, bar, (int)p0, j0, (int)q0, plane);
+          tma_load_4d(dA + 2048, tmA, bar, (int)p0 + 64, j0, (int)q0, plane);
+        } else {
+          tma_load_3d(dA, tmA, bar, j0, (int)q0, plane);
+        }
+        const uint32_t dB = smem_u32(st + 3 * a_bytes + s * b_bytes);
+        tma_load_3d(dB, tmB, bar, k0, 0, s);
+        tma_load_3d(dB + n * 32, tmB, bar, k0, n, s);
+      }
+    };
+    // split products, small terms first: (l,h) (h,l) (m,m) (m,h) (h,m) (h,h)
+    const int pa[6] = {2, 0, 1, 1, 0, 0};
+    const int pb[6] = {0, 2, 1, 0, 1, 0};
+    int loaded = 0;  // stages whose TMA has been issued
+    for (; loaded < kMmaStages && loaded < nk; ++loaded) issue_load(loaded, loaded);
+    int consumed = 0;  // stages whose full barrier has been waited
+    int committed = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int slot = kb % kMmaStages;
+      if (!mbar_wait(smem_u32(&full[slot]), (kb / kMmaStages) & 1)) { ok = false; break; }
+      consumed = kb + 1;
+      tc_fence_after();
+      uint8_t* st = base + slot * stage_bytes;
+      for (int pr = 0; pr < 6; ++pr) {
+        const uint32_t aaddr = smem_u32(st + pa[pr] * a_bytes);
+        const uint64_t adesc = a.a_mn ? smem_desc(aaddr, 2048, 1024, 2) : smem_desc(aaddr, 16, 256, 6);
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t baddr = smem_u32(st + 3 * a_bytes + pb[pr] * b_bytes + h * n * 32);
+          mma_bf16(tmem + h * n, adesc, smem_desc(baddr, 16, 256, 6), idesc, (kb > 0 || pr > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(smem_u32(&empty[slot]));
+      committed = kb + 1;
+      // refill the slot consumed one iteration ago with stage kb + 2
+      if (kb >= 1 && loaded < nk) {
+        const int ps = (kb - 1) % kMmaStages;
+        if (!mbar_wait(smem_u32(&empty[ps]), ((kb - 1) / kMmaStages) & 1)) { ok = false; break; }
+        issue_load(loaded, ps);
+        ++loaded;
+      }
+    }
+    if (ok) {
+      mma_commit(smem_u32(accum));
+    } else {
+      // give up: wait (bounded) for this CTA's own copies and MMAs in flight
+      atomicOr(a.status, 2);
+      *abort_flag = 1;
+      for (int kb = consumed; kb < loaded; ++kb)
+        mbar_wait(smem_u32(&full[kb % kMmaStages]), (kb / kMmaStages) & 1);
+      if (committed > 0)
+        mbar_wait(smem_u32(&empty[(committed - 1) % kMmaStages]), ((committed - 1) / kMmaStages) & 1);
+    }
+  }
+  __syncthreads();
+
+  bool good = (*abort_flag == 0);
+  if (good && !mbar_wait(smem_u32(accum), 0)) {
+    good = false;
+    atomicOr(a.status, 2);
+  }
+  // the TMEM loads below are warp-collective: take one CTA-wide decision
+  good = __syncthreads_and(good) != 0;
+  tc_fence_after();
+  if (good) {
+    const int m = threadIdx.x;  // TMEM lane = fiber of the tile
+    bool valid;
+    int64_t obase, ostride;     // output index of (c', i) = obase + ostride * i
+    if (a.a_mn) {
+      valid = true;
+      obase = (p0 + m) + a.P * (int64_t)n * q0;
+      ostride = a.P;
+    } else {
+      const int64_t q = q0 + m;
+      valid = q < a.Q;
+      obase = (int64_t)n * q;
+      ostride = 1;
+    }
+    const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    for (int h = 0; h < 2; ++h) {
+      for (int i0 = 0; i0 < n; i0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(lane_addr + h * n + i0, r);
+        if (!valid) continue;
+        if (a.out_fp32) {
+          float* o = reinterpret_cast<float*>(a.out[rhs]) + (int64_t)h * a.N;
+#pragma unroll
+          for (int t = 0; t < 16; ++t) o[obase + ostride * (i0 + t)] = __uint_as_float(r[t]);
+        } else {
+          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out[rhs]);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            __nv_bfloat16 sh, sm, sl;
+            split3(__uint_as_float(r[t]), sh, sm, sl);
+            const int64_t idx = obase + ostride * (i0 + t);
+            o[(0 * 2 + h) * a.N + idx] = sh;
+            o[(1 * 2 + h) * a.N + idx] = sm;
+            o[(2 * 2 + h) * a.N + idx] = sl;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, a.tmem_cols);
+  }
+}
+
+// ------------------------------------------------------------------ pointwise stages
+
+// Start of a sweep: prologue on complex64 inputs, BF16x3 planes of each rhs.
+__global__ void split_prologue_kernel(const float2* in0, const float2* in1, int nin, OpArgs op,
+                                      __nv_bfloat16* s0, __nv_bfloat16* s1, int nrhs, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 in[2], z[2];
+    in[0] = in0[i];
+    in[1] = nin > 1 ? in1[i] : in[0];
+    apply_prologue<float, float2>(op, in, z);
+    __nv_bfloat16* dst[2] = {s0, s1};
+    for (int r = 0; r < nrhs; ++r) {
+      __nv_bfloat16 h, m, l;
+      split3(z[r].x, h, m, l);
+      dst[r][0 * N + i] = h;
+      dst[r][2 * N + i] = m;
+      dst[r][4 * N + i] = l;
+      split3(z[r].y, h, m, l);
+      dst[r][1 * N + i] = h;
+      dst[r][3 * N + i] = m;
+      dst[r][5 * N + i] = l;
+    }
+  }
+}
+
+// End of a sweep: FP32 planes of each rhs + extras -> epilogue -> complex64.
+__global__ void plane_epilogue_kernel(const float* y0, const float* y1, int nrhs, const float2* e0,
+                                      const float2* e1, const float2* e2, int nextra, OpArgs op, float2* o0,
+                                      float2* o1, int nout, int64_t N, int* status) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 y[2], ex[3], o[2];
+    y[0] = make_float2(y0[i], y0[N + i]);
+    y[1] = nrhs > 1 ? make_float2(y1[i], y1[N + i]) : y[0];
+    if (nextra > 0) ex[0] = e0[i];
+    if (nextra > 1) ex[1] = e1[i];
+    if (nextra > 2) ex[2] = e2[i];
+    const int no = apply_epilogue<float, float2>(op, y, ex, o);
+    if (no > 0 && nout > 0) { o0[i] = o[0]; bad |= !finite2(o[0]); }
+    if (no > 1 && nout > 1) { o1[i] = o[1]; bad |= !finite2(o[1]); }
+  }
+  if (bad && status) atomicOr(status, 1);
+}
+
+// Real form of an FP64 factor F (n x n, column-major), split in three BF16
+// matrices: out[s][row (c', i)][col (c, j)], K = col contiguous.
+__global__ void factor_split_kernel(const double2* F, int n, __nv_bfloat16* out) {
+  const int64_t total = 4ll * n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / (2 * n)), col = (int)(e % (2 * n));
+    const int cp = row / n, i = row % n, c = col / n, j = col % n;
+    const double2 f = F[i + (int64_t)j * n];
+    double v;
+    if (cp == 0) v = (c == 0) ? f.x : -f.y;
+    else v = (c == 0) ? f.y : f.x;
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    const double r1 = v - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(m);
+    const __nv_bfloat16 l = __double2bfloat16(r2);
+    out[e] = h;
+    out[total + e] = m;
+    out[2 * total + e] = l;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// A operand map of one rhs for mode geometry (n, P, Q) over a buffer of six
+// BF16 planes of N values each.
+cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N) {
+  auto enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_out);
+  std::memset(m, 0, sizeof(CUtensorMap));
+  CUresult r;
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (P == 1) {
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)Q, 6};
+    const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)N * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kMmaK, (cuuint32_t)kMmaM, 1};
+    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(splits), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    const cuuint64_t dims[4] = {(cuuint64_t)P, (cuuint64_t)n, (cuuint64_t)Q, 6};
+    const cuuint64_t strides[3] = {(cuuint64_t)P * 2, (cuuint64_t)P * n * 2, (cuuint64_t)N * 2};
+    const cuuint32_t box[4] = {64, (cuuint32_t)kMmaK, 1, 1};
+    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(splits), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// B operand map over three (2n x 2n) BF16 factor splits.
+cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n) {
+  auto enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_out);
+  std::memset(m, 0, sizeof(CUtensorMap));
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * n, (cuuint64_t)2 * n, 3};
+  const cuuint64_t strides[2] = {(cuuint64_t)4 * n, (cuuint64_t)8 * n * n};
+  const cuuint32_t box[3] = {(cuuint32_t)kMmaK, (cuuint32_t)n, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fsplit), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static size_t mma_smem_bytes(int n) { return (size_t)kMmaStages * mma_stage_bytes(n) + 1024 + 256; }
+
+cudaError_t prepare_mma_pass() {
+  return cudaFuncSetAttribute(mma_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mma_smem_bytes(256));
+}
+
+cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
+  MmaPassArgs a{};
+  a.n = L.n;
+  a.P = L.P;
+  a.Q = L.Q;
+  a.a_mn = L.P > 1 ? 1 : 0;
+  a.out_fp32 = L.out_fp32;
+  a.out[0] = L.out[0];
+  a.out[1] = L.out[1];
+  a.N = L.N;
+  a.mtiles = L.P > 1 ? (L.P / kMmaM) * L.Q : (L.Q + kMmaM - 1) / kMmaM;
+  int cols = 32;
+  while (cols < 2 * L.n) cols *= 2;
+  a.tmem_cols = cols;
+  a.status = L.status;
+  const CUtensorMap* A0 = reinterpret_cast<const CUtensorMap*>(L.tmA[0]);
+  const CUtensorMap* A1 = reinterpret_cast<const CUtensorMap*>(L.tmA[L.nrhs > 1 ? 1 : 0]);
+  const CUtensorMap* B0 = reinterpret_cast<const CUtensorMap*>(L.tmB[0]);
+  const CUtensorMap* B1 = reinterpret_cast<const CUtensorMap*>(L.tmB[L.nrhs > 1 ? 1 : 0]);
+  dim3 grid((unsigned)a.mtiles, (unsigned)L.nrhs);
+  mma_mode_kernel<<<grid, kMmaThreads, mma_smem_bytes(L.n), s>>>(*A0, *A1, *B0, *B1, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_prologue(const void* in0, const void* in1, int nin, const OpArgs& op, void* s0, void* s1,
+                                  int nrhs, int64_t N, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
+  split_prologue_kernel<<<blocks, 256, 0, s>>>((const float2*)in0, (const float2*)in1, nin, op,
+                                               (__nv_bfloat16*)s0, (__nv_bfloat16*)s1, nrhs, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_epilogue(const void* y0, const void* y1, int nrhs, void* const* extra, int nextra,
+                                  const OpArgs& op, void* o0, void* o1, int nout, int64_t N, int* status,
+                                  cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
+  plane_epilogue_kernel<<<blocks, 256, 0, s>>>((const float*)y0, (const float*)y1, nrhs, (const float2*)extra[0],
+                                               (const float2*)extra[1], (const float2*)extra[2], nextra, op,
+                                               (float2*)o0, (float2*)o1, nout, N, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_factor_split(const double2* F, int n, void* out, cudaStream_t s) {
+  const int64_t total = 4ll * n * n;
+  factor_split_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(
+      F, n, (__nv_bfloat16*)out);
+  return cudaGetLastError();
+}
+
+}  // namespace cgl

@@ -18,8 +18,8 @@ from paper_2403_02816_gb300 import native as nat
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-11, "f32": 2e-5}
-DT = {"f64": torch.complex128, "f32": torch.complex64}
+TOL = {"f64": 1e-11, "f32": 2e-5, "bf16x3": 2e-5}
+DT = {"f64": torch.complex128, "f32": torch.complex64, "bf16x3": torch.complex64}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -112,6 +112,41 @@ def test_linear_flow(n, bc, prec):
             check(nat.from_device(u), L.expK(U, c), prec, "c=%g" % c)
 
 
+# ------------------------------------------------------------ tensor cores (BF16x3)
+
+# shapes the tcgen05 path takes: n_mu multiple of 16 and <= 256, n_1 a
+# multiple of 128 for d >= 2; several 128-fiber tiles and a ragged last tile
+# of mode-1 fibers (Q not a multiple of 128) included
+MMA_SHAPES = [((16,), (0,)), ((48,), (1,)), ((256,), (0,)), ((128, 16), (0, 1)), ((128, 48), (1, 0)),
+              ((256, 64), (0, 0)), ((128, 32, 16), (1, 0, 1)), ((128, 16, 80), (0, 1, 1)),
+              ((256, 256, 3 * 16), (1, 1, 0))]
+
+
+@pytest.mark.parametrize("n,bc", MMA_SHAPES)
+def test_linear_flow_tensor_cores(n, bc):
+    """Tucker operator with every mode product on tcgen05 (BF16x3, FP32
+    accumulation) against the FP64 oracle."""
+    p, rng = rand_problem(5, n, bc)
+    tau = 0.013
+    U = rng.standard_normal(p.n) + 1j * rng.standard_normal(p.n)
+    L = O.LinearOperator(oprob(p), tau)
+    with nat.Plan(p, tau, "split4", "bf16x3") as plan:
+        for c in (1.0, 0.5):
+            u = nat.to_device(U, DT["bf16x3"])
+            plan.linear_flow(u, c)
+            torch.cuda.synchronize()
+            assert plan.device_status() == nat.CGL_OK
+            check(nat.from_device(u), L.expK(U, c), "bf16x3", "c=%g" % c)
+
+
+@pytest.mark.parametrize("n,bc", [((64, 64), (0, 0)), ((24,), (0,)), ((128, 300), (0, 0)), ((8, 8), (2, 2))])
+def test_tensor_core_path_rejects_unsupported_shapes(n, bc):
+    p, _ = rand_problem(5, n, bc)
+    with pytest.raises(nat.CglError) as ei:
+        nat.Plan(p, 0.01, "strang", "bf16x3")
+    assert ei.value.status == nat.CGL_EUNSUPPORTED
+
+
 # ------------------------------------------------------------ schemes
 
 SCHEME_CASES = [
@@ -136,6 +171,21 @@ def test_schemes_match_oracle(n, bc, schemes, cubic, prec):
         ref = O.integrate(oprob(p), U0, tau, nsteps, s)
         got = run_gpu(p, U0, tau, nsteps, s, prec)
         check(got, ref, prec, "%s cubic=%s" % (s, cubic))
+
+
+MMA_SCHEME_CASES = [((128, 32), (0, 1)), ((128, 16, 32), (1, 0, 1)), ((64,), (0,))]
+
+
+@pytest.mark.parametrize("n,bc", MMA_SCHEME_CASES)
+@pytest.mark.parametrize("cubic", [True, False])
+def test_schemes_match_oracle_tensor_cores(n, bc, cubic):
+    p, rng = rand_problem(6, n, bc, cubic=cubic)
+    U0 = smooth_data(p, rng, amp=0.8)
+    tau, nsteps = 0.004, 5
+    for s in ("strang", "split4", "lawson4", "lawson2"):
+        ref = O.integrate(oprob(p), U0, tau, nsteps, s)
+        got = run_gpu(p, U0, tau, nsteps, s, "bf16x3")
+        check(got, ref, "bf16x3", "%s cubic=%s" % (s, cubic))
 
 
 def test_plane_wave_orders_on_gpu():
@@ -174,6 +224,17 @@ def test_workload_3d_periodic_full_size(scheme):
     ref = O.integrate(oprob(w.prob), U0, w.tau, 2, scheme)
     got = run_gpu(w.prob, U0, w.tau, 2, scheme)
     check(got, ref, "f64", scheme)
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16x3"])
+def test_workload_3d_neumann_full_size(prec):
+    """3D cubic Neumann 256^3, Lawson4, tau = 0.01: the complex64 paths (FP32
+    SIMT and BF16x3 tensor cores) against the FP64 oracle, 2 steps at full size."""
+    w = I.workload_3d_neumann()
+    U0 = I.u0_3d_neumann(w)
+    ref = O.integrate(oprob(w.prob), U0, w.tau, 2, "lawson4")
+    got = run_gpu(w.prob, U0, w.tau, 2, "lawson4", prec)
+    check(got, ref, prec, "lawson4 " + prec)
 
 
 def test_workload_3d_periodic_longer_run_small_grid():
