@@ -55,7 +55,121 @@ def parse():
     ap.add_argument("--scheme", default="split4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--workload", default="periodic128", choices=["periodic128", "neumann256"],
+                    help="periodic128: the headline 3D periodic workload; neumann256: the 3D Neumann "
+                         "precision study (FP64 / FP32 / BF16x3 tensor cores)")
+    ap.add_argument("--t1-steps", type=int, default=100, help="neumann256: steps of the T=1 error run")
     return ap.parse_args()
+
+
+def profiled_traffic(summary, sources):
+    """Per-launch DRAM bytes recorded by an ncu capture in profiles/<summary>,
+    or None when the kernel sources changed since the capture."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for s in sources:
+        with open(os.path.join(ROOT, "paper_2403_02816_gb300", "csrc", s), "rb") as f:
+            h.update(f.read())
+    val = sha = None
+    for line in text.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            val = float(line.split(":")[1])
+        if line.startswith("source_sha256_16:"):
+            sha = line.split(":")[1].split()[0]
+    return val if (val is not None and sha == h.hexdigest()[:16]) else None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def run_neumann256(args):
+    """3D cubic Neumann 256^3, Lawson4, tau = 0.01: throughput of each
+    precision and its relative L2 error at T = steps * tau against the FP64
+    path (itself held to 1e-11 of the FP64 oracle by the parity tests)."""
+    import torch
+    from paper_2403_02816_gb300 import native as nat
+
+    dev = torch.device("cuda", 0)
+    nat.load()
+    w = I.workload_3d_neumann(args.n if args.n != 128 else 256)
+    U0 = I.u0_3d_neumann(w)
+    N = w.prob.N
+    chunk = args.chunk
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    finals = {}
+    prof = {}
+    with Clocks(0) as clk:
+        for prec in ("bf16x3", "f32", "f64"):
+            dt = torch.complex128 if prec == "f64" else torch.complex64
+            with nat.Plan(w.prob, w.tau, "lawson4", prec) as plan:
+                u = nat.to_device(U0, dt, dev)
+                K = args.steps if prec != "f64" else max(1, args.steps // 2)
+                for _ in range(max(args.warmup, 3)):
+                    plan.step(u, 1)
+                torch.cuda.synchronize()
+                ms = 0.0
+                for _ in range(K):
+                    flush.fill_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    plan.step(u, chunk)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                res[prec] = {"grid_pt_steps_per_s": N * chunk * K / (ms / 1e3), "ms_per_time_step": ms / (chunk * K)}
+                prof[prec] = plan.profile(u, 1)
+                # T = t1_steps * tau run from the initial field
+                v = nat.to_device(U0, dt, dev)
+                plan.step(v, args.t1_steps)
+                torch.cuda.synchronize()
+                res[prec]["device_status"] = plan.device_status()
+                finals[prec] = v
+    ref = finals["f64"]
+    for prec in ("bf16x3", "f32"):
+        e2, einf, nf = nat.cgl_rel_error(finals[prec].to(torch.complex128), ref, nat.CGL_F64)
+        res[prec]["rel_l2_vs_f64_at_T"] = e2
+        res[prec]["rel_inf_vs_f64_at_T"] = einf
+        res[prec]["speedup_vs_f64"] = res[prec]["grid_pt_steps_per_s"] / res["f64"]["grid_pt_steps_per_s"]
+    peaks = measured_peaks()
+    mma = [r for r in prof["bf16x3"] if r["name"] == "mma_mode_bf16x3"][0]
+    achieved = mma["flops"] / (mma["total_ms"] / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops", 1948.7))
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "mma_mode_bf16x3", "launches_profiled": mma["launches"],
+                "avg_launch_ms": mma["total_ms"] / mma["launches"],
+                "flops_counted": "issued: 6 split products x 8 n real flops per point per mode",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
+                "share": mma["total_ms"] / sum(r["total_ms"] for r in prof["bf16x3"]),
+                "frac_of_sustained": achieved / float(peaks.get("bf16_tflops_sustained", 1712.8))}
+    f64k = [r for r in prof["f64"] if r["name"] == "mode_pass_f64"][0]
+    f32k = [r for r in prof["f32"] if r["name"] == "mode_pass_f32"][0]
+    line = {
+        "metric": METRIC, "value": res["bf16x3"]["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": res["bf16x3"]["ms_per_time_step"] * chunk,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+        "config": {"workload": w.name, "scheme": "lawson4", "tau": w.tau, "grid": list(w.prob.n),
+                   "time_steps_per_bench_step": chunk, "T": args.t1_steps * w.tau,
+                   "l2": "flushed (256 MiB write) between timed iterations"},
+        "precisions": res, "roofline": roofline,
+        "simt_kernels": {
+            "mode_pass_f64": {"achieved_tflops": f64k["flops"] / (f64k["total_ms"] / 1e3) / 1e12,
+                              "frac_of_fp64_peak": f64k["flops"] / (f64k["total_ms"] / 1e3) / 1e12 / fp64_peak_tflops()},
+            "mode_pass_f32": {"achieved_tflops": f32k["flops"] / (f32k["total_ms"] / 1e3) / 1e12}},
+        "kernels": prof, "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
 
 
 class Clocks:
@@ -158,6 +272,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.workload == "neumann256":
+        run_neumann256(args)
+        return
 
     import torch
     from paper_2403_02816_gb300 import native as nat
@@ -221,6 +338,8 @@ def main():
     achieved = dom["flops"] / (dom["total_ms"] / 1e3) / 1e12
     peak = fp64_peak_tflops()
     traffic = None
+    if args.n == 128 and args.scheme == "split4":
+        traffic = profiled_traffic("fft_pass_f64_dram_split4_128cubed.md", ["fft.cu", "cgl_internal.cuh"])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom["name"], "launches_profiled": dom["launches"],
                 "avg_launch_ms": dom["total_ms"] / dom["launches"],

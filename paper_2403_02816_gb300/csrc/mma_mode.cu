@@ -9,12 +9,14 @@
 // = 2n contiguous values.  The state is held as three BF16 planes per
 // component (x = h + m + l, h = bf16(x), m = bf16(x - h), l = bf16(x - h - m)),
 // the factor likewise (split once from FP64), and six products
-// (lh, hl, mm, mh, hm, hh; small terms first) accumulate in one FP32 TMEM
-// accumulator: about 24 significant bits, i.e. FP32 accuracy.
+// (lh, hl, mm, mh, hm, hh) accumulate in FP32 tensor memory: about 24
+// significant bits, i.e. FP32 accuracy.
 //
-// Kernel shape: one CTA per tile of 128 fibers (TMEM lanes) x all 2n outputs
-// (TMEM columns, n <= 256); K advances 16 per pipeline stage, three stages,
-// filled by TMA (A: K-major for mode 1 whose fibers are contiguous, MN-major
+// Kernel shape: one CTA per tile of 128 fibers (TMEM lanes) x the n outputs
+// of one component (re or im; n <= 256), with the (h,h) product and the five
+// correction products in separate TMEM accumulators that the epilogue adds in
+// FP32; K advances 16 per pipeline stage, five stages, filled by TMA
+// (A: K-major for mode 1 whose fibers are contiguous, MN-major
 // for the other modes; B: K-major), consumed by tcgen05.mma issued by one
 // thread, freed by tcgen05.commit.  Every mbarrier wait is bounded: on
 // timeout the kernel sets bit 1 of the status word, skips its stores, waits
@@ -32,7 +34,7 @@
 namespace cgl {
 
 constexpr int kMmaThreads = 128;
-constexpr int kMmaStages = 3;
+constexpr int kMmaStages = 5;
 constexpr int kMmaM = 128;
 constexpr int kMmaK = 16;
 constexpr long long kSpinLimit = 1ll << 24;
@@ -166,15 +168,20 @@ struct MmaPassArgs {
   int out_fp32;      // 1: FP32 planes (re, im); 0: BF16x3 planes (6)
   void* out[kMaxRhs];
   int64_t N;         // plane length (field size)
-  int64_t mtiles;    // tiles of 128 fibers
   int tmem_cols;     // power of two >= 2n
   int* status;
 };
 
+// One pipeline stage: three A splits (128 fibers x 16) and three B splits
+// (n output rows of one half x 16).
 static __host__ __device__ constexpr uint32_t mma_stage_bytes(int n) {
-  return 3u * (kMmaM * kMmaK * 2u) + 3u * (2u * n * kMmaK * 2u);
+  return 3u * (kMmaM * kMmaK * 2u) + 3u * (static_cast<uint32_t>(n) * kMmaK * 2u);
 }
 
+// CTA (tile, half): 128 fibers x the n outputs of component c' = half.
+// TMEM columns [0, n): the (h, h) product; [n, 2n): the five correction
+// products.  Keeping the large term in its own accumulator keeps the
+// accumulator rounding of the many small MMAs relative to the small terms.
 __global__ void __launch_bounds__(kMmaThreads, 1)
     mma_mode_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                     const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
@@ -187,7 +194,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   const CUtensorMap* tmB = rhs ? &tmB1 : &tmB0;
   const int nk = (2 * n) / kMmaK;
   const uint32_t a_bytes = kMmaM * kMmaK * 2;
-  const uint32_t b_bytes = 2u * n * kMmaK * 2;
+  const uint32_t b_bytes = static_cast<uint32_t>(n) * kMmaK * 2;
   const uint32_t stage_bytes = mma_stage_bytes(n);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + kMmaStages * stage_bytes);
   uint64_t* empty = full + kMmaStages;
@@ -196,8 +203,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5;
 
-  // fiber tile coordinates
-  const int64_t tile = blockIdx.x;
+  // the two halves of a fiber tile are adjacent blocks, so the second read
+  // of the tile's A data is served from L2
+  const int64_t tile = blockIdx.x >> 1;
+  const int half = blockIdx.x & 1;
   int64_t q0 = 0, p0 = 0;
   if (a.a_mn) {
     const int64_t per_q = a.P / kMmaM;
@@ -221,6 +230,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t d_main = tmem, d_corr = tmem + n;
 
   if (threadIdx.x == 0) {
     const uint32_t idesc = idesc_bf16(kMmaM, n, a.a_mn);
@@ -239,18 +249,15 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
         } else {
           tma_load_3d(dA, tmA, bar, j0, (int)q0, plane);
         }
-        const uint32_t dB = smem_u32(st + 3 * a_bytes + s * b_bytes);
-        tma_load_3d(dB, tmB, bar, k0, 0, s);
-        tma_load_3d(dB + n * 32, tmB, bar, k0, n, s);
+        tma_load_3d(smem_u32(st + 3 * a_bytes + s * b_bytes), tmB, bar, k0, half * n, s);
       }
     };
-    // split products, small terms first: (l,h) (h,l) (m,m) (m,h) (h,m) (h,h)
+    // split products: five corrections (l,h) (h,l) (m,m) (m,h) (h,m), then (h,h)
     const int pa[6] = {2, 0, 1, 1, 0, 0};
     const int pb[6] = {0, 2, 1, 0, 1, 0};
-    int loaded = 0;  // stages whose TMA has been issued
+    int loaded = 0;
     for (; loaded < kMmaStages && loaded < nk; ++loaded) issue_load(loaded, loaded);
-    int consumed = 0;  // stages whose full barrier has been waited
-    int committed = 0;
+    int consumed = 0, committed = 0;
     bool ok = true;
     for (int kb = 0; kb < nk; ++kb) {
       const int slot = kb % kMmaStages;
@@ -261,14 +268,13 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       for (int pr = 0; pr < 6; ++pr) {
         const uint32_t aaddr = smem_u32(st + pa[pr] * a_bytes);
         const uint64_t adesc = a.a_mn ? smem_desc(aaddr, 2048, 1024, 2) : smem_desc(aaddr, 16, 256, 6);
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t baddr = smem_u32(st + 3 * a_bytes + pb[pr] * b_bytes + h * n * 32);
-          mma_bf16(tmem + h * n, adesc, smem_desc(baddr, 16, 256, 6), idesc, (kb > 0 || pr > 0) ? 1u : 0u);
-        }
+        const uint64_t bdesc = smem_desc(smem_u32(st + 3 * a_bytes + pb[pr] * b_bytes), 16, 256, 6);
+        if (pr < 5) mma_bf16(d_corr, adesc, bdesc, idesc, (kb > 0 || pr > 0) ? 1u : 0u);
+        else mma_bf16(d_main, adesc, bdesc, idesc, kb > 0 ? 1u : 0u);
       }
       mma_commit(smem_u32(&empty[slot]));
       committed = kb + 1;
-      // refill the slot consumed one iteration ago with stage kb + 2
+      // refill the slot consumed one iteration ago
       if (kb >= 1 && loaded < nk) {
         const int ps = (kb - 1) % kMmaStages;
         if (!mbar_wait(smem_u32(&empty[ps]), ((kb - 1) / kMmaStages) & 1)) { ok = false; break; }
@@ -301,7 +307,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   if (good) {
     const int m = threadIdx.x;  // TMEM lane = fiber of the tile
     bool valid;
-    int64_t obase, ostride;     // output index of (c', i) = obase + ostride * i
+    int64_t obase, ostride;     // output index of row i = obase + ostride * i
     if (a.a_mn) {
       valid = true;
       obase = (p0 + m) + a.P * (int64_t)n * q0;
@@ -312,26 +318,45 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       obase = (int64_t)n * q;
       ostride = 1;
     }
-    const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    for (int h = 0; h < 2; ++h) {
-      for (int i0 = 0; i0 < n; i0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(lane_addr + h * n + i0, r);
-        if (!valid) continue;
-        if (a.out_fp32) {
-          float* o = reinterpret_cast<float*>(a.out[rhs]) + (int64_t)h * a.N;
+    const uint32_t lane_addr = static_cast<uint32_t>(warp * 32) << 16;
+    for (int i0 = 0; i0 < n; i0 += 16) {
+      uint32_t rm[16], rc[16];
+      tmem_ld16(d_main + lane_addr + i0, rm);
+      tmem_ld16(d_corr + lane_addr + i0, rc);
+      if (!valid) continue;
+      float v[16];
 #pragma unroll
-          for (int t = 0; t < 16; ++t) o[obase + ostride * (i0 + t)] = __uint_as_float(r[t]);
+      for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(rm[t]) + __uint_as_float(rc[t]);
+      if (a.out_fp32) {
+        float* o = reinterpret_cast<float*>(a.out[rhs]) + (int64_t)half * a.N;
+        if (!a.a_mn) {
+          float4* d4 = reinterpret_cast<float4*>(o + obase + i0);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) d4[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
         } else {
-          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out[rhs]);
 #pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            __nv_bfloat16 sh, sm, sl;
-            split3(__uint_as_float(r[t]), sh, sm, sl);
-            const int64_t idx = obase + ostride * (i0 + t);
-            o[(0 * 2 + h) * a.N + idx] = sh;
-            o[(1 * 2 + h) * a.N + idx] = sm;
-            o[(2 * 2 + h) * a.N + idx] = sl;
+          for (int t = 0; t < 16; ++t) o[obase + ostride * (i0 + t)] = v[t];
+        }
+      } else {
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out[rhs]);
+        __nv_bfloat16 sp[3][16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) split3(v[t], sp[0][t], sp[1][t], sp[2][t]);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          __nv_bfloat16* plane = o + (int64_t)(s * 2 + half) * a.N;
+          if (!a.a_mn) {
+            uint32_t w[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              w[k] = static_cast<uint32_t>(__bfloat16_as_ushort(sp[s][2 * k])) |
+                     (static_cast<uint32_t>(__bfloat16_as_ushort(sp[s][2 * k + 1])) << 16);
+            uint4* d4 = reinterpret_cast<uint4*>(plane + obase + i0);
+            d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) plane[obase + ostride * (i0 + t)] = sp[s][t];
           }
         }
       }
@@ -485,7 +510,7 @@ cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
   a.out[0] = L.out[0];
   a.out[1] = L.out[1];
   a.N = L.N;
-  a.mtiles = L.P > 1 ? (L.P / kMmaM) * L.Q : (L.Q + kMmaM - 1) / kMmaM;
+  const int64_t mtiles = L.P > 1 ? (L.P / kMmaM) * L.Q : (L.Q + kMmaM - 1) / kMmaM;
   int cols = 32;
   while (cols < 2 * L.n) cols *= 2;
   a.tmem_cols = cols;
@@ -494,7 +519,7 @@ cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
   const CUtensorMap* A1 = reinterpret_cast<const CUtensorMap*>(L.tmA[L.nrhs > 1 ? 1 : 0]);
   const CUtensorMap* B0 = reinterpret_cast<const CUtensorMap*>(L.tmB[0]);
   const CUtensorMap* B1 = reinterpret_cast<const CUtensorMap*>(L.tmB[L.nrhs > 1 ? 1 : 0]);
-  dim3 grid((unsigned)a.mtiles, (unsigned)L.nrhs);
+  dim3 grid((unsigned)(2 * mtiles), (unsigned)L.nrhs);  // (fiber tile, output component)
   mma_mode_kernel<<<grid, kMmaThreads, mma_smem_bytes(L.n), s>>>(*A0, *A1, *B0, *B1, a);
   return cudaGetLastError();
 }
