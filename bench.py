@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--scheme", default="split4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--workload", default="periodic128", choices=["periodic128", "neumann256"],
+    ap.add_argument("--workload", default="periodic128", choices=["periodic128", "neumann256", "batch512"],
                     help="periodic128: the headline 3D periodic workload; neumann256: the 3D Neumann "
                          "precision study (FP64 / FP32 / BF16x3 tensor cores)")
     ap.add_argument("--t1-steps", type=int, default=100, help="neumann256: steps of the T=1 error run")
@@ -90,6 +90,99 @@ def measured_peaks():
             return json.load(f)
     except Exception:
         return {}
+
+
+def run_batch512(args):
+    """512 independent 2D cubic / cubic-quintic instances (grids 48..256 per
+    direction, Dirichlet/Neumann mixes, random parameters and bumps),
+    Lawson4, tau = 0.01: batched persistent launches (FP32 and FP64) against
+    the plain method (one FP64 plan per instance, stepped one after another),
+    and the FP32 batch's error after 200 steps against the FP64 batch."""
+    import torch
+    from paper_2403_02816_gb300 import native as nat
+
+    dev = torch.device("cuda", 0)
+    nat.load()
+    count = 512
+    probs = I.batched_problems(count)
+    fields = [I.u0_bumps(p, np.random.Generator(np.random.PCG64(I.SEED_BASE + 3 + 1000 * i)))
+              for i, p in enumerate(probs)]
+    total = sum(p.N for p in probs)
+    tau, chunk = 0.01, args.chunk
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    # algorithmic flops per Lawson4 step: 2 sweeps x 2 fields x 8 n_mu N per mode,
+    # plus g (15), the first-sweep combination (46) and the last (19) per point
+    flops_step = sum(4 * 8 * (p.n[0] + p.n[1]) * p.N + (15 + 46 + 19) * p.N for p in probs)
+
+    def timed(step_fn, K):
+        for _ in range(max(args.warmup, 3)):
+            step_fn(1)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(K):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step_fn(chunk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / (K * chunk)
+
+    res, finals = {}, {}
+    with Clocks(0) as clk:
+        for prec in ("f32", "f64"):
+            t0 = time.perf_counter()
+            with nat.Batch(probs, tau, "lawson4", prec) as b:
+                create_s = time.perf_counter() - t0
+                u = b.pack(fields, dev)
+                ms = timed(lambda k: b.step(u, k), args.steps if prec == "f32" else max(1, args.steps // 2))
+                res["batched_" + prec] = {"grid_pt_steps_per_s": total / (ms / 1e3), "ms_per_time_step": ms,
+                                          "create_s": create_s, "launches_per_step": b.launches_per_step,
+                                          "achieved_tflops": flops_step / (ms / 1e3) / 1e12}
+                v = b.pack(fields, dev)
+                b.step(v, args.t1_steps)
+                torch.cuda.synchronize()
+                res["batched_" + prec]["device_status"] = b.device_status()
+                finals[prec] = b.unpack(v)
+        # the plain method: one FP64 plan per instance, stepped in turn
+        plans = [nat.Plan(p, tau, "lawson4", "f64") for p in probs]
+        us = [nat.to_device(U, torch.complex128, dev) for U in fields]
+
+        def seq(k):
+            for pl, uu in zip(plans, us):
+                pl.step(uu, k)
+        ms = timed(seq, 1)
+        res["single_plans_f64"] = {"grid_pt_steps_per_s": total / (ms / 1e3), "ms_per_time_step": ms,
+                                   "achieved_tflops": flops_step / (ms / 1e3) / 1e12}
+        for pl in plans:
+            pl.close()
+    errs = []
+    from oracle import cgl_oracle as O
+    for a, r in zip(finals["f32"], finals["f64"]):
+        errs.append(O.rel_l2(a, r))
+    fp32_peak = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    f32 = res["batched_f32"]
+    line = {
+        "metric": METRIC, "value": f32["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": f32["ms_per_time_step"] * chunk, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched_512x2d_lawson4_c64", "instances": count, "total_points": total,
+                   "tau": tau, "time_steps_per_bench_step": chunk, "T_steps_for_error": args.t1_steps,
+                   "l2": "flushed (256 MiB write) between timed iterations"},
+        "results": res,
+        "f32_vs_f64_rel_l2_per_instance": {"max": max(errs), "median": float(np.median(errs))},
+        "speedup_batched_f32_vs_single_f64": f32["grid_pt_steps_per_s"] / res["single_plans_f64"]["grid_pt_steps_per_s"],
+        "speedup_batched_f64_vs_single_f64": res["batched_f64"]["grid_pt_steps_per_s"] /
+        res["single_plans_f64"]["grid_pt_steps_per_s"],
+        "roofline": {"bound": "alu", "kernel": "batched_mode_pass_kernel<float>", "achieved": f32["achieved_tflops"],
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": f32["achieved_tflops"] / fp32_peak,
+                     "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
+                     "note": "whole-step time, all passes"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
 
 
 def run_neumann256(args):
@@ -274,6 +367,9 @@ def main():
         return
     if args.workload == "neumann256":
         run_neumann256(args)
+        return
+    if args.workload == "batch512":
+        run_batch512(args)
         return
 
     import torch

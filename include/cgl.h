@@ -181,6 +181,70 @@ int cgl_profile_step(cgl_plan* plan, void* u, int64_t nsteps, void* stream,
 int cgl_rel_error(const void* x, const void* y, int64_t count, int precision,
                   double* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent instances of eq. 1 (each with its own grid,
+ * boundary conditions and parameters) advanced together.
+ * ---------------------------------------------------------------------- */
+
+/* One problem of a batch: d, n[d], bc[d], lo[d], hi[d] and the parameters
+ * exactly as in cgl_plan_create (entries beyond d are ignored). */
+typedef struct cgl_problem {
+    int d;
+    int64_t n[3];
+    int bc[3];
+    double lo[3], hi[3];
+    double a1, b1, a2, a3, b3, a4, b4;
+} cgl_problem;
+
+typedef struct cgl_batch cgl_batch;
+
+/*
+ * Create a batch of `count` finite-difference problems (Dirichlet/Neumann;
+ * periodic -> EUNSUPPORTED) sharing one step size and scheme (strang,
+ * split4, lawson4, lawson2) in CGL_F64 or CGL_F32.  Each instance gets its own
+ * FP64 factors exp(c tau A_mu) (Sec. 3.1).  Every mu-mode pass of a time step
+ * is ONE persistent launch over all instances: a fixed grid of CTAs pulls
+ * (instance, fiber tile) work items, largest first, from a device queue; the
+ * fibers per tile come from cgl_autotune_mode_tile.  The whole time step is
+ * replayed as one CUDA graph.  Synchronous (set-up and autotuning).
+ * Errors: EINVAL (per-instance validation as cgl_plan_create, message names
+ * the instance), EUNSUPPORTED, ENOMEM, ECUDA.
+ */
+int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, double tau, int scheme,
+                     int precision, void* stream);
+
+/*
+ * Layout of the batch's packed field: *total_points = sum of N_i; offsets
+ * (count entries, may be NULL) = element offset of instance i, in instance
+ * order; workspace bytes; launches per time step.  Any pointer may be NULL.
+ */
+int cgl_batch_info(const cgl_batch* batch, int64_t* total_points, int64_t* offsets,
+                   size_t* workspace_bytes, int* launches_per_step);
+
+/*
+ * Advance every instance of the packed device field u (total_points complex
+ * values; instance i at offsets[i], each in the layout of cgl_step) by nsteps
+ * steps, in place.  Asynchronous on `stream`; graph captured per u pointer.
+ */
+int cgl_batch_step(cgl_batch* batch, void* u, int64_t nsteps, void* stream);
+
+/* Read and clear the batch's device status word (as cgl_last_device_status). */
+int cgl_batch_last_device_status(cgl_batch* batch, void* stream);
+
+/* Destroy a batch; NULL is accepted. */
+int cgl_batch_destroy(cgl_batch* batch);
+
+/*
+ * Tile-size autotuner of the mu-mode pass: times every admissible number of
+ * fibers per CTA (2, 4, ..., 64, within 96 KiB of shared memory) for mode
+ * length n, contiguous (mode 1) or strided fibers, precision (CGL_F64 /
+ * CGL_F32) and nrhs (1 or 2) on a synthetic 2048-fiber field, and returns the
+ * fastest in *tb (*ms = its time per pass, may be NULL).  Results are cached
+ * per process and, when the environment variable CGL_AUTOTUNE_CACHE names a
+ * file, appended to / read from that file (one line per shape).  Synchronous.
+ */
+int cgl_autotune_mode_tile(int n, int contiguous, int precision, int nrhs, int* tb, double* ms);
+
 /*
  * Allocation-free variant of cgl_rel_error (the paper has no counterpart:
  * this entry point exists for callers of the library, not for the method).

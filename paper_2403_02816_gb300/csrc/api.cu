@@ -18,10 +18,11 @@
 #include <vector>
 
 #include "cgl_internal.cuh"
+#include "plan.cuh"
 
 using namespace cgl;
 
-namespace {
+namespace cgl {
 
 thread_local std::string g_last_error;
 
@@ -30,76 +31,10 @@ int fail(int status, const std::string& msg) {
   return status;
 }
 
-#define CUDA_TRY(expr)                                                                   \
-  do {                                                                                   \
-    cudaError_t _e = (expr);                                                             \
-    if (_e != cudaSuccess)                                                               \
-      return fail(_e == cudaErrorMemoryAllocation ? CGL_ENOMEM : CGL_ECUDA,              \
-                  std::string(#expr) + ": " + cudaGetErrorString(_e));                   \
-  } while (0)
+}  // namespace cgl
 
-enum { BUF_U = 0, BUF_W0 = 1, BUF_W1 = 2, BUF_W2 = 3, NBUF = 4 };
-constexpr int FAC_K = -1;  // the Runge-Kutta sweeps apply K, not an exponential
 
-struct Sweep {
-  int nin = 1, in[2] = {BUF_U, BUF_U};
-  int nrhs = 1, fac[2] = {0, 0}, work[2] = {BUF_U, BUF_U};
-  int nextra = 0, extra[3] = {BUF_U, BUF_U, BUF_U};
-  int nout = 1, out[2] = {BUF_U, BUF_U};
-  OpArgs op{};
-};
-
-struct KernelStat {
-  int64_t launches = 0;
-  double ms = 0, flops = 0, bytes = 0;
-};
-
-}  // namespace
-
-struct cgl_plan {
-  int dev = 0;
-  int d = 0;
-  int64_t n[3] = {1, 1, 1};
-  int bc[3] = {0, 0, 0};
-  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-  double a1 = 0, b1 = 0, a2 = 0, a3 = 0, b3 = 0, a4 = 0, b4 = 0, tau = 0;
-  int scheme = 0, precision = 0, periodic = 0, cubic = 0;
-  int64_t N = 0;
-  size_t elem = 0;
-
-  int nfac = 0;
-  double cval[2] = {0, 0};
-  void* fac[2][3] = {{nullptr}};        // working-precision factors / symbol vectors
-  double2* fac64[2][3] = {{nullptr}};   // FP64 masters
-  void* ksym[3] = {nullptr};            // K symbol vectors (periodic Runge-Kutta)
-  void* twiddle[3] = {nullptr};         // FFT twiddles per axis
-  std::vector<void*> allocations;
-
-  int nwork = 0;
-  void* work[3] = {nullptr, nullptr, nullptr};
-  int* status = nullptr;
-  void* host_stage = nullptr;  // device field for cgl_step_host
-
-  std::vector<Sweep> sweeps;
-
-  // BF16x3 tensor-core path: per-rhs BF16x3 state planes and FP32 output
-  // planes, per-(factor, mode) BF16x3 factor splits, and their TMA maps.
-  void* splits[2] = {nullptr, nullptr};
-  void* planes[2] = {nullptr, nullptr};
-  void* fsplit[2][3] = {{nullptr}};
-  alignas(64) unsigned char tmA[3][2][kTensorMapBytes];
-  alignas(64) unsigned char tmB[2][3][kTensorMapBytes];
-
-  cudaStream_t cap = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  void* graph_u = nullptr;
-
-  // profiling (when `prof` is set, launches are bracketed by events)
-  bool prof = false;
-  std::map<std::string, KernelStat>* stats = nullptr;
-};
-
-namespace {
+namespace cgl {
 
 int64_t axis_P(const cgl_plan* p, int axis) {
   int64_t P = 1;
@@ -171,6 +106,26 @@ struct Timer {
   }
 };
 
+ModePassArgs make_mode_args(const cgl_plan* p, const Sweep& sw, int mu, void* const* bufs) {
+  ModePassArgs a{};
+  a.g = geom(p, mu);
+  a.f.nin = sw.nin;
+  a.f.nrhs = sw.nrhs;
+  a.f.nextra = sw.nextra;
+  a.f.nout = sw.nout;
+  for (int r = 0; r < 2; ++r) {
+    a.f.in[r] = bufs[sw.in[r]];
+    a.f.work[r] = bufs[sw.work[r]];
+    a.f.out[r] = bufs[sw.out[r]];
+  }
+  for (int x = 0; x < 3; ++x) a.f.extra[x] = bufs[sw.extra[x]];
+  a.op = sw.op;
+  a.flags = (mu == 0 ? PASS_PRO : 0) | (mu == p->d - 1 ? PASS_EPI : 0);
+  for (int r = 0; r < 2; ++r) a.factor[r] = p->fac[sw.fac[r < sw.nrhs ? r : 0]][mu];
+  a.status = p->status;
+  return a;
+}
+
 int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
   void* bufs[NBUF] = {u, p->work[0], p->work[1], p->work[2]};
   PassFields f{};
@@ -232,13 +187,7 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
 
   if (!p->periodic) {
     for (int mu = 0; mu < p->d; ++mu) {
-      ModePassArgs a{};
-      a.g = geom(p, mu);
-      a.f = f;
-      a.op = sw.op;
-      a.flags = (mu == 0 ? PASS_PRO : 0) | (mu == p->d - 1 ? PASS_EPI : 0);
-      for (int r = 0; r < 2; ++r) a.factor[r] = p->fac[sw.fac[r < sw.nrhs ? r : 0]][mu];
-      a.status = p->status;
+      const ModePassArgs a = make_mode_args(p, sw, mu, bufs);
       double flops = 8.0 * (double)p->n[mu] * Nd * sw.nrhs;
       double rd = (mu == 0 ? sw.nin : sw.nrhs), wr = (mu == p->d - 1 ? sw.nout : sw.nrhs);
       if (mu == 0) flops += pro_flops(p, sw.op) * Nd;
@@ -562,7 +511,7 @@ void free_plan(cgl_plan* p) {
   delete p;
 }
 
-}  // namespace
+}  // namespace cgl
 
 extern "C" {
 
@@ -581,9 +530,13 @@ const char* cgl_strerror(int status) {
 
 const char* cgl_last_error(void) { return g_last_error.c_str(); }
 
-int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
-                    double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
-                    int scheme, int precision, void* stream) {
+}  // extern "C"
+
+namespace cgl {
+
+int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
+                     double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
+                     int scheme, int precision, void* stream, bool minimal) {
   g_last_error.clear();
   if (!out) return fail(CGL_EINVAL, "out is NULL");
   *out = nullptr;
@@ -659,11 +612,13 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, cons
     delete p;
     return fail(CGL_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
   }
-  e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
-  if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("stream create: ") + cudaGetErrorString(e));
+  if (!minimal) {
+    e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("stream create: ") + cudaGetErrorString(e));
+  }
   if (!st) st = dev_alloc(p, (void**)&p->status, sizeof(int));
   if (!st && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) st = fail(CGL_ECUDA, "memset status");
-  for (int w = 0; !st && w < p->nwork; ++w) st = dev_alloc(p, &p->work[w], p->N * p->elem);
+  for (int w = 0; !st && !minimal && w < p->nwork; ++w) st = dev_alloc(p, &p->work[w], p->N * p->elem);
   if (!st && precision == CGL_BF16X3) {
     const int nr = scheme == CGL_STRANG ? 1 : 2;
     for (int r = 0; !st && r < nr; ++r) {
@@ -688,6 +643,16 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, cons
   build_program(p);
   *out = p;
   return CGL_OK;
+}
+
+}  // namespace cgl
+
+extern "C" {
+
+int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
+                    double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
+                    int scheme, int precision, void* stream) {
+  return plan_create_impl(out, d, n, bc, lo, hi, a1, b1, a2, a3, b3, a4, b4, tau, scheme, precision, stream, false);
 }
 
 int cgl_plan_destroy(cgl_plan* p) {

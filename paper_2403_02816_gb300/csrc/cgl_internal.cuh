@@ -281,6 +281,21 @@ template <class T> cudaError_t launch_mode_pass(const ModePassArgs& a, cudaStrea
 template <class T> cudaError_t prepare_fft_pass();
 template <class T> cudaError_t prepare_mode_pass();
 
+// Mode pass with an explicit number of fibers per CTA (tb), and the
+// persistent grouped variant over many instances (batch.cu).
+struct BatchItem {
+  int inst;     // index into the per-instance ModePassArgs table
+  int tb;       // fibers per tile
+  int64_t b0;   // first fiber
+};
+int mode_tb_max(int n, int nrhs, size_t elem);
+size_t mode_smem_bytes(int n, int nrhs, size_t elem, int tb);
+template <class T> cudaError_t launch_mode_pass_tb(const ModePassArgs& a, int tb, cudaStream_t s);
+template <class T>
+cudaError_t launch_batched_mode_pass(const ModePassArgs* table, const BatchItem* items, int nitems, int* counter,
+                                     int nrhs, size_t smem, int grid, cudaStream_t s);
+template <class T> int batched_mode_blocks_per_sm(int nrhs, size_t smem);
+
 // expm.cu: FP64 complex n x n exponential of (scale * A) on the device.
 // dA: n x n column-major double2 (device); dOut: same layout.  work: 3*n*n double2.
 cudaError_t expm_device(const double2* dA, double scale, int n, double2* dOut, double2* work,

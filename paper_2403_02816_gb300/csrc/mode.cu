@@ -52,14 +52,14 @@ __device__ __forceinline__ void finish_point(const ModePassArgs& a, typename C2<
   }
 }
 
+// One tile: fibers b0 .. b0+tbmax-1 (clipped) of the pass described by `a`,
+// using `smem_raw` (tbmax * (n+1) * NRHS values + tbmax offsets).
 template <class T, int NRHS>
-__global__ void __launch_bounds__(kModeThreads) mode_pass_kernel(const ModePassArgs a, int tbmax) {
+__device__ __forceinline__ void mode_tile(const ModePassArgs& a, int tbmax, int64_t b0, unsigned char* smem_raw) {
   using T2 = typename C2<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = (int)a.g.n_ax;
   const int pitch = n + 1;
   const int64_t P = a.g.P;
-  const int64_t b0 = (int64_t)blockIdx.x * tbmax;
   const int tb = (int)min((int64_t)tbmax, a.g.npencils - b0);
 
   T2* Z0 = reinterpret_cast<T2*>(smem_raw);
@@ -166,11 +166,82 @@ __global__ void __launch_bounds__(kModeThreads) mode_pass_kernel(const ModePassA
   if (bad && a.status) atomicOr(a.status, 1);
 }
 
+template <class T, int NRHS>
+__global__ void __launch_bounds__(kModeThreads) mode_pass_kernel(const ModePassArgs a, int tbmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  mode_tile<T, NRHS>(a, tbmax, (int64_t)blockIdx.x * tbmax, smem_raw);
+}
+
+// Persistent grouped pass over many independent instances: a fixed grid of
+// CTAs pulls work items (instance, first fiber, fibers) from `items` through
+// the atomic `counter` (zeroed before the launch) until the list is empty.
+// Items are ordered by decreasing cost, so the long tiles start first.
+template <class T, int NRHS>
+__global__ void __launch_bounds__(kModeThreads) batched_mode_pass_kernel(const ModePassArgs* __restrict__ table,
+                                                                         const BatchItem* __restrict__ items,
+                                                                         int nitems, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem bi = items[it];
+    const ModePassArgs a = table[bi.inst];
+    mode_tile<T, NRHS>(a, bi.tb, bi.b0, smem_raw);
+    __syncthreads();
+  }
+}
+
 static int mode_tb(int n, int nrhs, size_t elem, int64_t npencils) {
   const size_t per = (size_t)(n + 1) * elem * nrhs + sizeof(int64_t);
   int tb = (int)std::min<size_t>(16, kModeMaxSmem / per);
   tb = std::max(tb, 1);
   return (int)std::min<int64_t>(tb, npencils);
+}
+
+int mode_tb_max(int n, int nrhs, size_t elem) {
+  const size_t per = (size_t)(n + 1) * elem * nrhs + sizeof(int64_t);
+  return std::max<int>(1, (int)(kModeMaxSmem / per));
+}
+
+size_t mode_smem_bytes(int n, int nrhs, size_t elem, int tb) {
+  return (size_t)tb * (n + 1) * elem * nrhs + (size_t)tb * sizeof(int64_t);
+}
+
+template <class T> cudaError_t launch_mode_pass_tb(const ModePassArgs& a, int tb, cudaStream_t s) {
+  using T2 = typename C2<T>::type;
+  const int n = (int)a.g.n_ax;
+  const int nrhs = a.f.nrhs;
+  tb = (int)std::min<int64_t>(std::max(tb, 1), a.g.npencils);
+  const int64_t grid = (a.g.npencils + tb - 1) / tb;
+  const size_t smem = mode_smem_bytes(n, nrhs, sizeof(T2), tb);
+  if (nrhs > 1)
+    mode_pass_kernel<T, 2><<<(unsigned)grid, kModeThreads, smem, s>>>(a, tb);
+  else
+    mode_pass_kernel<T, 1><<<(unsigned)grid, kModeThreads, smem, s>>>(a, tb);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_batched_mode_pass(const ModePassArgs* table, const BatchItem* items, int nitems, int* counter,
+                                     int nrhs, size_t smem, int grid, cudaStream_t s) {
+  if (nrhs > 1)
+    batched_mode_pass_kernel<T, 2><<<grid, kModeThreads, smem, s>>>(table, items, nitems, counter);
+  else
+    batched_mode_pass_kernel<T, 1><<<grid, kModeThreads, smem, s>>>(table, items, nitems, counter);
+  return cudaGetLastError();
+}
+
+template <class T> int batched_mode_blocks_per_sm(int nrhs, size_t smem) {
+  int b = 0;
+  if (nrhs > 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_mode_pass_kernel<T, 2>, kModeThreads, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_mode_pass_kernel<T, 1>, kModeThreads, smem);
+  return std::max(b, 1);
 }
 
 template <class T> cudaError_t launch_mode_pass(const ModePassArgs& a, cudaStream_t s) {
@@ -193,12 +264,25 @@ template <class T> cudaError_t prepare_mode_pass() {
   cudaError_t e = cudaFuncSetAttribute(mode_pass_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kModeMaxSmem + 4096);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(mode_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(mode_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kModeMaxSmem + 4096);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(batched_mode_pass_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kModeMaxSmem + 4096);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(batched_mode_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kModeMaxSmem + 4096);
 }
 
 template cudaError_t prepare_mode_pass<double>();
 template cudaError_t prepare_mode_pass<float>();
+template cudaError_t launch_mode_pass_tb<double>(const ModePassArgs&, int, cudaStream_t);
+template cudaError_t launch_mode_pass_tb<float>(const ModePassArgs&, int, cudaStream_t);
+template cudaError_t launch_batched_mode_pass<double>(const ModePassArgs*, const BatchItem*, int, int*, int, size_t,
+                                                      int, cudaStream_t);
+template cudaError_t launch_batched_mode_pass<float>(const ModePassArgs*, const BatchItem*, int, int*, int, size_t,
+                                                     int, cudaStream_t);
+template int batched_mode_blocks_per_sm<double>(int, size_t);
+template int batched_mode_blocks_per_sm<float>(int, size_t);
 
 template cudaError_t launch_mode_pass<double>(const ModePassArgs&, cudaStream_t);
 template cudaError_t launch_mode_pass<float>(const ModePassArgs&, cudaStream_t);

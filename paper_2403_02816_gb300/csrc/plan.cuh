@@ -1,0 +1,101 @@
+// Internal plan layout shared by the libcgl host translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cgl_internal.cuh"
+
+namespace cgl {
+
+// Records `msg` as the calling thread's last error and returns `status`.
+int fail(int status, const std::string& msg);
+
+enum { BUF_U = 0, BUF_W0 = 1, BUF_W1 = 2, BUF_W2 = 3, NBUF = 4 };
+constexpr int FAC_K = -1;  // the Runge-Kutta sweeps apply K, not an exponential
+
+struct Sweep {
+  int nin = 1, in[2] = {BUF_U, BUF_U};
+  int nrhs = 1, fac[2] = {0, 0}, work[2] = {BUF_U, BUF_U};
+  int nextra = 0, extra[3] = {BUF_U, BUF_U, BUF_U};
+  int nout = 1, out[2] = {BUF_U, BUF_U};
+  OpArgs op{};
+};
+
+struct KernelStat {
+  int64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+
+}  // namespace cgl
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return cgl::fail(_e == cudaErrorMemoryAllocation ? CGL_ENOMEM : CGL_ECUDA,         \
+                       std::string(#expr) + ": " + cudaGetErrorString(_e));              \
+  } while (0)
+
+struct cgl_plan {
+  int dev = 0;
+  int d = 0;
+  int64_t n[3] = {1, 1, 1};
+  int bc[3] = {0, 0, 0};
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  double a1 = 0, b1 = 0, a2 = 0, a3 = 0, b3 = 0, a4 = 0, b4 = 0, tau = 0;
+  int scheme = 0, precision = 0, periodic = 0, cubic = 0;
+  int64_t N = 0;
+  size_t elem = 0;
+
+  int nfac = 0;
+  double cval[2] = {0, 0};
+  void* fac[2][3] = {{nullptr}};        // working-precision factors / symbol vectors
+  double2* fac64[2][3] = {{nullptr}};   // FP64 masters
+  void* ksym[3] = {nullptr};            // K symbol vectors (periodic Runge-Kutta)
+  void* twiddle[3] = {nullptr};         // FFT twiddles per axis
+  std::vector<void*> allocations;
+
+  int nwork = 0;
+  void* work[3] = {nullptr, nullptr, nullptr};
+  int* status = nullptr;
+  void* host_stage = nullptr;  // device field for cgl_step_host
+
+  std::vector<cgl::Sweep> sweeps;
+
+  // BF16x3 tensor-core path: per-rhs BF16x3 state planes and FP32 output
+  // planes, per-(factor, mode) BF16x3 factor splits, and their TMA maps.
+  void* splits[2] = {nullptr, nullptr};
+  void* planes[2] = {nullptr, nullptr};
+  void* fsplit[2][3] = {{nullptr}};
+  alignas(64) unsigned char tmA[3][2][cgl::kTensorMapBytes];
+  alignas(64) unsigned char tmB[2][3][cgl::kTensorMapBytes];
+
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* graph_u = nullptr;
+
+  // profiling (when `prof` is set, launches are bracketed by events)
+  bool prof = false;
+  std::map<std::string, cgl::KernelStat>* stats = nullptr;
+};
+
+namespace cgl {
+
+int64_t axis_P(const cgl_plan* p, int axis);
+PassGeom geom(const cgl_plan* p, int axis);
+int dev_alloc(cgl_plan* p, void** ptr, size_t bytes);
+cudaError_t prepare_kernels(int dev);
+void free_plan(cgl_plan* p);
+// Arguments of mode pass `mu` of sweep `sw` over the buffers {u, W0, W1, W2}.
+ModePassArgs make_mode_args(const cgl_plan* p, const Sweep& sw, int mu, void* const* bufs);
+// Plan construction; `minimal` skips the workspace, the capture stream and
+// the tensor-core buffers (factors only, for batches).
+int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
+                     double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
+                     int scheme, int precision, void* stream, bool minimal);
+
+}  // namespace cgl

@@ -42,6 +42,27 @@ class cgl_kernel_time(ctypes.Structure):
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class cgl_problem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("bc", ctypes.c_int * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("a1", ctypes.c_double), ("b1", ctypes.c_double), ("a2", ctypes.c_double),
+                ("a3", ctypes.c_double), ("b3", ctypes.c_double), ("a4", ctypes.c_double),
+                ("b4", ctypes.c_double)]
+
+
+def to_cgl_problem(prob) -> cgl_problem:
+    q = cgl_problem()
+    q.d = prob.d
+    for m in range(prob.d):
+        q.n[m] = int(prob.n[m])
+        q.bc[m] = int(prob.bc[m])
+        q.lo[m] = float(prob.lo[m])
+        q.hi[m] = float(prob.hi[m])
+    for k in ("a1", "b1", "a2", "a3", "b3", "a4", "b4"):
+        setattr(q, k, float(getattr(prob, k)))
+    return q
+
+
 _lib = None
 
 
@@ -68,6 +89,13 @@ def load() -> ctypes.CDLL:
         "cgl_profile_step": (I, [P, VP, I64, VP, ctypes.POINTER(cgl_kernel_time), I, ctypes.POINTER(I)]),
         "cgl_rel_error": (I, [VP, VP, I64, I, ctypes.POINTER(D), VP]),
         "cgl_rel_error_noalloc": (I, [VP, VP, I64, I, ctypes.POINTER(D), VP]),
+        "cgl_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(cgl_problem), D, I, I, VP]),
+        "cgl_batch_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(SZ),
+                               ctypes.POINTER(I)]),
+        "cgl_batch_step": (I, [P, VP, I64, VP]),
+        "cgl_batch_last_device_status": (I, [P, VP]),
+        "cgl_batch_destroy": (I, [P]),
+        "cgl_autotune_mode_tile": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "cgl_strerror": (ctypes.c_char_p, [I]),
         "cgl_last_error": (ctypes.c_char_p, []),
     }
@@ -228,3 +256,88 @@ def from_device(t):
     """torch tensor (n_d..n_1) -> complex128 numpy array (n_1..n_d)."""
     import torch
     return t.to(torch.complex128).cpu().numpy().T.copy()
+
+
+def cgl_batch_create(probs, tau, scheme, precision, stream=None):
+    arr = (cgl_problem * len(probs))(*[to_cgl_problem(p) for p in probs])
+    h = ctypes.c_void_p()
+    st = load().cgl_batch_create(ctypes.byref(h), len(probs), arr, float(tau), int(scheme), int(precision),
+                                 _stream_handle(stream))
+    return st, h
+
+
+def cgl_autotune_mode_tile(n, contiguous, precision, nrhs):
+    tb, ms = ctypes.c_int(), ctypes.c_double()
+    check(load().cgl_autotune_mode_tile(int(n), int(contiguous), int(precision), int(nrhs), ctypes.byref(tb),
+                                        ctypes.byref(ms)), "cgl_autotune_mode_tile")
+    return tb.value, ms.value
+
+
+class Batch:
+    """Many independent finite-difference problems advanced together.  The
+    field is one packed complex tensor; instance i occupies
+    [offsets[i], offsets[i] + N_i) in the layout of a single plan."""
+
+    def __init__(self, probs, tau: float, scheme: str, precision: str = "f32", stream=None):
+        self.probs = list(probs)
+        self.prec = PRECISIONS[precision]
+        st, self.handle = cgl_batch_create(self.probs, tau, SCHEMES[scheme], self.prec, stream)
+        check(st, "cgl_batch_create")
+        total = ctypes.c_int64()
+        offs = (ctypes.c_int64 * len(self.probs))()
+        nl = ctypes.c_int()
+        check(load().cgl_batch_info(self.handle, ctypes.byref(total), offs, None, ctypes.byref(nl)),
+              "cgl_batch_info")
+        self.total = total.value
+        self.offsets = list(offs)
+        self.launches_per_step = nl.value
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.complex128 if self.prec == CGL_F64 else torch.complex64
+
+    def pack(self, fields, device="cuda"):
+        """numpy arrays (n_1..n_d), one per instance -> packed device tensor."""
+        import numpy as np
+        import torch
+        flat = np.concatenate([np.ascontiguousarray(U.T).reshape(-1) for U in fields])
+        return torch.from_numpy(flat).to(self.dtype).to(device)
+
+    def unpack(self, t):
+        """packed tensor -> list of complex128 numpy arrays (n_1..n_d)."""
+        import torch
+        host = t.to(torch.complex128).cpu().numpy()
+        out = []
+        for p, off in zip(self.probs, self.offsets):
+            N = int(p.N) if hasattr(p, "N") else int(__import__("numpy").prod(p.n))
+            out.append(host[off:off + N].reshape(tuple(reversed(p.n))).T.copy())
+        return out
+
+    def step(self, u, nsteps: int, stream=None):
+        if not u.is_cuda or not u.is_contiguous() or u.dtype != self.dtype or u.numel() != self.total:
+            raise ValueError("packed field must be a contiguous %s CUDA tensor of %d values" % (self.dtype,
+                                                                                               self.total))
+        check(load().cgl_batch_step(self.handle, ctypes.c_void_p(u.data_ptr()), int(nsteps),
+                                    _stream_handle(stream)), "cgl_batch_step")
+        return u
+
+    def device_status(self, stream=None) -> int:
+        return load().cgl_batch_last_device_status(self.handle, _stream_handle(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().cgl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -76,3 +76,20 @@ def test_null_arguments(lib):
     assert lib.cgl_plan_destroy(None) == nat.CGL_OK
     assert lib.cgl_rel_error(None, None, 4, 0, None, None) == nat.CGL_EINVAL
     assert lib.cgl_plan_info(None, None, None, None) == nat.CGL_EINVAL
+
+
+def test_batch_validation_before_any_cuda_call(lib):
+    import ctypes
+    probs = [nat.to_cgl_problem(type("P", (), dict(d=2, n=(8, 8), bc=(2, 2), lo=(0, 0), hi=(1, 1), a1=1.0, b1=0.0,
+                                                   a2=1.0, a3=-1.0, b3=1.0, a4=0.0, b4=0.0))())]
+    arr = (nat.cgl_problem * 1)(*probs)
+    h = ctypes.c_void_p()
+    assert lib.cgl_batch_create(ctypes.byref(h), 1, arr, 0.01, nat.CGL_LAWSON4, nat.CGL_F32, None) \
+        == nat.CGL_EUNSUPPORTED  # periodic
+    assert lib.cgl_batch_create(ctypes.byref(h), 0, arr, 0.01, nat.CGL_LAWSON4, nat.CGL_F32, None) == nat.CGL_EINVAL
+    assert lib.cgl_batch_create(ctypes.byref(h), 1, arr, 0.01, nat.CGL_RK4, nat.CGL_F32, None) \
+        == nat.CGL_EUNSUPPORTED
+    assert lib.cgl_batch_create(ctypes.byref(h), 1, arr, 0.01, nat.CGL_LAWSON4, nat.CGL_BF16X3, None) \
+        == nat.CGL_EUNSUPPORTED
+    assert lib.cgl_batch_destroy(None) == nat.CGL_OK
+    assert lib.cgl_autotune_mode_tile(1, 1, 0, 1, None, None) == nat.CGL_EINVAL
