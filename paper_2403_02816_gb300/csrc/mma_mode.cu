@@ -319,14 +319,56 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       ostride = 1;
     }
     const uint32_t lane_addr = static_cast<uint32_t>(warp * 32) << 16;
+    // strided fibers (modes > 1): stage 16 output rows x 128 fibers in the
+    // (now idle) pipeline buffers and store them as 16-byte chunks along the
+    // contiguous fiber index
+    const int64_t tile0 = p0 + a.P * (int64_t)n * q0;
     for (int i0 = 0; i0 < n; i0 += 16) {
       uint32_t rm[16], rc[16];
       tmem_ld16(d_main + lane_addr + i0, rm);
       tmem_ld16(d_corr + lane_addr + i0, rc);
-      if (!valid) continue;
       float v[16];
 #pragma unroll
       for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(rm[t]) + __uint_as_float(rc[t]);
+      if (a.a_mn) {
+        if (a.out_fp32) {
+          float* so = reinterpret_cast<float*>(base);  // [16 rows][128 fibers]
+#pragma unroll
+          for (int t = 0; t < 16; ++t) so[t * kMmaM + m] = v[t];
+          __syncthreads();
+          float* o = reinterpret_cast<float*>(a.out[rhs]) + (int64_t)half * a.N + tile0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int c = threadIdx.x + k * kMmaThreads;  // float4 chunk: row c / 32, column (c % 32) * 4
+            const int row = c >> 5, col = (c & 31) * 4;
+            *reinterpret_cast<float4*>(o + a.P * (i0 + row) + col) =
+                *reinterpret_cast<const float4*>(so + row * kMmaM + col);
+          }
+          __syncthreads();
+        } else {
+          __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(base);  // [3 splits][16 rows][128 fibers]
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            __nv_bfloat16 sh, sm, sl;
+            split3(v[t], sh, sm, sl);
+            so[(0 * 16 + t) * kMmaM + m] = sh;
+            so[(1 * 16 + t) * kMmaM + m] = sm;
+            so[(2 * 16 + t) * kMmaM + m] = sl;
+          }
+          __syncthreads();
+          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out[rhs]);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const int c = threadIdx.x + k * kMmaThreads;  // 16-byte chunk of 8 fibers
+            const int s = c >> 8, row = (c >> 4) & 15, col = (c & 15) * 8;
+            *reinterpret_cast<uint4*>(o + (int64_t)(s * 2 + half) * a.N + tile0 + a.P * (i0 + row) + col) =
+                *reinterpret_cast<const uint4*>(so + (s * 16 + row) * kMmaM + col);
+          }
+          __syncthreads();
+        }
+        continue;
+      }
+      if (!valid) continue;
       if (a.out_fp32) {
         float* o = reinterpret_cast<float*>(a.out[rhs]) + (int64_t)half * a.N;
         if (!a.a_mn) {
