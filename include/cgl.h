@@ -245,6 +245,53 @@ int cgl_batch_destroy(cgl_batch* batch);
  */
 int cgl_autotune_mode_tile(int n, int contiguous, int precision, int nrhs, int* tb, double* ms);
 
+/* ------------------------------------------------------------------------
+ * Learned corrector of a coarse periodic step (2D).  The corrected step is
+ * u_{n+1} = C(u_n) + N(x) with C one coarse step of a plan (e.g. Lawson4,
+ * eq. lawson4, in CGL_F32) and N a residual CNN: 3x3 convolutions with
+ * circular padding, 9 -> hidden -> ... -> hidden -> 2 channels, ReLU between
+ * layers; x = 9 planes (Re, Im of C(u_n); Re, Im of u_n; a1, b1, a2, a3, b3 as
+ * constant planes).  BF16 weights in every convolution (FP32 masters), FP32
+ * accumulation, Adam on the masters.  The paper has no learned part; this
+ * follows the fine method (the plain integrator at a smaller step) as the
+ * training target and as the judge of the corrected error.
+ *
+ * Field arguments are complex64 device arrays [P][H][W] (W fastest, the
+ * layout of a 2D plan field with n_1 = W); `params` is float [P][5]
+ * (a1, b1, a2, a3, b3); `idx` (device int[batch], may be NULL for 0..batch-1)
+ * selects the samples of a batch.  Weights are a flat float array: per layer
+ * w[Cout][Cin][3][3] then b[Cout].
+ * ---------------------------------------------------------------------- */
+typedef struct cgl_corrector cgl_corrector;
+
+/* height, width: multiples of 16; hidden in 1..32; layers in 2..16;
+ * max_batch >= 1 (sizes the activation buffers).  Weights He-uniform from
+ * splitmix64(seed) (last layer x 0.1), zero biases.  Synchronous. */
+int cgl_corrector_create(cgl_corrector** out, int height, int width, int hidden, int layers,
+                         int max_batch, uint64_t seed, void* stream);
+int cgl_corrector_num_params(const cgl_corrector* c, int64_t* count);
+/* Host FP32 weights in/out (count must equal num_params); set resets Adam. */
+int cgl_corrector_set_weights(cgl_corrector* c, const float* host, int64_t count);
+int cgl_corrector_get_weights(const cgl_corrector* c, float* host, int64_t count);
+/* N(x) into the device float array out[batch][2][H][W].  Asynchronous. */
+int cgl_corrector_forward(cgl_corrector* c, const void* coarse, const void* un, const float* params,
+                          const int* idx, int batch, float* out, void* stream);
+/* Loss = mean over batch x 2 x H x W of (C(u_n) + N(x) - target)^2 and its
+ * gradient w.r.t. the weights (host float[num_params], may be NULL); *loss
+ * (may be NULL).  Synchronous when grads_host or loss is given. */
+int cgl_corrector_gradients(cgl_corrector* c, const void* coarse, const void* un, const void* target,
+                            const float* params, const int* idx, int batch, float* grads_host,
+                            double* loss, void* stream);
+/* One Adam step (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the loss
+ * above; *loss (may be NULL) is the loss before the step. */
+int cgl_corrector_train_step(cgl_corrector* c, const void* coarse, const void* un, const void* target,
+                             const float* params, const int* idx, int batch, float lr, double* loss,
+                             void* stream);
+/* u_out[b] = coarse[b] + N(x_b), complex64 [batch][H][W].  Asynchronous. */
+int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, const float* params,
+                        int batch, void* u_out, void* stream);
+int cgl_corrector_destroy(cgl_corrector* c);
+
 /*
  * Allocation-free variant of cgl_rel_error (the paper has no counterpart:
  * this entry point exists for callers of the library, not for the method).

@@ -1,0 +1,596 @@
+// Learned residual corrector for the coarse periodic step: training and
+// inference kernels.
+//
+// The corrected step is u_{n+1} = C(u_n) + N(x): C a coarse Lawson4 step
+// (eq. lawson4), x = 9 planes (Re, Im of C(u_n); Re, Im of u_n; the
+// parameters a1, b1, a2, a3, b3 as constant planes), N a stack of 3x3
+// convolutions with circular padding (the periodic boundary), ReLU between
+// layers, 2 output planes.  Weights: FP32 masters, BF16 copies used by every
+// convolution, FP32 accumulation; Adam (Kingma & Ba 2015) on the masters.
+//
+// Activations are NCHW FP32 (W fastest).  A 3x3 convolution is an implicit
+// GEMM per 16x16 pixel tile: the tile and its one-pixel circular halo for all
+// input channels, and the weights of all output channels (as FP32, output
+// channel fastest for 128-bit loads), sit in shared memory; each thread owns
+// one pixel and accumulates every output channel.  The backward pass w.r.t.
+// the input is the same convolution with the kernel flipped and the channel
+// roles swapped; the weight gradient is a per-tile reduction finished with
+// atomics.  The layers here are 9..32 channels wide: about 144 flop per byte
+// of activation traffic, so these convolutions are bounded by memory and
+// shared-memory bandwidth, not by arithmetic.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "plan.cuh"
+
+using namespace cgl;
+
+namespace cgl {
+
+constexpr int kTile = 16;
+constexpr int kHalo = kTile + 2;
+constexpr int kConvThreads = kTile * kTile;
+constexpr int kMaxCh = 32;
+
+// ------------------------------------------------------------------ kernels
+
+// x[b][c][i][j] from complex64 coarse results / states [P][H][W] selected by
+// idx (or b itself) and parameters [P][5].
+__global__ void features_kernel(const float2* __restrict__ coarse, const float2* __restrict__ un,
+                                const float* __restrict__ params, const int* __restrict__ idx, int B, int H, int W,
+                                float* __restrict__ x) {
+  const int64_t HW = (int64_t)H * W;
+  const int64_t total = (int64_t)B * HW;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / HW);
+    const int64_t p = e - (int64_t)b * HW;
+    const int src = idx ? idx[b] : b;
+    const float2 c = coarse[(int64_t)src * HW + p];
+    const float2 u = un[(int64_t)src * HW + p];
+    float* xb = x + (int64_t)b * 9 * HW + p;
+    xb[0 * HW] = c.x;
+    xb[1 * HW] = c.y;
+    xb[2 * HW] = u.x;
+    xb[3 * HW] = u.y;
+    for (int k = 0; k < 5; ++k) xb[(4 + k) * HW] = params[(int64_t)src * 5 + k];
+  }
+}
+
+// y = conv3x3(x, w) + bias (optional ReLU).  w: BF16 [Cout][Cin][3][3].
+// Grid: (W/16, H/16, B).  COUTP = Cout rounded up to a multiple of 4.
+template <int COUTP>
+__global__ void __launch_bounds__(kConvThreads) conv3x3_kernel(const float* __restrict__ x,
+                                                               const __nv_bfloat16* __restrict__ w,
+                                                               const float* __restrict__ bias, float* __restrict__ y,
+                                                               int Cin, int Cout, int H, int W, int relu) {
+  extern __shared__ __align__(16) float smem[];
+  float* sw = smem;                        // [Cin][9][COUTP]
+  float* sx = smem + Cin * 9 * COUTP;      // [Cin][18][18]
+  const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+  const int j0 = blockIdx.x * kTile, i0 = blockIdx.y * kTile, b = blockIdx.z;
+  const int64_t HW = (int64_t)H * W;
+  for (int e = threadIdx.x; e < Cin * 9 * COUTP; e += kConvThreads) {
+    const int co = e % COUTP, k = (e / COUTP) % 9, ci = e / (9 * COUTP);
+    sw[e] = co < Cout ? __bfloat162float(w[((int64_t)co * Cin + ci) * 9 + k]) : 0.f;
+  }
+  const float* xb = x + (int64_t)b * Cin * HW;
+  for (int e = threadIdx.x; e < Cin * kHalo * kHalo; e += kConvThreads) {
+    const int c = e % kHalo, r = (e / kHalo) % kHalo, ci = e / (kHalo * kHalo);
+    const int gi = (i0 + r - 1 + H) % H, gj = (j0 + c - 1 + W) % W;
+    sx[e] = xb[ci * HW + (int64_t)gi * W + gj];
+  }
+  __syncthreads();
+  float acc[COUTP];
+#pragma unroll
+  for (int o = 0; o < COUTP; ++o) acc[o] = 0.f;
+  for (int ci = 0; ci < Cin; ++ci) {
+    const float* sxc = sx + ci * kHalo * kHalo;
+    const float4* swc = reinterpret_cast<const float4*>(sw + ci * 9 * COUTP);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float xv = sxc[(ty + k / 3) * kHalo + tx + k % 3];
+#pragma unroll
+      for (int o4 = 0; o4 < COUTP / 4; ++o4) {
+        const float4 wv = swc[k * (COUTP / 4) + o4];
+        acc[4 * o4 + 0] = fmaf(xv, wv.x, acc[4 * o4 + 0]);
+        acc[4 * o4 + 1] = fmaf(xv, wv.y, acc[4 * o4 + 1]);
+        acc[4 * o4 + 2] = fmaf(xv, wv.z, acc[4 * o4 + 2]);
+        acc[4 * o4 + 3] = fmaf(xv, wv.w, acc[4 * o4 + 3]);
+      }
+    }
+  }
+  float* yb = y + (int64_t)b * Cout * HW + (int64_t)(i0 + ty) * W + (j0 + tx);
+#pragma unroll
+  for (int o = 0; o < COUTP; ++o) {
+    if (o < Cout) {
+      float v = acc[o] + (bias ? bias[o] : 0.f);
+      if (relu) v = fmaxf(v, 0.f);
+      yb[o * HW] = v;
+    }
+  }
+}
+
+// dw[co][ci][k] += sum over the CTA's tiles of dy[co][p] x[ci][p + tap k];
+// db[co] += sum dy[co].  Grid: (tiles per image / tiles_per_cta, B).
+__global__ void __launch_bounds__(256) conv3x3_wgrad_kernel(const float* __restrict__ x,
+                                                            const float* __restrict__ dy, float* __restrict__ dw,
+                                                            float* __restrict__ db, int Cin, int Cout, int H, int W,
+                                                            int tiles_per_cta) {
+  extern __shared__ __align__(16) float smem[];
+  float* sx = smem;                           // [Cin][18][18]
+  float* sdy = smem + Cin * kHalo * kHalo;    // [Cout][16][16]
+  const int b = blockIdx.y;
+  const int64_t HW = (int64_t)H * W;
+  const int tiles_x = W / kTile;
+  const int ntiles = tiles_x * (H / kTile);
+  const int pairs = Cin * Cout;
+  constexpr int kMaxPairsPerThread = (kMaxCh * kMaxCh + 255) / 256;
+  float acc[kMaxPairsPerThread][9];
+  float bacc = 0.f;
+#pragma unroll
+  for (int q = 0; q < kMaxPairsPerThread; ++q)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[q][k] = 0.f;
+  for (int t = 0; t < tiles_per_cta; ++t) {
+    const int tile = blockIdx.x * tiles_per_cta + t;
+    if (tile >= ntiles) break;
+    const int i0 = (tile / tiles_x) * kTile, j0 = (tile % tiles_x) * kTile;
+    const float* xb = x + (int64_t)b * Cin * HW;
+    for (int e = threadIdx.x; e < Cin * kHalo * kHalo; e += 256) {
+      const int c = e % kHalo, r = (e / kHalo) % kHalo, ci = e / (kHalo * kHalo);
+      const int gi = (i0 + r - 1 + H) % H, gj = (j0 + c - 1 + W) % W;
+      sx[e] = xb[ci * HW + (int64_t)gi * W + gj];
+    }
+    const float* dyb = dy + (int64_t)b * Cout * HW;
+    for (int e = threadIdx.x; e < Cout * kTile * kTile; e += 256) {
+      const int c = e % kTile, r = (e / kTile) % kTile, co = e / (kTile * kTile);
+      sdy[e] = dyb[co * HW + (int64_t)(i0 + r) * W + j0 + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kMaxPairsPerThread; ++q) {
+      const int pr = threadIdx.x + q * 256;
+      if (pr < pairs) {
+        const int co = pr / Cin, ci = pr % Cin;
+        const float* sxc = sx + ci * kHalo * kHalo;
+        const float* sdc = sdy + co * kTile * kTile;
+        for (int r = 0; r < kTile; ++r) {
+          // sliding 3x3 window along the row
+          float w00 = sxc[r * kHalo + 0], w01 = sxc[r * kHalo + 1];
+          float w10 = sxc[(r + 1) * kHalo + 0], w11 = sxc[(r + 1) * kHalo + 1];
+          float w20 = sxc[(r + 2) * kHalo + 0], w21 = sxc[(r + 2) * kHalo + 1];
+          for (int c = 0; c < kTile; ++c) {
+            const float w02 = sxc[r * kHalo + c + 2], w12 = sxc[(r + 1) * kHalo + c + 2],
+                        w22 = sxc[(r + 2) * kHalo + c + 2];
+            const float g = sdc[r * kTile + c];
+            acc[q][0] = fmaf(g, w00, acc[q][0]);
+            acc[q][1] = fmaf(g, w01, acc[q][1]);
+            acc[q][2] = fmaf(g, w02, acc[q][2]);
+            acc[q][3] = fmaf(g, w10, acc[q][3]);
+            acc[q][4] = fmaf(g, w11, acc[q][4]);
+            acc[q][5] = fmaf(g, w12, acc[q][5]);
+            acc[q][6] = fmaf(g, w20, acc[q][6]);
+            acc[q][7] = fmaf(g, w21, acc[q][7]);
+            acc[q][8] = fmaf(g, w22, acc[q][8]);
+            w00 = w01; w01 = w02;
+            w10 = w11; w11 = w12;
+            w20 = w21; w21 = w22;
+          }
+        }
+      }
+    }
+    if (threadIdx.x < Cout) {
+      const float* sdc = sdy + threadIdx.x * kTile * kTile;
+      for (int p = 0; p < kTile * kTile; ++p) bacc += sdc[p];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kMaxPairsPerThread; ++q) {
+    const int pr = threadIdx.x + q * 256;
+    if (pr < pairs) {
+      const int co = pr / Cin, ci = pr % Cin;
+      for (int k = 0; k < 9; ++k) atomicAdd(&dw[((int64_t)co * Cin + ci) * 9 + k], acc[q][k]);
+    }
+  }
+  if (threadIdx.x < Cout) atomicAdd(&db[threadIdx.x], bacc);
+}
+
+// dy *= (a > 0)
+__global__ void relu_backward_kernel(float* __restrict__ dy, const float* __restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!(a[i] > 0.f)) dy[i] = 0.f;
+}
+
+// r = C(u_n) + out - target (complex64 [P] selected by idx); dout = 2 r / count;
+// loss partial sums in FP64.
+__global__ void loss_kernel(const float* __restrict__ out, const float2* __restrict__ coarse,
+                            const float2* __restrict__ target, const int* __restrict__ idx, int B, int64_t HW,
+                            float* __restrict__ dout, double* __restrict__ loss_sum) {
+  const double inv = 1.0 / (2.0 * (double)B * (double)HW);
+  double s = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)B * HW;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / HW);
+    const int64_t p = e - (int64_t)b * HW;
+    const int src = idx ? idx[b] : b;
+    const float2 c = coarse[(int64_t)src * HW + p], t = target[(int64_t)src * HW + p];
+    const float* ob = out + (int64_t)b * 2 * HW + p;
+    const float rr = c.x + ob[0] - t.x, ri = c.y + ob[HW] - t.y;
+    s += (double)rr * rr + (double)ri * ri;
+    float* db = dout + (int64_t)b * 2 * HW + p;
+    db[0] = (float)(2.0 * inv) * rr;
+    db[HW] = (float)(2.0 * inv) * ri;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, s * inv);
+}
+
+// Adam on FP32 masters, BF16 copies refreshed.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, __nv_bfloat16* __restrict__ pbf, int64_t n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pbf[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = __float2bfloat16_rn(p[i]);
+}
+
+// wr[ci][co][8-k] = w[co][ci][k]: the kernel of the input-gradient convolution.
+__global__ void flip_weights_kernel(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wr, int Cin,
+                                    int Cout) {
+  const int n = Cin * Cout * 9;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int k = e % 9, ci = (e / 9) % Cin, co = e / (9 * Cin);
+    wr[((int64_t)ci * Cout + co) * 9 + (8 - k)] = w[e];
+  }
+}
+
+// u = C(u_n) + correction
+__global__ void residual_add_kernel(const float2* __restrict__ coarse, const float* __restrict__ out, int B,
+                                    int64_t HW, float2* __restrict__ u) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)B * HW;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / HW);
+    const int64_t p = e - (int64_t)b * HW;
+    const float2 c = coarse[e];
+    const float* ob = out + (int64_t)b * 2 * HW + p;
+    u[e] = make_float2(c.x + ob[0], c.y + ob[HW]);
+  }
+}
+
+}  // namespace cgl
+
+// ------------------------------------------------------------------ host side
+
+struct cgl_corrector {
+  int dev = 0;
+  int H = 0, W = 0, hidden = 0, nlayers = 0, max_batch = 0;
+  struct Layer {
+    int cin, cout, relu;
+    int64_t w_off, b_off;
+  };
+  std::vector<Layer> layers;
+  int64_t nparams = 0;
+  float* master = nullptr;
+  __nv_bfloat16* wbf = nullptr;
+  __nv_bfloat16* wflip = nullptr;
+  float* grad = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  int64_t t = 0;
+  std::vector<float*> acts;  // acts[0] = features, acts[l+1] = output of layer l
+  float* dbuf[2] = {nullptr, nullptr};
+  double* loss = nullptr;
+  std::vector<void*> allocations;
+};
+
+namespace {
+
+int corr_alloc(cgl_corrector* c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(CGL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->allocations.push_back(*p);
+  return CGL_OK;
+}
+
+void free_corrector(cgl_corrector* c) {
+  if (!c) return;
+  for (void* a : c->allocations) cudaFree(a);
+  delete c;
+}
+
+int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 32); }
+
+size_t conv_smem(int cin, int coutp) { return (size_t)(cin * 9 * coutp + cin * kHalo * kHalo) * sizeof(float); }
+
+cudaError_t launch_conv(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int B, int cin, int cout,
+                        int H, int W, int relu, cudaStream_t s) {
+  dim3 grid(W / kTile, H / kTile, B);
+  if (cout <= 4) {
+    conv3x3_kernel<4><<<grid, kConvThreads, conv_smem(cin, 4), s>>>(x, w, bias, y, cin, cout, H, W, relu);
+  } else if (cout <= 12) {
+    conv3x3_kernel<12><<<grid, kConvThreads, conv_smem(cin, 12), s>>>(x, w, bias, y, cin, cout, H, W, relu);
+  } else {
+    conv3x3_kernel<32><<<grid, kConvThreads, conv_smem(cin, 32), s>>>(x, w, bias, y, cin, cout, H, W, relu);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_corrector_kernels() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(conv3x3_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)))
+    return e;
+  if ((e = cudaFuncSetAttribute(conv3x3_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)))
+    return e;
+  if ((e = cudaFuncSetAttribute(conv3x3_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)))
+    return e;
+  return cudaFuncSetAttribute(conv3x3_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+}
+
+// splitmix64 (Steele, Lea & Flood 2014): a counter-based generator for the
+// initial weights.
+uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+int forward_pass(cgl_corrector* c, int B, cudaStream_t s) {
+  for (int l = 0; l < c->nlayers; ++l) {
+    const auto& L = c->layers[l];
+    cudaError_t e = launch_conv(c->acts[l], c->wbf + L.w_off, c->master + L.b_off, c->acts[l + 1], B, L.cin, L.cout,
+                                c->H, c->W, L.relu, s);
+    if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("conv forward: ") + cudaGetErrorString(e));
+  }
+  return CGL_OK;
+}
+
+int check_batch(cgl_corrector* c, int B) {
+  if (!c) return fail(CGL_EINVAL, "corrector is NULL");
+  if (B < 1 || B > c->max_batch) return fail(CGL_EINVAL, "batch must be in 1..max_batch");
+  return CGL_OK;
+}
+
+// features -> forward -> loss -> backward (gradients in c->grad); loss to *loss_out.
+int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const void* target, const float* params,
+                  const int* idx, int B, double* loss_out, cudaStream_t s) {
+  const int64_t HW = (int64_t)c->H * c->W;
+  features_kernel<<<grid_for(B * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, idx, B, c->H,
+                                                   c->W, c->acts[0]);
+  CUDA_TRY(cudaGetLastError());
+  int st = forward_pass(c, B, s);
+  if (st) return st;
+  CUDA_TRY(cudaMemsetAsync(c->loss, 0, sizeof(double), s));
+  CUDA_TRY(cudaMemsetAsync(c->grad, 0, c->nparams * sizeof(float), s));
+  loss_kernel<<<grid_for(B * HW), 256, 0, s>>>(c->acts[c->nlayers], (const float2*)coarse, (const float2*)target, idx,
+                                               B, HW, c->dbuf[0], c->loss);
+  CUDA_TRY(cudaGetLastError());
+  int cur = 0;
+  const int tiles = (c->H / kTile) * (c->W / kTile);
+  const int tiles_per_cta = std::max(1, tiles / 4);
+  for (int l = c->nlayers - 1; l >= 0; --l) {
+    const auto& L = c->layers[l];
+    float* dy = c->dbuf[cur];
+    if (l < c->nlayers - 1) {
+      relu_backward_kernel<<<grid_for(B * L.cout * HW), 256, 0, s>>>(dy, c->acts[l + 1], (int64_t)B * L.cout * HW);
+      CUDA_TRY(cudaGetLastError());
+    }
+    dim3 wg((tiles + tiles_per_cta - 1) / tiles_per_cta, B);
+    const size_t wsm = (size_t)(L.cin * kHalo * kHalo + L.cout * kTile * kTile) * sizeof(float);
+    conv3x3_wgrad_kernel<<<wg, 256, wsm, s>>>(c->acts[l], dy, c->grad + L.w_off, c->grad + L.b_off, L.cin, L.cout,
+                                              c->H, c->W, tiles_per_cta);
+    CUDA_TRY(cudaGetLastError());
+    if (l > 0) {
+      flip_weights_kernel<<<grid_for(L.cin * L.cout * 9), 256, 0, s>>>(c->wbf + L.w_off, c->wflip, L.cin, L.cout);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(launch_conv(dy, c->wflip, nullptr, c->dbuf[1 - cur], B, L.cout, L.cin, c->H, c->W, 0, s));
+      cur = 1 - cur;
+    }
+  }
+  if (loss_out) {
+    CUDA_TRY(cudaMemcpyAsync(loss_out, c->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return CGL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cgl_corrector_create(cgl_corrector** out, int height, int width, int hidden, int layers, int max_batch,
+                         uint64_t seed, void* stream) {
+  if (!out) return fail(CGL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (height < kTile || width < kTile || height % kTile || width % kTile)
+    return fail(CGL_EINVAL, "height and width must be positive multiples of 16");
+  if (hidden < 1 || hidden > kMaxCh || layers < 2 || layers > 16 || max_batch < 1)
+    return fail(CGL_EINVAL, "hidden in 1..32, layers in 2..16, max_batch >= 1");
+  cudaError_t e = prepare_corrector_kernels();
+  if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  cgl_corrector* c = new cgl_corrector();
+  cudaGetDevice(&c->dev);
+  c->H = height;
+  c->W = width;
+  c->hidden = hidden;
+  c->nlayers = layers;
+  c->max_batch = max_batch;
+  int64_t off = 0;
+  int maxc = 9;
+  for (int l = 0; l < layers; ++l) {
+    cgl_corrector::Layer L;
+    L.cin = l == 0 ? 9 : hidden;
+    L.cout = l == layers - 1 ? 2 : hidden;
+    L.relu = l < layers - 1;
+    L.w_off = off;
+    off += (int64_t)L.cout * L.cin * 9;
+    L.b_off = off;
+    off += L.cout;
+    maxc = std::max(maxc, L.cout);
+    c->layers.push_back(L);
+  }
+  c->nparams = off;
+  int st = CGL_OK;
+  const int64_t HW = (int64_t)height * width;
+  st = corr_alloc(c, (void**)&c->master, off * sizeof(float));
+  if (!st) st = corr_alloc(c, (void**)&c->wbf, off * sizeof(__nv_bfloat16));
+  if (!st) st = corr_alloc(c, (void**)&c->wflip, (size_t)kMaxCh * kMaxCh * 9 * sizeof(__nv_bfloat16));
+  if (!st) st = corr_alloc(c, (void**)&c->grad, off * sizeof(float));
+  if (!st) st = corr_alloc(c, (void**)&c->m, off * sizeof(float));
+  if (!st) st = corr_alloc(c, (void**)&c->v, off * sizeof(float));
+  if (!st) st = corr_alloc(c, (void**)&c->loss, sizeof(double));
+  for (int l = 0; !st && l <= layers; ++l) {
+    const int ch = l == 0 ? 9 : c->layers[l - 1].cout;
+    float* a = nullptr;
+    st = corr_alloc(c, (void**)&a, (size_t)max_batch * ch * HW * sizeof(float));
+    c->acts.push_back(a);
+  }
+  for (int k = 0; !st && k < 2; ++k) st = corr_alloc(c, (void**)&c->dbuf[k], (size_t)max_batch * maxc * HW * sizeof(float));
+  if (!st) {
+    // He-uniform initial weights from splitmix64(seed, index); last layer
+    // scaled by 0.1 so the untrained correction starts small; zero biases.
+    std::vector<float> h(off, 0.f);
+    for (int l = 0; l < layers; ++l) {
+      const auto& L = c->layers[l];
+      const double bound = std::sqrt(6.0 / (L.cin * 9.0)) * (l == layers - 1 ? 0.1 : 1.0);
+      for (int64_t k = 0; k < (int64_t)L.cout * L.cin * 9; ++k) {
+        const double u = (splitmix64(seed ^ (uint64_t)(L.w_off + k) * 0x2545F4914F6CDD1Dull) >> 11) * (1.0 / 9007199254740992.0);
+        h[L.w_off + k] = (float)((2.0 * u - 1.0) * bound);
+      }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(c->master, h.data(), off * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(c->m, 0, off * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(c->v, 0, off * sizeof(float), s) != cudaSuccess)
+      st = fail(CGL_ECUDA, "corrector initialisation");
+    if (!st) {
+      to_bf16_kernel<<<grid_for(off), 256, 0, s>>>(c->master, c->wbf, off);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        st = fail(CGL_ECUDA, "corrector initialisation");
+    }
+  }
+  if (st) {
+    free_corrector(c);
+    return st;
+  }
+  *out = c;
+  return CGL_OK;
+}
+
+int cgl_corrector_num_params(const cgl_corrector* c, int64_t* count) {
+  if (!c || !count) return fail(CGL_EINVAL, "NULL argument");
+  *count = c->nparams;
+  return CGL_OK;
+}
+
+int cgl_corrector_set_weights(cgl_corrector* c, const float* host, int64_t count) {
+  if (!c || !host || count != c->nparams) return fail(CGL_EINVAL, "weights: NULL or wrong count");
+  CUDA_TRY(cudaMemcpy(c->master, host, count * sizeof(float), cudaMemcpyHostToDevice));
+  to_bf16_kernel<<<grid_for(count), 256>>>(c->master, c->wbf, count);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemset(c->m, 0, count * sizeof(float)));
+  CUDA_TRY(cudaMemset(c->v, 0, count * sizeof(float)));
+  CUDA_TRY(cudaDeviceSynchronize());
+  c->t = 0;
+  return CGL_OK;
+}
+
+int cgl_corrector_get_weights(const cgl_corrector* c, float* host, int64_t count) {
+  if (!c || !host || count != c->nparams) return fail(CGL_EINVAL, "weights: NULL or wrong count");
+  CUDA_TRY(cudaMemcpy(host, c->master, count * sizeof(float), cudaMemcpyDeviceToHost));
+  return CGL_OK;
+}
+
+int cgl_corrector_forward(cgl_corrector* c, const void* coarse, const void* un, const float* params, const int* idx,
+                          int batch, float* out, void* stream) {
+  int st = check_batch(c, batch);
+  if (st) return st;
+  if (!coarse || !un || !params || !out) return fail(CGL_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t HW = (int64_t)c->H * c->W;
+  features_kernel<<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, idx, batch,
+                                                       c->H, c->W, c->acts[0]);
+  CUDA_TRY(cudaGetLastError());
+  if ((st = forward_pass(c, batch, s))) return st;
+  CUDA_TRY(cudaMemcpyAsync(out, c->acts[c->nlayers], (size_t)batch * 2 * HW * sizeof(float), cudaMemcpyDeviceToDevice,
+                           s));
+  return CGL_OK;
+}
+
+int cgl_corrector_gradients(cgl_corrector* c, const void* coarse, const void* un, const void* target,
+                            const float* params, const int* idx, int batch, float* grads_host, double* loss,
+                            void* stream) {
+  int st = check_batch(c, batch);
+  if (st) return st;
+  if (!coarse || !un || !target || !params) return fail(CGL_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = loss_backward(c, coarse, un, target, params, idx, batch, loss, s))) return st;
+  if (grads_host) {
+    CUDA_TRY(cudaMemcpyAsync(grads_host, c->grad, c->nparams * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return CGL_OK;
+}
+
+int cgl_corrector_train_step(cgl_corrector* c, const void* coarse, const void* un, const void* target,
+                             const float* params, const int* idx, int batch, float lr, double* loss, void* stream) {
+  int st = check_batch(c, batch);
+  if (st) return st;
+  if (!coarse || !un || !target || !params || !(lr > 0.f)) return fail(CGL_EINVAL, "NULL argument or lr <= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = loss_backward(c, coarse, un, target, params, idx, batch, loss, s))) return st;
+  c->t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)c->t), c2 = 1.f - std::pow(b2, (float)c->t);
+  adam_kernel<<<grid_for(c->nparams), 256, 0, s>>>(c->master, c->grad, c->m, c->v, c->wbf, c->nparams, lr, b1, b2,
+                                                   1e-8f, c1, c2);
+  CUDA_TRY(cudaGetLastError());
+  return CGL_OK;
+}
+
+int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, const float* params, int batch,
+                        void* u_out, void* stream) {
+  int st = check_batch(c, batch);
+  if (st) return st;
+  if (!coarse || !un || !params || !u_out) return fail(CGL_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t HW = (int64_t)c->H * c->W;
+  features_kernel<<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, nullptr,
+                                                       batch, c->H, c->W, c->acts[0]);
+  CUDA_TRY(cudaGetLastError());
+  if ((st = forward_pass(c, batch, s))) return st;
+  residual_add_kernel<<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, c->acts[c->nlayers], batch, HW,
+                                                           (float2*)u_out);
+  CUDA_TRY(cudaGetLastError());
+  return CGL_OK;
+}
+
+int cgl_corrector_destroy(cgl_corrector* c) {
+  if (!c) return CGL_OK;
+  cudaSetDevice(c->dev);
+  free_corrector(c);
+  return CGL_OK;
+}
+
+}  // extern "C"

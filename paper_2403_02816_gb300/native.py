@@ -96,6 +96,16 @@ def load() -> ctypes.CDLL:
         "cgl_batch_last_device_status": (I, [P, VP]),
         "cgl_batch_destroy": (I, [P]),
         "cgl_autotune_mode_tile": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "cgl_corrector_create": (I, [ctypes.POINTER(P), I, I, I, I, I, ctypes.c_uint64, VP]),
+        "cgl_corrector_num_params": (I, [P, ctypes.POINTER(I64)]),
+        "cgl_corrector_set_weights": (I, [P, ctypes.POINTER(ctypes.c_float), I64]),
+        "cgl_corrector_get_weights": (I, [P, ctypes.POINTER(ctypes.c_float), I64]),
+        "cgl_corrector_forward": (I, [P, VP, VP, VP, VP, I, VP, VP]),
+        "cgl_corrector_gradients": (I, [P, VP, VP, VP, VP, VP, I, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(D), VP]),
+        "cgl_corrector_train_step": (I, [P, VP, VP, VP, VP, VP, I, ctypes.c_float, ctypes.POINTER(D), VP]),
+        "cgl_corrector_apply": (I, [P, VP, VP, VP, I, VP, VP]),
+        "cgl_corrector_destroy": (I, [P]),
         "cgl_strerror": (ctypes.c_char_p, [I]),
         "cgl_last_error": (ctypes.c_char_p, []),
     }
@@ -328,6 +338,87 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             load().cgl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Corrector:
+    """Residual CNN corrector of a coarse 2D periodic step (cgl_corrector_*).
+    Fields are complex64 CUDA tensors [P, H, W]; params float32 [P, 5];
+    idx int32 [batch] (or None)."""
+
+    def __init__(self, height, width, hidden=32, layers=6, max_batch=32, seed=2403028164, stream=None):
+        self.handle = ctypes.c_void_p()
+        check(load().cgl_corrector_create(ctypes.byref(self.handle), int(height), int(width), int(hidden),
+                                          int(layers), int(max_batch), ctypes.c_uint64(seed),
+                                          _stream_handle(stream)), "cgl_corrector_create")
+        n = ctypes.c_int64()
+        check(load().cgl_corrector_num_params(self.handle, ctypes.byref(n)), "cgl_corrector_num_params")
+        self.nparams = n.value
+        self.hw = (int(height), int(width))
+
+    def set_weights(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        check(load().cgl_corrector_set_weights(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               a.size), "cgl_corrector_set_weights")
+
+    def get_weights(self):
+        import numpy as np
+        a = np.empty(self.nparams, dtype=np.float32)
+        check(load().cgl_corrector_get_weights(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               a.size), "cgl_corrector_get_weights")
+        return a
+
+    def forward(self, coarse, un, params, idx=None, batch=None, stream=None):
+        import torch
+        batch = int(batch if batch is not None else (idx.numel() if idx is not None else coarse.shape[0]))
+        out = torch.empty((batch, 2) + self.hw, dtype=torch.float32, device=coarse.device)
+        check(load().cgl_corrector_forward(self.handle, _ptr(coarse), _ptr(un), _ptr(params), _ptr(idx), batch,
+                                           _ptr(out), _stream_handle(stream)), "cgl_corrector_forward")
+        return out
+
+    def gradients(self, coarse, un, target, params, idx=None, batch=None, stream=None):
+        import numpy as np
+        batch = int(batch if batch is not None else (idx.numel() if idx is not None else coarse.shape[0]))
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = ctypes.c_double()
+        check(load().cgl_corrector_gradients(self.handle, _ptr(coarse), _ptr(un), _ptr(target), _ptr(params),
+                                             _ptr(idx), batch, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                             ctypes.byref(loss), _stream_handle(stream)), "cgl_corrector_gradients")
+        return loss.value, g
+
+    def train_step(self, coarse, un, target, params, idx, lr, want_loss=False, stream=None):
+        loss = ctypes.c_double()
+        check(load().cgl_corrector_train_step(self.handle, _ptr(coarse), _ptr(un), _ptr(target), _ptr(params),
+                                              _ptr(idx), int(idx.numel()), ctypes.c_float(lr),
+                                              ctypes.byref(loss) if want_loss else None,
+                                              _stream_handle(stream)), "cgl_corrector_train_step")
+        return loss.value if want_loss else None
+
+    def apply(self, coarse, un, params, out, stream=None):
+        check(load().cgl_corrector_apply(self.handle, _ptr(coarse), _ptr(un), _ptr(params), int(coarse.shape[0]),
+                                         _ptr(out), _stream_handle(stream)), "cgl_corrector_apply")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().cgl_corrector_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
