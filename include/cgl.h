@@ -276,7 +276,8 @@ int cgl_corrector_get_weights(const cgl_corrector* c, float* host, int64_t count
 /* N(x) into the device float array out[batch][2][H][W].  Asynchronous. */
 int cgl_corrector_forward(cgl_corrector* c, const void* coarse, const void* un, const float* params,
                           const int* idx, int batch, float* out, void* stream);
-/* Loss = mean over batch x 2 x H x W of (C(u_n) + N(x) - target)^2 and its
+/* Loss = mean over batch x 2 x H x W of ((C(u_n) + N(x) - target) / s)^2,
+ * s the output scale (cgl_corrector_set_output_scale), and its
  * gradient w.r.t. the weights (host float[num_params], may be NULL); *loss
  * (may be NULL).  Synchronous when grads_host or loss is given. */
 int cgl_corrector_gradients(cgl_corrector* c, const void* coarse, const void* un, const void* target,
@@ -290,6 +291,10 @@ int cgl_corrector_train_step(cgl_corrector* c, const void* coarse, const void* u
 /* u_out[b] = coarse[b] + N(x_b), complex64 [batch][H][W].  Asynchronous. */
 int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, const float* params,
                         int batch, void* u_out, void* stream);
+/* N(x) = scale * (last convolution); default 1.  Training sets it to the
+ * typical size of the correction (fine minus coarse) so that the network's
+ * own outputs stay of order one.  EINVAL unless scale > 0 and finite. */
+int cgl_corrector_set_output_scale(cgl_corrector* c, float scale);
 int cgl_corrector_destroy(cgl_corrector* c);
 
 /*

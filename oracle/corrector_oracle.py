@@ -90,8 +90,9 @@ def features(coarse: np.ndarray, un: np.ndarray, params: np.ndarray) -> np.ndarr
 
 def forward(weights, x, round_weights=True):
     """weights: list of (w, b) FP32 masters.  Returns the activations
-    [x, a_1, ..., a_L] (a_L = output, no ReLU) using BF16-rounded w
-    (unrounded when round_weights is False)."""
+    [x, a_1, ..., a_L] (a_L = last convolution, no ReLU) using BF16-rounded w
+    (unrounded when round_weights is False).  The correction is
+    N(x) = out_scale * a_L."""
     acts = [x]
     for l, (w, b) in enumerate(weights):
         y = conv3x3(acts[-1], bf16_round(w) if round_weights else w, b)
@@ -101,15 +102,17 @@ def forward(weights, x, round_weights=True):
     return acts
 
 
-def loss_and_grads(weights, x, coarse, target, round_weights=True):
-    """Mean squared difference between C(u_n) + N(x) and the fine result over
-    all B x 2 x H x W real values; gradients by backpropagation (BF16 weights
-    in the forward pass, gradients taken with respect to those weights)."""
+def loss_and_grads(weights, x, coarse, target, round_weights=True, out_scale=1.0):
+    """Mean squared difference between C(u_n) + N(x), N(x) = out_scale * a_L,
+    and the fine result over all B x 2 x H x W real values, measured in units
+    of out_scale (i.e. the mean of ((C + N - F) / out_scale)^2); gradients by
+    backpropagation (BF16 weights in the forward pass, gradients taken with
+    respect to those weights).  Returns (loss, grads, N(x))."""
     acts = forward(weights, x, round_weights)
-    out = acts[-1]
+    out = out_scale * acts[-1]
     pred_re = coarse.real + out[:, 0]
     pred_im = coarse.imag + out[:, 1]
-    r_re, r_im = pred_re - target.real, pred_im - target.imag
+    r_re, r_im = (pred_re - target.real) / out_scale, (pred_im - target.imag) / out_scale
     count = out.size
     loss = float((np.sum(r_re * r_re) + np.sum(r_im * r_im)) / count)
     dy = np.stack([2 * r_re / count, 2 * r_im / count], axis=1)

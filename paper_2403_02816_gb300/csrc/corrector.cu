@@ -209,7 +209,7 @@ __global__ void relu_backward_kernel(float* __restrict__ dy, const float* __rest
 
 // r = C(u_n) + out - target (complex64 [P] selected by idx); dout = 2 r / count;
 // loss partial sums in FP64.
-__global__ void loss_kernel(const float* __restrict__ out, const float2* __restrict__ coarse,
+__global__ void loss_kernel(const float* __restrict__ out, float scale, const float2* __restrict__ coarse,
                             const float2* __restrict__ target, const int* __restrict__ idx, int B, int64_t HW,
                             float* __restrict__ dout, double* __restrict__ loss_sum) {
   const double inv = 1.0 / (2.0 * (double)B * (double)HW);
@@ -221,7 +221,8 @@ __global__ void loss_kernel(const float* __restrict__ out, const float2* __restr
     const int src = idx ? idx[b] : b;
     const float2 c = coarse[(int64_t)src * HW + p], t = target[(int64_t)src * HW + p];
     const float* ob = out + (int64_t)b * 2 * HW + p;
-    const float rr = c.x + ob[0] - t.x, ri = c.y + ob[HW] - t.y;
+    // residual in units of the output scale: (C(u_n) + scale*out - target) / scale
+    const float rr = (fmaf(scale, ob[0], c.x) - t.x) / scale, ri = (fmaf(scale, ob[HW], c.y) - t.y) / scale;
     s += (double)rr * rr + (double)ri * ri;
     float* db = dout + (int64_t)b * 2 * HW + p;
     db[0] = (float)(2.0 * inv) * rr;
@@ -262,17 +263,22 @@ __global__ void flip_weights_kernel(const __nv_bfloat16* __restrict__ w, __nv_bf
   }
 }
 
-// u = C(u_n) + correction
-__global__ void residual_add_kernel(const float2* __restrict__ coarse, const float* __restrict__ out, int B,
-                                    int64_t HW, float2* __restrict__ u) {
+// u = C(u_n) + scale * raw network output
+__global__ void residual_add_kernel(const float2* __restrict__ coarse, const float* __restrict__ out, float scale,
+                                    int B, int64_t HW, float2* __restrict__ u) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)B * HW;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / HW);
     const int64_t p = e - (int64_t)b * HW;
     const float2 c = coarse[e];
     const float* ob = out + (int64_t)b * 2 * HW + p;
-    u[e] = make_float2(c.x + ob[0], c.y + ob[HW]);
+    u[e] = make_float2(fmaf(scale, ob[0], c.x), fmaf(scale, ob[HW], c.y));
   }
+}
+
+__global__ void scale_copy_kernel(const float* __restrict__ a, float scale, float* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = scale * a[i];
 }
 
 }  // namespace cgl
@@ -295,6 +301,7 @@ struct cgl_corrector {
   float* m = nullptr;
   float* v = nullptr;
   int64_t t = 0;
+  float out_scale = 1.f;  // N(x) = out_scale * (last convolution)
   std::vector<float*> acts;  // acts[0] = features, acts[l+1] = output of layer l
   float* dbuf[2] = {nullptr, nullptr};
   double* loss = nullptr;
@@ -383,8 +390,8 @@ int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const vo
   if (st) return st;
   CUDA_TRY(cudaMemsetAsync(c->loss, 0, sizeof(double), s));
   CUDA_TRY(cudaMemsetAsync(c->grad, 0, c->nparams * sizeof(float), s));
-  loss_kernel<<<grid_for(B * HW), 256, 0, s>>>(c->acts[c->nlayers], (const float2*)coarse, (const float2*)target, idx,
-                                               B, HW, c->dbuf[0], c->loss);
+  loss_kernel<<<grid_for(B * HW), 256, 0, s>>>(c->acts[c->nlayers], c->out_scale, (const float2*)coarse,
+                                               (const float2*)target, idx, B, HW, c->dbuf[0], c->loss);
   CUDA_TRY(cudaGetLastError());
   int cur = 0;
   const int tiles = (c->H / kTile) * (c->W / kTile);
@@ -533,8 +540,9 @@ int cgl_corrector_forward(cgl_corrector* c, const void* coarse, const void* un, 
                                                        c->H, c->W, c->acts[0]);
   CUDA_TRY(cudaGetLastError());
   if ((st = forward_pass(c, batch, s))) return st;
-  CUDA_TRY(cudaMemcpyAsync(out, c->acts[c->nlayers], (size_t)batch * 2 * HW * sizeof(float), cudaMemcpyDeviceToDevice,
-                           s));
+  scale_copy_kernel<<<grid_for(batch * 2 * HW), 256, 0, s>>>(c->acts[c->nlayers], c->out_scale, out,
+                                                             (int64_t)batch * 2 * HW);
+  CUDA_TRY(cudaGetLastError());
   return CGL_OK;
 }
 
@@ -580,9 +588,15 @@ int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, co
                                                        batch, c->H, c->W, c->acts[0]);
   CUDA_TRY(cudaGetLastError());
   if ((st = forward_pass(c, batch, s))) return st;
-  residual_add_kernel<<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, c->acts[c->nlayers], batch, HW,
-                                                           (float2*)u_out);
+  residual_add_kernel<<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, c->acts[c->nlayers], c->out_scale,
+                                                           batch, HW, (float2*)u_out);
   CUDA_TRY(cudaGetLastError());
+  return CGL_OK;
+}
+
+int cgl_corrector_set_output_scale(cgl_corrector* c, float scale) {
+  if (!c || !(scale > 0.f) || !std::isfinite(scale)) return fail(CGL_EINVAL, "scale must be positive and finite");
+  c->out_scale = scale;
   return CGL_OK;
 }
 

@@ -81,11 +81,15 @@ class Dataset:
         torch.cuda.synchronize()
         self.seconds = time.perf_counter() - t0
         self.size = P
+        # typical size of the correction: the network's output scale
+        self.correction_rms = float((self.target - self.coarse).abs().pow(2).mean().sqrt())
 
 
 def train(corr, data, iters, batch, lr=1e-3, seed=SEED, log_every=0):
-    """Adam on random minibatches; the step size decays linearly to lr/10."""
+    """Adam on random minibatches; the step size decays linearly to lr/10.
+    The network's output scale is set to the dataset's RMS correction."""
     import torch
+    corr.set_output_scale(data.correction_rms)
     rng = np.random.default_rng(seed)
     losses = []
     t0 = time.perf_counter()

@@ -106,6 +106,7 @@ def load() -> ctypes.CDLL:
         "cgl_corrector_train_step": (I, [P, VP, VP, VP, VP, VP, I, ctypes.c_float, ctypes.POINTER(D), VP]),
         "cgl_corrector_apply": (I, [P, VP, VP, VP, I, VP, VP]),
         "cgl_corrector_destroy": (I, [P]),
+        "cgl_corrector_set_output_scale": (I, [P, ctypes.c_float]),
         "cgl_strerror": (ctypes.c_char_p, [I]),
         "cgl_last_error": (ctypes.c_char_p, []),
     }
@@ -371,6 +372,10 @@ class Corrector:
         check(load().cgl_corrector_num_params(self.handle, ctypes.byref(n)), "cgl_corrector_num_params")
         self.nparams = n.value
         self.hw = (int(height), int(width))
+
+    def set_output_scale(self, scale):
+        check(load().cgl_corrector_set_output_scale(self.handle, ctypes.c_float(scale)),
+              "cgl_corrector_set_output_scale")
 
     def set_weights(self, flat):
         import numpy as np

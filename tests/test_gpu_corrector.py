@@ -56,14 +56,17 @@ def test_forward_selects_samples_by_index():
     assert rel(out, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("H,W,B,hidden,layers", [(32, 32, 2, 8, 4), (64, 32, 3, 32, 6)])
-def test_gradients_match_oracle(H, W, B, hidden, layers):
+@pytest.mark.parametrize("H,W,B,hidden,layers,out_scale", [(32, 32, 2, 8, 4, 1.0), (64, 32, 3, 32, 6, 1.0),
+                                                            (32, 16, 2, 8, 3, 1e-3)])
+def test_gradients_match_oracle(H, W, B, hidden, layers, out_scale):
     weights, coarse, un, target, params, d = setup(H, W, B, hidden, layers, 3, scale=0.2)
     corr = nat.Corrector(H, W, hidden, layers, max_batch=B)
     corr.set_weights(C.flatten(weights))
+    corr.set_output_scale(out_scale)
     loss, g = corr.gradients(d[0], d[1], d[2], d[3])
     x = C.features(coarse.astype(complex), un.astype(complex), params)
-    rloss, rgrads, _ = C.loss_and_grads(weights, x, coarse.astype(complex), target.astype(complex))
+    rloss, rgrads, _ = C.loss_and_grads(weights, x, coarse.astype(complex), target.astype(complex),
+                                        out_scale=out_scale)
     assert loss == pytest.approx(rloss, rel=1e-5)
     gref = np.concatenate([np.concatenate([gw.ravel(), gb.ravel()]) for gw, gb in rgrads])
     assert rel(g, gref) <= 1e-4
@@ -106,6 +109,7 @@ def test_apply_is_coarse_plus_network_output():
     weights, coarse, un, target, params, d = setup(16, 32, 2, 8, 3, 5)
     corr = nat.Corrector(16, 32, 8, 3, max_batch=2)
     corr.set_weights(C.flatten(weights))
+    corr.set_output_scale(0.25)
     out = corr.forward(d[0], d[1], d[3]).cpu().numpy()
     u = torch.empty_like(d[0])
     corr.apply(d[0], d[1], d[3], u)
