@@ -55,10 +55,13 @@ def parse():
     ap.add_argument("--scheme", default="split4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--workload", default="periodic128", choices=["periodic128", "neumann256", "batch512"],
+    ap.add_argument("--workload", default="periodic128", choices=["periodic128", "neumann256", "batch512", "corrector"],
                     help="periodic128: the headline 3D periodic workload; neumann256: the 3D Neumann "
                          "precision study (FP64 / FP32 / BF16x3 tensor cores)")
     ap.add_argument("--t1-steps", type=int, default=100, help="neumann256: steps of the T=1 error run")
+    ap.add_argument("--corr-traj", type=int, default=96, help="corrector: training trajectories")
+    ap.add_argument("--corr-iters", type=int, default=3000, help="corrector: training iterations")
+    ap.add_argument("--corr-test", type=int, default=8, help="corrector: held-out trajectories")
     return ap.parse_args()
 
 
@@ -178,6 +181,75 @@ def run_batch512(args):
                      "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
                      "note": "whole-step time, all passes"},
         "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
+def run_corrector(args):
+    """Learned corrector on the 2D periodic cubic CGL 128^2: data from the fine
+    method (Lawson4, complex128, tau = 0.002), training of the 6-layer CNN,
+    and held-out trajectories run to t = 4.992 with the corrected coarse step
+    (Lawson4, complex64, tau = 0.016) against the fine method."""
+    import torch
+    from paper_2403_02816_gb300 import learned as Lm
+    from paper_2403_02816_gb300 import native as nat
+
+    nat.load()
+    ntraj, iters, batch = args.corr_traj, args.corr_iters, 32
+    data = Lm.Dataset(ntraj=ntraj, snaps=8)
+    corr = nat.Corrector(Lm.N, Lm.N, 32, 6, max_batch=batch)
+    losses, train_s = Lm.train(corr, data, iters=iters, batch=batch, lr=1e-3, log_every=max(1, iters // 4))
+    # throughput of one corrected coarse step vs 8 fine steps (one instance, 128^2)
+    p = Lm.problem((1.0, 0.5, 0.5, -1.0, 1.0))
+    rng = np.random.default_rng(0)
+    U0 = I.u0_bumps(p, rng)
+    stream = torch.cuda.current_stream()
+    with nat.Plan(p, Lm.FINE_TAU, "lawson4", "f64") as fine, nat.Plan(p, Lm.COARSE_TAU, "lawson4", "f32") as crs:
+        uf = nat.to_device(U0, torch.complex128)
+        uc = nat.to_device(U0, torch.complex64).reshape(1, Lm.N, Lm.N)
+        prev = torch.empty_like(uc)
+        prm = torch.tensor([[1.0, 0.5, 0.5, -1.0, 1.0]], dtype=torch.float32, device="cuda")
+        reps = 50
+
+        def corrected(k):
+            for _ in range(k):
+                prev.copy_(uc)
+                crs.step(uc, 1)
+                corr.apply(uc, prev, prm, uc)
+
+        for fn, key in ((lambda k: fine.step(uf, Lm.SUB * k), "fine_8_steps_f64"),
+                        (lambda k: crs.step(uc, k), "coarse_step_f32"), (corrected, "corrected_coarse_step")):
+            fn(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(reps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            if key == "fine_8_steps_f64":
+                t_fine = ms
+            elif key == "coarse_step_f32":
+                t_coarse = ms
+            else:
+                t_corr = ms
+    rows = Lm.evaluate(corr, ntraj=args.corr_test, seed=Lm.SEED + 7777)
+    e_c = float(np.mean([r["coarse"] for r in rows]))
+    e_l = float(np.mean([r["corrected"] for r in rows]))
+    npts = Lm.N * Lm.N
+    line = {
+        "metric": METRIC, "value": npts / (t_corr / 1e3), "unit": UNIT, "n_gpus": 1, "steps": reps,
+        "warmup": 3, "ms_per_step": t_corr, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+bf16", "data": "synthetic",
+        "config": {"workload": "learned_corrector_2d_periodic_128^2", "fine_tau": Lm.FINE_TAU,
+                   "coarse_tau": Lm.COARSE_TAU, "train_trajectories": ntraj, "pairs": data.size,
+                   "iterations": iters, "batch": batch, "test_trajectories": args.corr_test,
+                   "t_final": Lm.COARSE_STEPS * Lm.COARSE_TAU},
+        "dataset_seconds": data.seconds, "train_seconds": train_s,
+        "train_samples_per_s": iters * batch / train_s, "losses": losses,
+        "ms": {"fine_8_steps_f64": t_fine, "coarse_step_f32": t_coarse, "corrected_coarse_step": t_corr},
+        "speedup_corrected_vs_fine_f64": t_fine / t_corr,
+        "held_out_rel_l2_vs_fine": {"coarse": e_c, "corrected": e_l, "gain": e_c / e_l, "rows": rows},
     }
     print(json.dumps(line))
 
@@ -367,6 +439,9 @@ def main():
         return
     if args.workload == "batch512":
         run_batch512(args)
+        return
+    if args.workload == "corrector":
+        run_corrector(args)
         return
 
     import torch

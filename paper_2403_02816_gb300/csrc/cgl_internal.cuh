@@ -119,7 +119,7 @@ template <class T, class T2> __device__ __forceinline__ T2 nl_flow(const NlParam
   const T2 k2 = nl_g<T, T2>(p, caxpy(u, h, k1));
   const T2 k3 = nl_g<T, T2>(p, caxpy(u, h, k2));
   const T2 k4 = nl_g<T, T2>(p, caxpy(u, t, k3));
-  const T2 s = cadd(cadd(k1, k4), cscale(cadd(k2, k3), T(2)));
+  const T2 s = caxpy(cadd(k1, k4), T(2), cadd(k2, k3));  // k1 + 2 k2 + 2 k3 + k4
   return caxpy(u, t * (T(1) / T(6)), s);
 }
 

@@ -50,34 +50,51 @@ def sample(rng, n=N):
 class Dataset:
     """Device tensors: un, coarse, target (complex64 [P, n, n]), params (float32 [P, 5])."""
 
-    def __init__(self, ntraj, snaps=8, seed=SEED, n=N, device="cuda"):
+    def __init__(self, ntraj, snaps=8, seed=SEED, n=N, device="cuda", concurrency=32):
+        """Trajectories run `concurrency` at a time, each on its own CUDA stream
+        (one 128^2 instance fills only a few SMs)."""
         import torch
         P = ntraj * snaps
         self.n = n
         self.un = torch.empty((P, n, n), dtype=torch.complex64, device=device)
         self.coarse = torch.empty_like(self.un)
         self.target = torch.empty_like(self.un)
-        self.params = torch.empty((P, 5), dtype=torch.float32, device=device)
+        host_params = np.empty((P, 5), dtype=np.float32)
         stride = COARSE_STEPS * SUB // snaps
+        streams = [torch.cuda.Stream() for _ in range(min(concurrency, ntraj))]
         t0 = time.perf_counter()
-        k = 0
-        for i in range(ntraj):
-            rng = np.random.Generator(np.random.PCG64(seed + 1000 * i))
-            par, p, U0 = sample(rng, n)
-            with nat.Plan(p, FINE_TAU, "lawson4", "f64") as fine, nat.Plan(p, COARSE_TAU, "lawson4", "f32") as crs:
-                u = nat.to_device(U0, torch.complex128, device)
-                for s in range(snaps):
-                    if s > 0:
-                        fine.step(u, stride)
-                    self.un[k].copy_(u)
-                    v = u.clone()
-                    fine.step(v, SUB)
-                    self.target[k].copy_(v)
-                    c = self.un[k].clone()
-                    crs.step(c, 1)
-                    self.coarse[k].copy_(c)
-                    self.params[k] = torch.tensor(par, dtype=torch.float32)
-                    k += 1
+        for g0 in range(0, ntraj, len(streams)):
+            group = []
+            for gi, i in enumerate(range(g0, min(ntraj, g0 + len(streams)))):
+                s = streams[gi]
+                rng = np.random.Generator(np.random.PCG64(seed + 1000 * i))
+                par, p, U0 = sample(rng, n)
+                fine = nat.Plan(p, FINE_TAU, "lawson4", "f64", stream=s)
+                crs = nat.Plan(p, COARSE_TAU, "lawson4", "f32", stream=s)
+                with torch.cuda.stream(s):
+                    u = nat.to_device(U0, torch.complex128, device)
+                    v = torch.empty_like(u)
+                    c = torch.empty((n, n), dtype=torch.complex64, device=device)
+                group.append((s, fine, crs, u, v, c, i))
+                host_params[i * snaps:(i + 1) * snaps] = par
+            for sn in range(snaps):
+                for s, fine, crs, u, v, c, i in group:
+                    k = i * snaps + sn
+                    with torch.cuda.stream(s):
+                        if sn > 0:
+                            fine.step(u, stride, stream=s)
+                        self.un[k].copy_(u)
+                        v.copy_(u)
+                        fine.step(v, SUB, stream=s)
+                        self.target[k].copy_(v)
+                        c.copy_(self.un[k])
+                        crs.step(c, 1, stream=s)
+                        self.coarse[k].copy_(c)
+            torch.cuda.synchronize()
+            for s, fine, crs, *_ in group:
+                fine.close()
+                crs.close()
+        self.params = torch.from_numpy(host_params).to(device)
         torch.cuda.synchronize()
         self.seconds = time.perf_counter() - t0
         self.size = P
@@ -102,6 +119,23 @@ def train(corr, data, iters, batch, lr=1e-3, seed=SEED, log_every=0):
             losses.append((it, loss))
     torch.cuda.synchronize()
     return losses, time.perf_counter() - t0
+
+
+def one_step_errors(corr, data, batch=16):
+    """Per pair of a (held-out) dataset: the one-step errors
+    |C(u_n) - F^8(u_n)| / |F^8(u_n)| and |C(u_n) + N(x_n) - F^8(u_n)| / |F^8(u_n)|
+    (relative L2 over the field)."""
+    import torch
+    coarse_err, corr_err = [], []
+    out = torch.empty((batch, data.n, data.n), dtype=torch.complex64, device=data.un.device)
+    for b0 in range(0, data.size, batch):
+        k = min(batch, data.size - b0)
+        corr.apply(data.coarse[b0:b0 + k], data.un[b0:b0 + k], data.params[b0:b0 + k], out[:k])
+        for j in range(k):
+            t = data.target[b0 + j]
+            coarse_err.append(nat.cgl_rel_error(data.coarse[b0 + j], t, nat.CGL_F32)[0])
+            corr_err.append(nat.cgl_rel_error(out[j], t, nat.CGL_F32)[0])
+    return np.array(coarse_err), np.array(corr_err)
 
 
 def evaluate(corr, ntraj, seed, n=N, device="cuda"):
