@@ -236,6 +236,12 @@ def run_corrector(args):
     rows = Lm.evaluate(corr, ntraj=args.corr_test, seed=Lm.SEED + 7777)
     e_c = float(np.mean([r["coarse"] for r in rows]))
     e_l = float(np.mean([r["corrected"] for r in rows]))
+    held = Lm.Dataset(ntraj=args.corr_test, snaps=8, seed=Lm.SEED + 7777)
+    one_step = {}
+    for name, ds in (("train_pairs", data), ("held_out_pairs", held)):
+        c, l = Lm.one_step_errors(corr, ds)
+        one_step[name] = {"coarse_mean": float(c.mean()), "corrected_mean": float(l.mean()),
+                          "gain": float(c.mean() / l.mean()), "fraction_improved": float(np.mean(l < c))}
     npts = Lm.N * Lm.N
     line = {
         "metric": METRIC, "value": npts / (t_corr / 1e3), "unit": UNIT, "n_gpus": 1, "steps": reps,
@@ -250,6 +256,7 @@ def run_corrector(args):
         "ms": {"fine_8_steps_f64": t_fine, "coarse_step_f32": t_coarse, "corrected_coarse_step": t_corr},
         "speedup_corrected_vs_fine_f64": t_fine / t_corr,
         "held_out_rel_l2_vs_fine": {"coarse": e_c, "corrected": e_l, "gain": e_c / e_l, "rows": rows},
+        "one_step_rel_l2_vs_fine": one_step,
     }
     print(json.dumps(line))
 

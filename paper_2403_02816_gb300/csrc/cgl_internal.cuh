@@ -320,6 +320,9 @@ struct MmaLaunch {
   int* status;
 };
 constexpr size_t kTensorMapBytes = 128;
+// Output rows of one component are split over this many CTAs (n >= 64 and a
+// multiple of 32: two blocks of n/2 rows, so two CTAs fit on an SM).
+inline int mma_row_blocks(int n) { return (n >= 64 && n % 32 == 0) ? 2 : 1; }
 cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N);
 cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n);
 cudaError_t prepare_mma_pass();

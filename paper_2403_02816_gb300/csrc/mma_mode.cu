@@ -12,10 +12,12 @@
 // (lh, hl, mm, mh, hm, hh) accumulate in FP32 tensor memory: about 24
 // significant bits, i.e. FP32 accuracy.
 //
-// Kernel shape: one CTA per tile of 128 fibers (TMEM lanes) x the n outputs
-// of one component (re or im; n <= 256), with the (h,h) product and the five
-// correction products in separate TMEM accumulators that the epilogue adds in
-// FP32; K advances 16 per pipeline stage, five stages, filled by TMA
+// Kernel shape: one CTA per tile of 128 fibers (TMEM lanes) x one block of
+// output rows of one component (re or im; nc = n or n/2 <= 128 rows, so that
+// two CTAs share an SM and one's epilogue overlaps the other's MMAs), with the
+// (h,h) product and the five correction products in separate TMEM
+// accumulators that the epilogue adds in FP32; K advances 16 per pipeline
+// stage, four stages, filled by TMA
 // (A: K-major for mode 1 whose fibers are contiguous, MN-major
 // for the other modes; B: K-major), consumed by tcgen05.mma issued by one
 // thread, freed by tcgen05.commit.  Every mbarrier wait is bounded: on
@@ -34,7 +36,7 @@
 namespace cgl {
 
 constexpr int kMmaThreads = 128;
-constexpr int kMmaStages = 5;
+constexpr int kMmaStages = 4;
 constexpr int kMmaM = 128;
 constexpr int kMmaK = 16;
 constexpr long long kSpinLimit = 1ll << 24;
@@ -168,14 +170,16 @@ struct MmaPassArgs {
   int out_fp32;      // 1: FP32 planes (re, im); 0: BF16x3 planes (6)
   void* out[kMaxRhs];
   int64_t N;         // plane length (field size)
-  int tmem_cols;     // power of two >= 2n
+  int nc;            // outputs (rows i) of one component per CTA: n or n/2
+  int nsub;          // n / nc
+  int tmem_cols;     // power of two >= 2 nc
   int* status;
 };
 
 // One pipeline stage: three A splits (128 fibers x 16) and three B splits
 // (n output rows of one half x 16).
-static __host__ __device__ constexpr uint32_t mma_stage_bytes(int n) {
-  return 3u * (kMmaM * kMmaK * 2u) + 3u * (static_cast<uint32_t>(n) * kMmaK * 2u);
+static __host__ __device__ constexpr uint32_t mma_stage_bytes(int nc) {
+  return 3u * (kMmaM * kMmaK * 2u) + 3u * (static_cast<uint32_t>(nc) * kMmaK * 2u);
 }
 
 // CTA (tile, half): 128 fibers x the n outputs of component c' = half.
@@ -194,8 +198,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   const CUtensorMap* tmB = rhs ? &tmB1 : &tmB0;
   const int nk = (2 * n) / kMmaK;
   const uint32_t a_bytes = kMmaM * kMmaK * 2;
-  const uint32_t b_bytes = static_cast<uint32_t>(n) * kMmaK * 2;
-  const uint32_t stage_bytes = mma_stage_bytes(n);
+  const int nc = a.nc;
+  const uint32_t b_bytes = static_cast<uint32_t>(nc) * kMmaK * 2;
+  const uint32_t stage_bytes = mma_stage_bytes(nc);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + kMmaStages * stage_bytes);
   uint64_t* empty = full + kMmaStages;
   uint64_t* accum = empty + kMmaStages;
@@ -205,8 +210,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
 
   // the two halves of a fiber tile are adjacent blocks, so the second read
   // of the tile's A data is served from L2
-  const int64_t tile = blockIdx.x >> 1;
-  const int half = blockIdx.x & 1;
+  // CTA (tile, component, row block); the CTAs of one fiber tile are adjacent
+  // blocks, so the repeated reads of the tile's A data are served from L2
+  const int64_t tile = blockIdx.x / (2 * a.nsub);
+  const int part = blockIdx.x % (2 * a.nsub);
+  const int half = part / a.nsub;
+  const int sub = part % a.nsub;
   int64_t q0 = 0, p0 = 0;
   if (a.a_mn) {
     const int64_t per_q = a.P / kMmaM;
@@ -230,10 +239,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t d_main = tmem, d_corr = tmem + n;
+  const uint32_t d_main = tmem, d_corr = tmem + nc;
 
   if (threadIdx.x == 0) {
-    const uint32_t idesc = idesc_bf16(kMmaM, n, a.a_mn);
+    const uint32_t idesc = idesc_bf16(kMmaM, nc, a.a_mn);
     auto issue_load = [&](int kb, int slot) {
       uint8_t* st = base + slot * stage_bytes;
       const uint32_t bar = smem_u32(&full[slot]);
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
         } else {
           tma_load_3d(dA, tmA, bar, j0, (int)q0, plane);
         }
-        tma_load_3d(smem_u32(st + 3 * a_bytes + s * b_bytes), tmB, bar, k0, half * n, s);
+        tma_load_3d(smem_u32(st + 3 * a_bytes + s * b_bytes), tmB, bar, k0, half * n + sub * nc, s);
       }
     };
     // split products: five corrections (l,h) (h,l) (m,m) (m,h) (h,m), then (h,h)
@@ -323,10 +332,11 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     // (now idle) pipeline buffers and store them as 16-byte chunks along the
     // contiguous fiber index
     const int64_t tile0 = p0 + a.P * (int64_t)n * q0;
-    for (int i0 = 0; i0 < n; i0 += 16) {
+    for (int c0 = 0; c0 < nc; c0 += 16) {
+      const int i0 = sub * nc + c0;  // first output row of this chunk
       uint32_t rm[16], rc[16];
-      tmem_ld16(d_main + lane_addr + i0, rm);
-      tmem_ld16(d_corr + lane_addr + i0, rc);
+      tmem_ld16(d_main + lane_addr + c0, rm);
+      tmem_ld16(d_corr + lane_addr + c0, rc);
       float v[16];
 #pragma unroll
       for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(rm[t]) + __uint_as_float(rc[t]);
@@ -522,13 +532,14 @@ cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P,
 
 // B operand map over three (2n x 2n) BF16 factor splits.
 cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n) {
+  const int nc = n / mma_row_blocks(n);
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_out);
   std::memset(m, 0, sizeof(CUtensorMap));
   const cuuint64_t dims[3] = {(cuuint64_t)2 * n, (cuuint64_t)2 * n, 3};
   const cuuint64_t strides[2] = {(cuuint64_t)4 * n, (cuuint64_t)8 * n * n};
-  const cuuint32_t box[3] = {(cuuint32_t)kMmaK, (cuuint32_t)n, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)kMmaK, (cuuint32_t)nc, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fsplit), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -536,10 +547,10 @@ cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-static size_t mma_smem_bytes(int n) { return (size_t)kMmaStages * mma_stage_bytes(n) + 1024 + 256; }
+static size_t mma_smem_bytes(int nc) { return (size_t)kMmaStages * mma_stage_bytes(nc) + 1024 + 256; }
 
 cudaError_t prepare_mma_pass() {
-  return cudaFuncSetAttribute(mma_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mma_smem_bytes(256));
+  return cudaFuncSetAttribute(mma_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mma_smem_bytes(240));
 }
 
 cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
@@ -554,15 +565,17 @@ cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
   a.N = L.N;
   const int64_t mtiles = L.P > 1 ? (L.P / kMmaM) * L.Q : (L.Q + kMmaM - 1) / kMmaM;
   int cols = 32;
-  while (cols < 2 * L.n) cols *= 2;
+  a.nsub = mma_row_blocks(L.n);
+  a.nc = L.n / a.nsub;
+  while (cols < 2 * a.nc) cols *= 2;
   a.tmem_cols = cols;
   a.status = L.status;
   const CUtensorMap* A0 = reinterpret_cast<const CUtensorMap*>(L.tmA[0]);
   const CUtensorMap* A1 = reinterpret_cast<const CUtensorMap*>(L.tmA[L.nrhs > 1 ? 1 : 0]);
   const CUtensorMap* B0 = reinterpret_cast<const CUtensorMap*>(L.tmB[0]);
   const CUtensorMap* B1 = reinterpret_cast<const CUtensorMap*>(L.tmB[L.nrhs > 1 ? 1 : 0]);
-  dim3 grid((unsigned)(2 * mtiles), (unsigned)L.nrhs);  // (fiber tile, output component)
-  mma_mode_kernel<<<grid, kMmaThreads, mma_smem_bytes(L.n), s>>>(*A0, *A1, *B0, *B1, a);
+  dim3 grid((unsigned)(2 * a.nsub * mtiles), (unsigned)L.nrhs);  // (fiber tile, component, row block)
+  mma_mode_kernel<<<grid, kMmaThreads, mma_smem_bytes(a.nc), s>>>(*A0, *A1, *B0, *B1, a);
   return cudaGetLastError();
 }
 
