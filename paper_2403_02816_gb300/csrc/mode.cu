@@ -98,7 +98,74 @@ __device__ __forceinline__ void mode_tile(const ModePassArgs& a, int tbmax, int6
   const T2* F1 = reinterpret_cast<const T2*>(a.factor[NRHS > 1 ? 1 : 0]);
   bool bad = false;
 
-  if (P == 1) {
+  if constexpr (sizeof(T) == 4) {
+    // FP32: 4 rows x 4 fibers per thread and right-hand side, so each factor
+    // load (4 consecutive rows, two 16-byte loads) and each fiber value feed
+    // 16 complex multiply-adds.  Consecutive threads take consecutive row
+    // blocks for contiguous fibers (P == 1) and consecutive fiber blocks
+    // otherwise, which keeps the epilogue's stores coalesced.
+    const int ni = (n + 3) / 4, nt = (tb + 3) / 4;
+    const int items = ni * nt;
+    for (int w = threadIdx.x; w < items; w += kModeThreads) {
+      int ig, tg;
+      if (P == 1) { tg = w / ni; ig = w - tg * ni; }
+      else { ig = w / nt; tg = w - ig * nt; }
+      const int i0 = ig * 4, t0 = tg * 4;
+      const int ilim = min(4, n - i0), tlim = min(4, tb - t0);
+      T2 acc0[4][4], acc1[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { acc0[u][v] = mk<T2>(0, 0); acc1[u][v] = mk<T2>(0, 0); }
+      const bool full_i = (ilim == 4) && ((n & 1) == 0);
+      for (int j = 0; j < n; ++j) {
+        T2 f0[4], f1[4], z0[4], z1[4];
+        const T2* c0 = F0 + i0 + (int64_t)j * n;
+        const T2* c1 = F1 + i0 + (int64_t)j * n;
+        if (full_i) {
+          const float4 a01 = __ldg(reinterpret_cast<const float4*>(c0));
+          const float4 a23 = __ldg(reinterpret_cast<const float4*>(c0) + 1);
+          f0[0] = mk<T2>(a01.x, a01.y); f0[1] = mk<T2>(a01.z, a01.w);
+          f0[2] = mk<T2>(a23.x, a23.y); f0[3] = mk<T2>(a23.z, a23.w);
+          if (NRHS > 1) {
+            const float4 b01 = __ldg(reinterpret_cast<const float4*>(c1));
+            const float4 b23 = __ldg(reinterpret_cast<const float4*>(c1) + 1);
+            f1[0] = mk<T2>(b01.x, b01.y); f1[1] = mk<T2>(b01.z, b01.w);
+            f1[2] = mk<T2>(b23.x, b23.y); f1[3] = mk<T2>(b23.z, b23.w);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            f0[u] = u < ilim ? c0[u] : mk<T2>(0, 0);
+            if (NRHS > 1) f1[u] = u < ilim ? c1[u] : mk<T2>(0, 0);
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int t = min(t0 + v, tb - 1);
+          z0[v] = Z0[t * pitch + j];
+          if (NRHS > 1) z1[v] = Z1[t * pitch + j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            cmac(acc0[u][v], f0[u], z0[v]);
+            if (NRHS > 1) cmac(acc1[u][v], f1[u], z1[v]);
+          }
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        if (v >= tlim) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u >= ilim) continue;
+          T2 y[2] = {acc0[u][v], acc1[u][v]};
+          finish_point<T>(a, y, pbase[t0 + v] + P * (i0 + u), bad);
+        }
+      }
+    }
+  } else if (P == 1) {
     // rows i fast, 4 fibers per thread
     const int tgroups = (tb + 3) / 4;
     const int items = n * tgroups;
