@@ -224,6 +224,7 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
       a.sym[r].sum_form = (fi == FAC_K) ? 1 : 0;
     }
     a.twiddle = p->twiddle[mu];
+    a.twform = p->twform[mu];
     a.status = p->status;
     const double nn = (double)p->n[mu];
     const double fft = 5.0 * std::log2(nn) * Nd * sw.nrhs;  // 5 n log2 n per pencil
@@ -374,10 +375,10 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
       CUDA_TRY(periodic_symbol_device(k64, n, L, 0.0, p->a1, p->b1, p->a2 / p->d, 1.0 / (double)p->N, 1, s));
       if ((st = make_working(p, k64, n, &p->ksym[mu], s))) return st;
     }
-    double2* tw64 = nullptr;
-    if ((st = dev_alloc(p, (void**)&tw64, n * sizeof(double2)))) return st;
-    CUDA_TRY(twiddle_device(tw64, n, s));
-    if ((st = make_working(p, tw64, n, &p->twiddle[mu], s))) return st;
+    const size_t treal = p->precision == CGL_F64 ? sizeof(double) : sizeof(float);
+    if ((st = dev_alloc(p, &p->twiddle[mu], 2 * 3 * (size_t)n * treal))) return st;
+    if ((st = dev_alloc(p, (void**)&p->twform[mu], 2 * (size_t)n * sizeof(int)))) return st;
+    CUDA_TRY(fma_twiddles_device(p->twiddle[mu], p->twform[mu], n, p->precision == CGL_F64, s));
   }
   return CGL_OK;
 }

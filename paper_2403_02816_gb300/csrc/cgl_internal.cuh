@@ -262,7 +262,8 @@ struct FftPassArgs {
   OpArgs op;
   int flags;
   Symbol sym[kMaxRhs];
-  const void* twiddle;  // T2[n_ax]: exp(-2 pi i m / n_ax)
+  const void* twiddle;  // T[2][n_ax][3]: FMA-butterfly form of exp(-+2 pi i m / n_ax), see fft.cu
+  const int* twform;    // int[2][n_ax]
   int* status;          // device status word (bit 0: non-finite output)
 };
 
@@ -305,7 +306,10 @@ cudaError_t expm_device(const double2* dA, double scale, int n, double2* dOut, d
 cudaError_t periodic_symbol_device(double2* dOut, int n, double L, double ctau, double ar,
                                    double ai, double beta, double post, int sum_form,
                                    cudaStream_t s);
-cudaError_t twiddle_device(double2* dOut, int n, cudaStream_t s);
+// FFT twiddles for the FMA butterflies: for w = exp(-+2 pi i m/n) = c + i s,
+// form 0 (|c| >= |s|): tau = s/c, m_re = m_im = c; form 1: tau = -c/s,
+// m_re = -s, m_im = s.  Tables in T (double when f64, else float).
+cudaError_t fma_twiddles_device(void* tab, int* form, int n, int f64, cudaStream_t s);
 cudaError_t convert_f64_to_f32(const double2* src, float2* dst, int64_t count, cudaStream_t s);
 
 // mma_mode.cu: BF16x3 mu-mode product on tcgen05 (complex64 state).

@@ -131,17 +131,33 @@ cudaError_t periodic_symbol_device(double2* dOut, int n, double L, double ctau, 
   return cudaGetLastError();
 }
 
-// exp(-2 pi i m / n) = (cospi(2m/n), -sinpi(2m/n))
-__global__ void twiddle_kernel(double2* out, int n) {
+// Twiddles w = exp(-+2 pi i m / n) = c + i s (forward: s = -sinpi(2m/n);
+// inverse: s = +sinpi(2m/n)), stored for the FMA butterfly a +- w b:
+//   form 0 (|c| >= |s|): w b = c ((b.x - tau b.y) + i (b.y + tau b.x)), tau = s/c
+//   form 1 (|c| <  |s|): w b = s (-(b.y + tau b.x) + i (b.x - tau b.y)), tau = -c/s
+// so both forms share u = b.x - tau b.y, v = b.y + tau b.x with |tau| <= 1.
+template <class T> __global__ void fma_twiddle_kernel(T* tab, int* form, int n) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
   double sn, cs;
   sincospi(2.0 * (double)m / (double)n, &sn, &cs);
-  out[m] = make_double2(cs, -sn);
+  for (int dir = 0; dir < 2; ++dir) {
+    const double c = cs, s = dir ? sn : -sn;
+    double tau, mre, mim;
+    int f;
+    if (fabs(c) >= fabs(s)) { tau = s / c; mre = c; mim = c; f = 0; }
+    else { tau = -c / s; mre = -s; mim = s; f = 1; }
+    T* e = tab + ((int64_t)dir * n + m) * 3;
+    e[0] = (T)tau;
+    e[1] = (T)mre;
+    e[2] = (T)mim;
+    form[dir * n + m] = f;
+  }
 }
 
-cudaError_t twiddle_device(double2* dOut, int n, cudaStream_t s) {
-  twiddle_kernel<<<(n + 127) / 128, 128, 0, s>>>(dOut, n);
+cudaError_t fma_twiddles_device(void* tab, int* form, int n, int f64, cudaStream_t s) {
+  if (f64) fma_twiddle_kernel<double><<<(n + 127) / 128, 128, 0, s>>>((double*)tab, form, n);
+  else fma_twiddle_kernel<float><<<(n + 127) / 128, 128, 0, s>>>((float*)tab, form, n);
   return cudaGetLastError();
 }
 

@@ -38,14 +38,49 @@ template <class T2> __device__ __forceinline__ void dft4(T2* x, bool inv) {
   x[3] = csub(d02, rot);
 }
 
+// Twiddle w = c + i s in FMA-butterfly form (built by fma_twiddles_device):
+// form 0 (|c| >= |s|): w = c (1 + i tau), m_re = m_im = c;
+// form 1 (|c| <  |s|): w = s (i - tau),   m_re = -s, m_im = s;  |tau| <= 1.
+// With u = b.x - tau b.y and v = b.y + tau b.x:
+//   form 0: w b = m_re u + i m_im v;   form 1: w b = m_re v + i m_im u.
+template <class T> struct Tw {
+  T tau, mre, mim;
+  int form;
+};
+
+template <class T> __device__ __forceinline__ Tw<T> load_tw(const T* tt, const int* tf, int m) {
+  Tw<T> w;
+  w.tau = tt[3 * m];
+  w.mre = tt[3 * m + 1];
+  w.mim = tt[3 * m + 2];
+  w.form = tf[m];
+  return w;
+}
+
+// (a, b) <- (a + w b, a - w b): two FMAs for u, v and four for the outputs,
+// against eight operations with a plain complex multiply.
+template <class T, class T2> __device__ __forceinline__ void fma_bfly(T2& a, T2& b, const Tw<T>& w) {
+  const T u = fma(-w.tau, b.y, b.x);
+  const T v = fma(w.tau, b.x, b.y);
+  const T P = w.form ? v : u;
+  const T Q = w.form ? u : v;
+  const T2 a0 = a;
+  a = mk<T2>(fma(w.mre, P, a0.x), fma(w.mim, Q, a0.y));
+  b = mk<T2>(fma(-w.mre, P, a0.x), fma(-w.mim, Q, a0.y));
+}
+
 // One Stockham stage of radix R on `tb` pencils of length n, for NR tiles
 // (right-hand sides) at once; tile r starts at s0 + r * tile_stride.
 // p = product of the radices already applied.  Butterfly i of a pencil
-// (k = i mod p) reads x_r = s[i + r n/R], multiplies by exp(-+2 pi i r k/(pR)),
-// does a length-R DFT and writes s[(i-k)R + k + r p].
-template <class T2, int R, int NR>
+// (k = i mod p) reads x_r = s[i + r n/R], multiplies by w_r = exp(-+2 pi i r k/(pR)),
+// does a length-R DFT and writes s[(i-k)R + k + r p].  With twiddles
+// (p > 1) the radix-4 DFT of (x0, w1 x1, w2 x2, w3 x3), w3 = w1 w2, is done as
+// four FMA butterflies: (x0, x2) and (x1, x3) with w2, then (x0, x1) with w1
+// and (x2, x3) with -+i w1 (table entry m1 + n/4); outputs y0 y1 y2 y3 =
+// x0 x2 x1 x3.  tt/tf: this direction's twiddle table.
+template <class T, class T2, int R, int NR>
 __device__ __forceinline__ void fft_stage(T2* s0, int tile_stride, int pitch, int n, int lognb, int tb, int p,
-                                          const T2* tw, bool inv) {
+                                          const T* tt, const int* tf, bool inv) {
   constexpr int BPT = 8 / R;
   const int nb = n / R;
   const int total = tb * nb;
@@ -65,18 +100,30 @@ __device__ __forceinline__ void fft_stage(T2* s0, int tile_stride, int pitch, in
       for (int rr = 0; rr < NR; ++rr)
 #pragma unroll
         for (int r = 0; r < R; ++r) v[rr][b][r] = s0[rr * tile_stride + src + r * nb];
-      if (p > 1) {
+      if (p == 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const T2 w = tw[r * k * twstride];
-#pragma unroll
-          for (int rr = 0; rr < NR; ++rr) v[rr][b][r] = inv ? cmulc(v[rr][b][r], w) : cmul(v[rr][b][r], w);
+        for (int rr = 0; rr < NR; ++rr) {
+          if (R == 2) dft2(v[rr][b]);
+          else dft4(v[rr][b], inv);
         }
-      }
+      } else if (R == 2) {
+        const Tw<T> w = load_tw(tt, tf, k * twstride);
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) {
-        if (R == 2) dft2(v[rr][b]);
-        else dft4(v[rr][b], inv);
+        for (int rr = 0; rr < NR; ++rr) fma_bfly<T, T2>(v[rr][b][0], v[rr][b][1], w);
+      } else {
+        const int m1 = k * twstride;
+        const Tw<T> w1 = load_tw(tt, tf, m1), w2 = load_tw(tt, tf, 2 * m1), w3 = load_tw(tt, tf, m1 + n / 4);
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+          T2* x = v[rr][b];
+          fma_bfly<T, T2>(x[0], x[2], w2);
+          fma_bfly<T, T2>(x[1], x[3], w2);
+          fma_bfly<T, T2>(x[0], x[1], w1);
+          fma_bfly<T, T2>(x[2], x[3], w3);
+          const T2 y1 = x[2];
+          x[2] = x[1];
+          x[1] = y1;
+        }
       }
       dst[b] = t * pitch + (i - k) * R + k;
     }
@@ -94,14 +141,15 @@ __device__ __forceinline__ void fft_stage(T2* s0, int tile_stride, int pitch, in
   __syncthreads();
 }
 
-template <class T2, int NR>
-__device__ void fft_tile(T2* s0, int tile_stride, int pitch, int n, int logn, int tb, const T2* tw, bool inv) {
+template <class T, class T2, int NR>
+__device__ void fft_tile(T2* s0, int tile_stride, int pitch, int n, int logn, int tb, const T* tt, const int* tf,
+                         bool inv) {
   int p = 1;
   for (int st = 0; st < logn / 2; ++st) {
-    fft_stage<T2, 4, NR>(s0, tile_stride, pitch, n, logn - 2, tb, p, tw, inv);
+    fft_stage<T, T2, 4, NR>(s0, tile_stride, pitch, n, logn - 2, tb, p, tt, tf, inv);
     p *= 4;
   }
-  if (logn & 1) fft_stage<T2, 2, NR>(s0, tile_stride, pitch, n, logn - 1, tb, p, tw, inv);
+  if (logn & 1) fft_stage<T, T2, 2, NR>(s0, tile_stride, pitch, n, logn - 1, tb, p, tt, tf, inv);
 }
 
 template <class T2> __device__ __forceinline__ T2 ldf(const void* base, int64_t off) {
@@ -124,12 +172,14 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned cha
   const int64_t P = a.g.P;
 
   T2* tile0 = reinterpret_cast<T2*>(smem_raw);
-  T2* tw = tile0 + NR * tile_stride;
-  T2* pfac = tw + n;  // [kMaxRhs][tbmax]
+  T2* pfac = tile0 + NR * tile_stride;  // [kMaxRhs][tbmax]
   int64_t* pbase = reinterpret_cast<int64_t*>(pfac + kMaxRhs * tbmax);
+  T* tt = reinterpret_cast<T*>(pbase + tbmax);  // [2][n][3] twiddles (forward, inverse)
+  int* tf = reinterpret_cast<int*>(tt + 6 * n);  // [2][n] twiddle forms
 
-  const T2* twg = reinterpret_cast<const T2*>(a.twiddle);
-  for (int m = threadIdx.x; m < n; m += kFftThreads) tw[m] = twg[m];
+  const T* ttg = reinterpret_cast<const T*>(a.twiddle);
+  for (int m = threadIdx.x; m < 6 * n; m += kFftThreads) tt[m] = ttg[m];
+  for (int m = threadIdx.x; m < 2 * n; m += kFftThreads) tf[m] = a.twform[m];
   for (int t = threadIdx.x; t < tb; t += kFftThreads) {
     const int64_t b = b0 + t;
     const int64_t p = b % P, q = b / P;
@@ -179,7 +229,7 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned cha
   __syncthreads();
 
   // ---- transforms (all right-hand sides together)
-  if (a.flags & PASS_FWD) fft_tile<T2, NR>(tile0, tile_stride, pitch, n, logn, tb, tw, false);
+  if (a.flags & PASS_FWD) fft_tile<T, T2, NR>(tile0, tile_stride, pitch, n, logn, tb, tt, tf, false);
   if (a.flags & PASS_MUL) {
     for (int e = threadIdx.x; e < cnt; e += kFftThreads) {
       const int t = e >> logn, j = e & (n - 1);
@@ -195,7 +245,7 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned cha
     }
     __syncthreads();
   }
-  if (a.flags & PASS_INV) fft_tile<T2, NR>(tile0, tile_stride, pitch, n, logn, tb, tw, true);
+  if (a.flags & PASS_INV) fft_tile<T, T2, NR>(tile0, tile_stride, pitch, n, logn, tb, tt + 3 * n, tf + n, true);
 
   // ---- store (+ epilogue)
   bool bad = false;
@@ -237,8 +287,9 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPassArgs
 static size_t fft_smem_bytes(int n, int nrhs, size_t elem) {
   const int tbmax = std::max(1, kFftTile / n);
   const int pitch = n + 1;
-  return (size_t)tbmax * pitch * elem * nrhs + (size_t)n * elem + (size_t)kMaxRhs * tbmax * elem +
-         (size_t)tbmax * sizeof(int64_t);
+  // tiles | pencil factors | pencil bases | twiddles [2][n][3] of T | forms [2][n]
+  return (size_t)tbmax * pitch * elem * nrhs + (size_t)kMaxRhs * tbmax * elem + (size_t)tbmax * sizeof(int64_t) +
+         (size_t)6 * n * (elem / 2) + (size_t)2 * n * sizeof(int);
 }
 
 template <class T> cudaError_t launch_fft_pass(const FftPassArgs& a, cudaStream_t s) {

@@ -56,7 +56,8 @@ struct cgl_plan {
   void* fac[2][3] = {{nullptr}};        // working-precision factors / symbol vectors
   double2* fac64[2][3] = {{nullptr}};   // FP64 masters
   void* ksym[3] = {nullptr};            // K symbol vectors (periodic Runge-Kutta)
-  void* twiddle[3] = {nullptr};         // FFT twiddles per axis
+  void* twiddle[3] = {nullptr};         // FFT twiddle tables per axis: [fwd, inv][n][tau, m_re, m_im]
+  int* twform[3] = {nullptr};           // [fwd, inv][n] twiddle form (0: m = cos, 1: m = sin)
   std::vector<void*> allocations;
 
   int nwork = 0;
