@@ -38,6 +38,8 @@ UNIT = "grid-pt·steps/s"
 FP64_FMA_PER_CLK_PER_SM = 2
 N_SM = 152
 SM_MAX_MHZ = 2070.0
+# FP32: 128 FP32 FMA per clock per SM.
+FP32_PEAK_TFLOPS = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
 def fp64_peak_tflops(sm_mhz=SM_MAX_MHZ):
@@ -55,9 +57,11 @@ def parse():
     ap.add_argument("--scheme", default="split4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--workload", default="periodic128", choices=["periodic128", "neumann256", "batch512", "corrector"],
-                    help="periodic128: the headline 3D periodic workload; neumann256: the 3D Neumann "
-                         "precision study (FP64 / FP32 / BF16x3 tensor cores)")
+    ap.add_argument("--workload", default="periodic128",
+                    choices=["periodic128", "periodic256_f32", "neumann256", "batch512", "corrector"],
+                    help="periodic128: the headline 3D periodic workload; periodic256_f32: the same "
+                         "problem at 256^3 in complex64 (HBM roofline, cuFFT yardstick); neumann256: the 3D "
+                         "Neumann precision study (FP64 / FP32 / BF16x3 tensor cores)")
     ap.add_argument("--t1-steps", type=int, default=100, help="neumann256: steps of the T=1 error run")
     ap.add_argument("--corr-traj", type=int, default=96, help="corrector: training trajectories")
     ap.add_argument("--corr-iters", type=int, default=3000, help="corrector: training iterations")
@@ -162,7 +166,7 @@ def run_batch512(args):
         for pl in plans:
             pl.close()
     errs = [float(np.linalg.norm(a - r) / np.linalg.norm(r)) for a, r in zip(finals["f32"], finals["f64"])]
-    fp32_peak = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak = FP32_PEAK_TFLOPS
     f32 = res["batched_f32"]
     line = {
         "metric": METRIC, "value": f32["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -335,10 +339,118 @@ def run_neumann256(args):
         "simt_kernels": {
             "mode_pass_f64": {"achieved_tflops": f64k["flops"] / (f64k["total_ms"] / 1e3) / 1e12,
                               "frac_of_fp64_peak": f64k["flops"] / (f64k["total_ms"] / 1e3) / 1e12 / fp64_peak_tflops()},
-            "mode_pass_f32": {"achieved_tflops": f32k["flops"] / (f32k["total_ms"] / 1e3) / 1e12}},
+            "mode_pass_f32": {"achieved_tflops": f32k["flops"] / (f32k["total_ms"] / 1e3) / 1e12,
+                              "frac_of_fp32_peak": f32k["flops"] / (f32k["total_ms"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
+            "fma_microbenchmark_tflops": measured_fma_peaks()},
         "kernels": prof, "clocks": clk.summary(),
     }
     print(json.dumps(line))
+
+
+def run_periodic_f32(args):
+    """3D cubic-quintic periodic 256^3 (the 128^3 workload's parameters and
+    initial data on a finer grid), split4, tau = 0.005, in complex64 and in
+    complex128: throughput, the FP32 FFT pass against the HBM roofline, the
+    FP32 result's relative L2 error against the FP64 path after `chunk`
+    steps, and cuFFT (torch.fft) applying the same linear flow as a
+    yardstick."""
+    import torch
+    from paper_2403_02816_gb300 import native as nat
+
+    dev = torch.device("cuda", 0)
+    nat.load()
+    n = args.n if args.n != 128 else 256
+    w = I.workload_3d_periodic(n)
+    U0 = I.u0_3d_periodic(w)
+    N = w.prob.N
+    chunk = args.chunk
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, K, W):
+        for _ in range(W):
+            fn()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(K):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / K
+
+    res, finals, prof = {}, {}, {}
+    W = max(args.warmup, 3)
+    with Clocks(0) as clk:
+        for prec in ("f32", "f64"):
+            dt = torch.complex64 if prec == "f32" else torch.complex128
+            with nat.Plan(w.prob, w.tau, args.scheme, prec) as plan:
+                u = nat.to_device(U0, dt, dev)
+                ms = timed(lambda: plan.step(u, chunk), args.steps if prec == "f32" else 2, W)
+                res[prec] = {"grid_pt_steps_per_s": N * chunk / (ms / 1e3), "ms_per_time_step": ms / chunk}
+                prof[prec] = plan.profile(u, 1)
+                v = nat.to_device(U0, dt, dev)
+                plan.step(v, chunk)
+                torch.cuda.synchronize()
+                res[prec]["device_status"] = plan.device_status()
+                finals[prec] = v
+                if prec == "f32":
+                    # yardstick: the linear flow exp(tau K) u by this library and by cuFFT
+                    y = nat.to_device(U0, dt, dev)
+                    ours_ms = timed(lambda: plan.linear_flow(y, 1.0), 10, W)
+                    E = None
+                    for mu in range(3):
+                        f = torch.from_numpy(plan.factor(1.0, mu) * w.prob.n[mu]).to(dev, torch.complex64)
+                        shape = [1, 1, 1]
+                        shape[2 - mu] = -1
+                        E = f.view(shape) if E is None else E * f.view(shape)
+                    x = nat.to_device(U0, dt, dev)
+                    z = torch.empty_like(x)
+
+                    def lib_flow():
+                        torch.fft.ifftn(E * torch.fft.fftn(x), out=z)
+
+                    lib_ms = timed(lib_flow, 10, W)
+                    yy = nat.to_device(U0, dt, dev)
+                    plan.linear_flow(yy, 1.0)
+                    lib_flow()
+                    torch.cuda.synchronize()
+                    agree = float(torch.linalg.vector_norm(yy - z) / torch.linalg.vector_norm(z))
+                    res["linear_flow_yardstick"] = {
+                        "ours_ms": ours_ms, "cufft_fftn_mul_ifftn_ms": lib_ms, "ours_over_cufft_speed": lib_ms / ours_ms,
+                        "rel_l2_ours_vs_cufft": agree}
+    e2, einf, _ = nat.cgl_rel_error(finals["f32"].to(torch.complex128), finals["f64"], nat.CGL_F64)
+    res["f32"]["rel_l2_vs_f64"] = e2
+    res["f32"]["rel_inf_vs_f64"] = einf
+    res["f32"]["speedup_vs_f64"] = res["f32"]["grid_pt_steps_per_s"] / res["f64"]["grid_pt_steps_per_s"]
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6790.0))
+    k = [r for r in prof["f32"] if r["name"] == "fft_pass_f32"][0]
+    achieved = k["bytes"] / (k["total_ms"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "fft_pass_f32", "launches_profiled": k["launches"],
+                "avg_launch_ms": k["total_ms"] / k["launches"],
+                "bytes_counted": "8 B per complex64 value of every field read or written by the pass",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "share": k["total_ms"] / sum(r["total_ms"] for r in prof["f32"])}
+    line = {
+        "metric": METRIC, "value": res["f32"]["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": W, "ms_per_step": res["f32"]["ms_per_time_step"] * chunk,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "scheme": args.scheme, "tau": w.tau, "grid": list(w.prob.n),
+                   "time_steps_per_bench_step": chunk, "l2": "flushed (256 MiB write) between timed iterations"},
+        "precisions": res, "roofline": roofline, "kernels": prof, "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
+def measured_fma_peaks():
+    """FP64 / FP32 FMA throughput measured by the library's microbenchmark."""
+    from paper_2403_02816_gb300 import native as nat
+    return {"f64_tflops": nat.cgl_measure_fma_peak("f64", 4096), "f32_tflops": nat.cgl_measure_fma_peak("f32", 65536)}
 
 
 class Clocks:
@@ -444,6 +556,9 @@ def main():
     if args.workload == "neumann256":
         run_neumann256(args)
         return
+    if args.workload == "periodic256_f32":
+        run_periodic_f32(args)
+        return
     if args.workload == "batch512":
         run_batch512(args)
         return
@@ -520,6 +635,9 @@ def main():
                 "avg_launch_ms": dom["total_ms"] / dom["launches"],
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz (1.25 TFLOP/s nominal FP64)",
                 "share": dom["total_ms"] / sum(r["total_ms"] for r in prof)}
+    fma = measured_fma_peaks()
+    roofline["peak_fma_microbenchmark"] = fma["f64_tflops"]
+    roofline["frac_of_fma_microbenchmark"] = achieved / fma["f64_tflops"]
 
     # end to end through the C ABI with host buffers (pinned)
     host = torch.from_numpy(np.ascontiguousarray(U0.T)).pin_memory()

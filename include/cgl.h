@@ -328,6 +328,22 @@ int cgl_corrector_destroy(cgl_corrector* c);
 int cgl_rel_error_noalloc(const void* x, const void* y, int64_t count, int precision,
                           double* out, void* stream);
 
+/*
+ * FMA throughput of the current device (a measurement aid, not part of the
+ * method): the ALU peak that the FP64 / FP32 SIMT kernels' roofline
+ * fractions are quoted against, measured rather than derived from clocks.
+ *
+ * precision  CGL_F64 (DFMA) or CGL_F32 (FFMA).
+ * iters      rounds of 8 independent FMA chains per thread (>= 1); choose
+ *            it so one launch runs for milliseconds (e.g. 4096 for FP64,
+ *            65536 for FP32).  The grid is 8 blocks of 256 threads per SM.
+ * tflops     out: 2 * 8 * iters * threads / seconds / 1e12, timed with CUDA
+ *            events around the second of two launches on `stream`.
+ * Allocates and frees a small output buffer on `stream`; synchronous.
+ * Errors: EINVAL (bad precision, iters < 1, NULL tflops), ENOMEM, ECUDA.
+ */
+int cgl_measure_fma_peak(int precision, int iters, double* tflops, void* stream);
+
 /* Message for a status code (static string). */
 const char* cgl_strerror(int status);
 

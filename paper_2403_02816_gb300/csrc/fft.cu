@@ -284,6 +284,316 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPassArgs
   fft_pass_body<T, NR>(a, smem_raw);
 }
 
+// ---------------------------------------------------------------------------
+// Four-step pass with the pencils in registers (FP32, 16 <= n <= 1024).  n = A * B with B = 2^ceil(log2(n)/2) >= A.  A pencil
+// is held by A threads, thread t holding the B elements j = t + A r.  The
+// DFT splits as X[s + B q] = sum_t w_A^(t q) w_n^(t s) sum_r x[t + A r] w_B^(r s):
+// the inner B-point DFT runs in each thread's registers, then the twiddle
+// w_n^(t s), then one transpose through shared memory (row s of a pencil's
+// B x A block, padded rows and pencils so no two lanes of a half-warp share
+// a bank), then A-point DFTs over t, again in registers.  Thread u ends up
+// holding X[u + A r'], r' = 0..B-1: the same layout it loaded, so the symbol
+// multiply and the inverse transform follow without another exchange, and
+// a forward-symbol-inverse pass touches shared memory for two transposes
+// where the Stockham pass above reads and writes its tile once per stage.
+// Threads map to (pencil, t) with t fastest when pencils are contiguous
+// (P = 1) and the pencil fastest otherwise, so every load and store of a
+// warp covers whole contiguous runs.  All loads of a thread are issued before
+// their first use.
+// ---------------------------------------------------------------------------
+
+constexpr size_t kFourStepExMax = 80 * 1024;  // above this, the fields share one exchange buffer
+
+template <int LOGN> struct FourStep {
+  static constexpr int n = 1 << LOGN;
+  static constexpr int B = 1 << ((LOGN + 1) / 2);  // elements per thread
+  static constexpr int A = n / B;                  // threads per pencil
+  static constexpr int PP = kFftThreads / A;       // pencils per CTA
+  static constexpr int RS = A + 1;                 // row stride of the exchange block
+  static constexpr int PS = (B * RS) | 1;          // pencil stride (odd)
+};
+
+// One in-register Stockham stage of radix R on M values (all indices are
+// compile-time): butterfly i (k = i mod P) takes v[i + r M/R], applies
+// w_(PR)^(r k) (table entries of an n-point table, n = NTAB) and writes
+// o[(i - k) R + k + r P].
+template <class T, class T2, int M, int R, int P, int NTAB>
+__device__ __forceinline__ void reg_stage(T2* v, const T* tt, const int* tf, bool inv) {
+  constexpr int nb = M / R;
+  constexpr int ts = NTAB / (P * R);
+  T2 o[M];
+#pragma unroll
+  for (int i = 0; i < nb; ++i) {
+    const int k = i % P;
+    T2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[i + r * nb];
+    if (k == 0) {
+      if (R == 2) dft2(x);
+      else dft4(x, inv);
+    } else if (R == 2) {
+      const Tw<T> w = load_tw(tt, tf, k * ts);
+      fma_bfly<T, T2>(x[0], x[1], w);
+    } else {
+      const int m1 = k * ts;
+      const Tw<T> w1 = load_tw(tt, tf, m1), w2 = load_tw(tt, tf, 2 * m1), w3 = load_tw(tt, tf, m1 + NTAB / 4);
+      fma_bfly<T, T2>(x[0], x[2], w2);
+      fma_bfly<T, T2>(x[1], x[3], w2);
+      fma_bfly<T, T2>(x[0], x[1], w1);
+      fma_bfly<T, T2>(x[2], x[3], w3);
+      const T2 y1 = x[2];
+      x[2] = x[1];
+      x[1] = y1;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[(i - k) * R + k + r * P] = x[r];
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) v[j] = o[j];
+}
+
+// M-point DFT of v in registers, natural order in and out: radix-4 stages
+// while they fit, then one radix-2 stage.
+template <class T, class T2, int M, int P, int NTAB>
+__device__ __forceinline__ void dft_reg(T2* v, const T* tt, const int* tf, bool inv) {
+  if constexpr (P * 4 <= M) {
+    reg_stage<T, T2, M, 4, P, NTAB>(v, tt, tf, inv);
+    dft_reg<T, T2, M, P * 4, NTAB>(v, tt, tf, inv);
+  } else if constexpr (P * 2 <= M) {
+    reg_stage<T, T2, M, 2, P, NTAB>(v, tt, tf, inv);
+  }
+}
+
+// One transform (forward or inverse) of the NR fields held by this thread.
+// tt/tf/tw: this direction's tables; ex: exchange buffers.
+template <class T, class T2, int NR, int LOGN>
+__device__ __forceinline__ void four_step(T2 (&v)[NR][FourStep<LOGN>::B], T2* ex, int pp, int t, const T* tt,
+                                          const int* tf, const T2* tw, bool inv) {
+  using G = FourStep<LOGN>;
+  constexpr int A = G::A, B = G::B, PS = G::PS, RS = G::RS, PP = G::PP;
+  constexpr bool kSeq = (size_t)NR * PP * PS * sizeof(T2) > kFourStepExMax;
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) {
+    dft_reg<T, T2, B, 1, G::n>(v[rr], tt, tf, inv);
+#pragma unroll
+    for (int s = 1; s < B; ++s) v[rr][s] = cmul(v[rr][s], tw[t * s]);
+  }
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) {
+    T2* e = ex + (kSeq ? 0 : rr * PP * PS) + pp * PS;
+    if (kSeq || rr == 0) __syncthreads();  // earlier readers of the buffer are done
+#pragma unroll
+    for (int s = 0; s < B; ++s) e[s * RS + t] = v[rr][s];
+    if (kSeq || rr == NR - 1) __syncthreads();
+    if (kSeq || rr == NR - 1) {
+#pragma unroll
+      for (int r2 = kSeq ? rr : 0; r2 <= rr; ++r2) {
+        const T2* e2 = ex + (kSeq ? 0 : r2 * PP * PS) + pp * PS;
+#pragma unroll
+        for (int m = 0; m < B / A; ++m) {
+          T2 y[A];
+#pragma unroll
+          for (int tq = 0; tq < A; ++tq) y[tq] = e2[(t + A * m) * RS + tq];
+          dft_reg<T, T2, A, 1, G::n>(y, tt, tf, inv);
+#pragma unroll
+          for (int q = 0; q < A; ++q) v[r2][m + (B / A) * q] = y[q];
+        }
+      }
+    }
+  }
+}
+
+template <class T, int NR, int LOGN>
+__global__ void __launch_bounds__(kFftThreads) fft4_pass_kernel(const FftPassArgs a) {
+  using T2 = typename C2<T>::type;
+  using G = FourStep<LOGN>;
+  constexpr int n = G::n, A = G::A, B = G::B, PP = G::PP, PS = G::PS;
+  constexpr bool kSeq = (size_t)NR * PP * PS * sizeof(T2) > kFourStepExMax;
+  constexpr int NX = kSeq ? 1 : NR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* ex = reinterpret_cast<T2*>(smem_raw);  // [NX][PP][PS]
+  T2* tw = ex + NX * PP * PS;                // [2][n] plain twiddles (forward, inverse)
+  T2* pfac = tw + 2 * n;                     // [kMaxRhs][PP]
+  int64_t* pbase = reinterpret_cast<int64_t*>(pfac + kMaxRhs * PP);
+  T* tt = reinterpret_cast<T*>(pbase + PP);  // [2][n][3]
+  int* tf = reinterpret_cast<int*>(tt + 6 * n);
+
+  const int64_t P = a.g.P;
+  const int64_t b0 = (int64_t)blockIdx.x * PP;
+  const int tb = (int)min((int64_t)PP, a.g.npencils - b0);
+  const T* ttg = reinterpret_cast<const T*>(a.twiddle);
+  for (int m = threadIdx.x; m < 6 * n; m += kFftThreads) tt[m] = ttg[m];
+  for (int m = threadIdx.x; m < 2 * n; m += kFftThreads) {
+    const int form = a.twform[m];
+    const T tau = ttg[3 * m], mre = ttg[3 * m + 1], mim = ttg[3 * m + 2];
+    tf[m] = form;
+    tw[m] = form ? mk<T2>(tau * mre, mim) : mk<T2>(mre, tau * mre);
+  }
+  for (int t = threadIdx.x; t < tb; t += kFftThreads) {
+    const int64_t b = b0 + t;
+    const int64_t p = b % P, q = b / P;
+    pbase[t] = p + P * (int64_t)n * q;
+    if (a.flags & PASS_MUL) {
+      int64_t kk[3] = {0, 0, 0};
+      int64_t rem = p;
+      for (int mu = 0; mu < a.g.axis; ++mu) { kk[mu] = rem % a.g.n[mu]; rem /= a.g.n[mu]; }
+      rem = q;
+      for (int mu = a.g.axis + 1; mu < a.g.d; ++mu) { kk[mu] = rem % a.g.n[mu]; rem /= a.g.n[mu]; }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const Symbol& S = a.sym[r];
+        T2 acc = S.sum_form ? mk<T2>(0, 0) : mk<T2>(1, 0);
+        for (int mu = 0; mu < a.g.d; ++mu) {
+          if (mu == a.g.axis) continue;
+          const T2 v = reinterpret_cast<const T2*>(S.vec[mu])[kk[mu]];
+          acc = S.sum_form ? cadd(acc, v) : cmul(acc, v);
+        }
+        pfac[r * PP + t] = acc;
+      }
+    }
+  }
+  __syncthreads();
+
+  int pp, t;
+  if (P == 1) { t = threadIdx.x % A; pp = threadIdx.x / A; }
+  else { pp = threadIdx.x % PP; t = threadIdx.x / PP; }
+  const bool live = pp < tb;
+  const int64_t base = live ? pbase[pp] : 0;
+
+  // ---- load (+ prologue): element j = t + A r of pencil pp
+  T2 v[NR][B];
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+    for (int r = 0; r < B; ++r) v[rr][r] = mk<T2>(0, 0);
+  if (live) {
+    if (a.flags & PASS_PRO) {
+      T2 in0[B], in1[B];
+#pragma unroll
+      for (int r = 0; r < B; ++r) in0[r] = ldf<T2>(a.f.in[0], base + P * (t + A * r));
+      if (a.f.nin > 1) {
+#pragma unroll
+        for (int r = 0; r < B; ++r) in1[r] = ldf<T2>(a.f.in[1], base + P * (t + A * r));
+      } else {
+#pragma unroll
+        for (int r = 0; r < B; ++r) in1[r] = in0[r];
+      }
+#pragma unroll
+      for (int r = 0; r < B; ++r) {
+        T2 in[2] = {in0[r], in1[r]}, z[2];
+        apply_prologue<T, T2>(a.op, in, z);
+        v[0][r] = z[0];
+        if (NR > 1) v[NR - 1][r] = z[1];
+      }
+    } else {
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+        for (int r = 0; r < B; ++r) v[rr][r] = ldf<T2>(a.f.work[rr], base + P * (t + A * r));
+    }
+  }
+
+  // ---- transforms
+  if (a.flags & PASS_FWD) four_step<T, T2, NR, LOGN>(v, ex, pp, t, tt, tf, tw, false);
+  if (a.flags & PASS_MUL) {
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) {
+      const Symbol& S = a.sym[rr];
+      const T2* va = reinterpret_cast<const T2*>(S.vec[a.g.axis]);
+      const T2 c = pfac[rr * PP + (live ? pp : 0)];
+#pragma unroll
+      for (int r = 0; r < B; ++r) {
+        const T2 e = va[t + A * r];
+        v[rr][r] = cmul(v[rr][r], S.sum_form ? cadd(c, e) : cmul(c, e));
+      }
+    }
+  }
+  if (a.flags & PASS_INV) four_step<T, T2, NR, LOGN>(v, ex, pp, t, tt + 3 * n, tf + n, tw + n, true);
+
+  // ---- store (+ epilogue), four elements at a time with their extra inputs loaded first
+  if (!live) return;
+  bool bad = false;
+  if (a.flags & PASS_EPI) {
+    constexpr int CH = B < 4 ? B : 4;
+#pragma unroll
+    for (int r0 = 0; r0 < B; r0 += CH) {
+      T2 ex4[CH][kMaxExtra];
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int x = 0; x < kMaxExtra; ++x)
+          if (x < a.f.nextra) ex4[c][x] = ldf<T2>(a.f.extra[x], base + P * (t + A * (r0 + c)));
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int64_t off = base + P * (t + A * (r0 + c));
+        T2 y[2] = {v[0][r0 + c], v[NR - 1][r0 + c]}, o[2];
+        const int no = apply_epilogue<T, T2>(a.op, y, ex4[c], o);
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          if (x < no && x < a.f.nout) {
+            stf<T2>(a.f.out[x], off, o[x]);
+            bad |= !finite2(o[x]);
+          }
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+      for (int r = 0; r < B; ++r) stf<T2>(a.f.work[rr], base + P * (t + A * r), v[rr][r]);
+  }
+  if (bad && a.status) atomicOr(a.status, 1);
+}
+
+template <class T, int LOGN> static size_t fft4_smem_bytes(int nrhs) {
+  using G = FourStep<LOGN>;
+  using T2 = typename C2<T>::type;
+  const bool seq = (size_t)nrhs * G::PP * G::PS * sizeof(T2) > kFourStepExMax;
+  const size_t nx = seq ? 1 : (size_t)nrhs;
+  // exchange | plain twiddles | pencil factors | pencil bases | FMA twiddles | forms
+  return nx * G::PP * G::PS * sizeof(T2) + 2 * (size_t)G::n * sizeof(T2) + (size_t)kMaxRhs * G::PP * sizeof(T2) +
+         (size_t)G::PP * sizeof(int64_t) + 6 * (size_t)G::n * sizeof(T) + 2 * (size_t)G::n * sizeof(int);
+}
+
+// Largest log2 n the four-step pass handles for element type T.  FP64 keeps
+// the Stockham pass: its FP64-bound passes run faster with the Stockham
+// kernel's ~100 registers (two CTAs per SM) than with the four-step
+// kernel's ~230 (one CTA per SM): 7.9e8 against 6.5e8 grid-pt.steps/s on
+// the 128^3 split4 workload.
+template <class T> constexpr int fft4_max_logn() { return sizeof(T) == 4 ? 10 : 0; }
+constexpr int kFft4MinLogn = 4;
+
+template <class T, int LOGN>
+static cudaError_t launch_fft4(const FftPassArgs& a, cudaStream_t s) {
+  using G = FourStep<LOGN>;
+  const int64_t grid = (a.g.npencils + G::PP - 1) / G::PP;
+  const size_t smem = fft4_smem_bytes<T, LOGN>(a.f.nrhs);
+  if (a.f.nrhs > 1) fft4_pass_kernel<T, 2, LOGN><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
+  else fft4_pass_kernel<T, 1, LOGN><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class T, int LOGN> static cudaError_t prepare_fft4() {
+  cudaError_t e = cudaFuncSetAttribute(fft4_pass_kernel<T, 1, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fft4_smem_bytes<T, LOGN>(1));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fft4_pass_kernel<T, 2, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fft4_smem_bytes<T, LOGN>(2));
+}
+
+// Dispatch on log2 n (compile-time sizes).  Returns cudaErrorNotSupported
+// for sizes outside [kFft4MinLogn, fft4_max_logn<T>()].
+template <class T, int LOGN = kFft4MinLogn>
+static cudaError_t fft4_dispatch(int logn, bool prepare, const FftPassArgs* a, cudaStream_t s) {
+  if constexpr (LOGN > fft4_max_logn<T>()) {
+    return cudaErrorNotSupported;
+  } else {
+    if (logn == LOGN) return prepare ? prepare_fft4<T, LOGN>() : launch_fft4<T, LOGN>(*a, s);
+    return fft4_dispatch<T, LOGN + 1>(logn, prepare, a, s);
+  }
+}
+
 static size_t fft_smem_bytes(int n, int nrhs, size_t elem) {
   const int tbmax = std::max(1, kFftTile / n);
   const int pitch = n + 1;
@@ -295,6 +605,8 @@ static size_t fft_smem_bytes(int n, int nrhs, size_t elem) {
 template <class T> cudaError_t launch_fft_pass(const FftPassArgs& a, cudaStream_t s) {
   using T2 = typename C2<T>::type;
   const int n = (int)a.g.n_ax;
+  const int logn = __builtin_ctz((unsigned)n);
+  if (logn >= kFft4MinLogn && logn <= fft4_max_logn<T>()) return fft4_dispatch<T>(logn, false, &a, s);
   const int tbmax = std::max(1, kFftTile / n);
   const int64_t grid = (a.g.npencils + tbmax - 1) / tbmax;
   const size_t smem = fft_smem_bytes(n, a.f.nrhs, sizeof(T2));
@@ -310,7 +622,11 @@ template <class T> cudaError_t launch_fft_pass(const FftPassArgs& a, cudaStream_
 template <class T> cudaError_t prepare_fft_pass() {
   cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fft_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem);
+  e = cudaFuncSetAttribute(fft_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem);
+  if (e != cudaSuccess) return e;
+  for (int logn = kFft4MinLogn; logn <= fft4_max_logn<T>(); ++logn)
+    if ((e = fft4_dispatch<T>(logn, true, nullptr, nullptr)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 template cudaError_t prepare_fft_pass<double>();

@@ -89,6 +89,7 @@ def load() -> ctypes.CDLL:
         "cgl_profile_step": (I, [P, VP, I64, VP, ctypes.POINTER(cgl_kernel_time), I, ctypes.POINTER(I)]),
         "cgl_rel_error": (I, [VP, VP, I64, I, ctypes.POINTER(D), VP]),
         "cgl_rel_error_noalloc": (I, [VP, VP, I64, I, ctypes.POINTER(D), VP]),
+        "cgl_measure_fma_peak": (I, [I, I, ctypes.POINTER(D), VP]),
         "cgl_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(cgl_problem), D, I, I, VP]),
         "cgl_batch_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(SZ),
                                ctypes.POINTER(I)]),
@@ -163,6 +164,14 @@ def cgl_rel_error(x, y, precision, stream=None):
     check(load().cgl_rel_error(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
                                int(precision), out, _stream_handle(stream)), "cgl_rel_error")
     return out[0], out[1], int(out[2])
+
+
+def cgl_measure_fma_peak(precision, iters, stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s ("f64" or "f32")."""
+    out = ctypes.c_double()
+    check(load().cgl_measure_fma_peak(PRECISIONS[precision], int(iters), ctypes.byref(out), _stream_handle(stream)),
+          "cgl_measure_fma_peak")
+    return out.value
 
 
 class Plan:

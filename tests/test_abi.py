@@ -76,6 +76,10 @@ def test_null_arguments(lib):
     assert lib.cgl_plan_destroy(None) == nat.CGL_OK
     assert lib.cgl_rel_error(None, None, 4, 0, None, None) == nat.CGL_EINVAL
     assert lib.cgl_plan_info(None, None, None, None) == nat.CGL_EINVAL
+    assert lib.cgl_measure_fma_peak(nat.CGL_F64, 16, None, None) == nat.CGL_EINVAL
+    out = ctypes.c_double()
+    assert lib.cgl_measure_fma_peak(nat.CGL_F64, 0, ctypes.byref(out), None) == nat.CGL_EINVAL
+    assert lib.cgl_measure_fma_peak(nat.CGL_BF16X3, 16, ctypes.byref(out), None) == nat.CGL_EINVAL
 
 
 def test_batch_validation_before_any_cuda_call(lib):

@@ -297,3 +297,12 @@ def test_rel_error_kernel():
     x[3] = np.nan
     e2, einf, nf = nat.cgl_rel_error(torch.from_numpy(x).cuda(), ty, nat.CGL_F64)
     assert nf == 1
+
+
+def test_fma_peak_microbenchmark():
+    """The measured FMA rates lie near the unit-count peaks (152 SMs x 2 FP64
+    or 128 FP32 FMA per clock x 2 flop at 1.0-2.1 GHz)."""
+    f64 = nat.cgl_measure_fma_peak("f64", 1024)
+    f32 = nat.cgl_measure_fma_peak("f32", 8192)
+    assert 0.3 < f64 < 1.4
+    assert 20.0 < f32 < 90.0
