@@ -430,8 +430,11 @@ def run_periodic_f32(args):
     hbm = float(peaks.get("hbm_gbs", 6790.0))
     k = [r for r in prof["f32"] if r["name"] == "fft_pass_f32"][0]
     achieved = k["bytes"] / (k["total_ms"] / 1e3) / 1e9
+    traffic = None
+    if n == 256 and args.scheme == "split4":
+        traffic = profiled_traffic("fft4_pass_f32_dram_split4_256cubed.md", ["fft.cu", "cgl_internal.cuh"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "fft_pass_f32", "launches_profiled": k["launches"],
+                "traffic": traffic, "kernel": "fft_pass_f32", "launches_profiled": k["launches"],
                 "avg_launch_ms": k["total_ms"] / k["launches"],
                 "bytes_counted": "8 B per complex64 value of every field read or written by the pass",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",

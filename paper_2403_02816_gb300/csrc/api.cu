@@ -457,6 +457,7 @@ void build_program(cgl_plan* p) {
       break;
     }
   }
+  for (Sweep& s : p->sweeps) single_copies(s.op);
 }
 
 bool finite_all(std::initializer_list<double> v) {
@@ -702,6 +703,7 @@ int cgl_linear_flow(cgl_plan* p, double c, void* u, void* stream) {
   CUDA_TRY(cudaSetDevice(p->dev));
   Sweep s;
   s.op.nl = NlParams{p->a3, p->b3, p->a4, p->b4, p->cubic, p->tau};
+  single_copies(s.op);
   s.fac[0] = idx;
   return enqueue_sweep(p, s, u, (cudaStream_t)stream);
 }

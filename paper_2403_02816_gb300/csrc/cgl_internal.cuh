@@ -69,6 +69,9 @@ struct NlParams {
   double a3, b3, a4, b4;
   int cubic;       // a4 = b4 = 0: exact flow (eq. exsolcub); else one RK4 step
   double tau;
+  // FP32 copies (set by single_copies): FP32 kernels read these, so no
+  // FP64-to-FP32 conversion runs per grid point
+  float a3f, b3f, a4f, b4f, tauf;
 };
 
 struct OpArgs {
@@ -78,13 +81,32 @@ struct OpArgs {
   int rk_scheme;   // 4 or 2 (EPI_RK)
   int rk_stage;    // 1-based stage (EPI_RK)
   NlParams nl;
+  float t0f, t1f, tef;  // FP32 copies of t0, t1, te
 };
+
+// Fill the FP32 copies of an operator's parameters.
+inline void single_copies(OpArgs& o) {
+  o.t0f = (float)o.t0;
+  o.t1f = (float)o.t1;
+  o.tef = (float)o.te;
+  o.nl.a3f = (float)o.nl.a3;
+  o.nl.b3f = (float)o.nl.b3;
+  o.nl.a4f = (float)o.nl.a4;
+  o.nl.b4f = (float)o.nl.b4;
+  o.nl.tauf = (float)o.nl.tau;
+}
+
+// The parameter in the working precision: the FP64 value or its FP32 copy.
+template <class T> __device__ __forceinline__ T pv(double d, float f) {
+  if constexpr (sizeof(T) == sizeof(double)) return d;
+  else return f;
+}
 
 // g(u) = (a3 + i b3)|u|^2 u + (a4 + i b4)|u|^4 u  (eq. 1)
 template <class T, class T2> __device__ __forceinline__ T2 nl_g(const NlParams& p, T2 u) {
   const T rho = fma(u.x, u.x, u.y * u.y);
-  const T cr = rho * fma(T(p.a4), rho, T(p.a3));
-  const T ci = rho * fma(T(p.b4), rho, T(p.b3));
+  const T cr = rho * fma(pv<T>(p.a4, p.a4f), rho, pv<T>(p.a3, p.a3f));
+  const T ci = rho * fma(pv<T>(p.b4, p.b4f), rho, pv<T>(p.b3, p.b3f));
   return mk<T2>(fma(cr, u.x, -ci * u.y), fma(cr, u.y, ci * u.x));
 }
 
@@ -113,7 +135,7 @@ template <class T, class T2> __device__ __forceinline__ T2 exact_power_flow(T2 u
 // phi_t: nonlinear flow of the splitting schemes (Sec. 2.1): exact for the
 // cubic model (eq. exsolcub); one RK4 step of u' = g(u) otherwise (Sec. 4.3).
 template <class T, class T2> __device__ __forceinline__ T2 nl_flow(const NlParams& p, T2 u, T t) {
-  if (p.cubic) return exact_power_flow<T, T2>(u, T(p.a3), T(p.b3), 1, t);
+  if (p.cubic) return exact_power_flow<T, T2>(u, pv<T>(p.a3, p.a3f), pv<T>(p.b3, p.b3f), 1, t);
   const T h = t * T(0.5);
   const T2 k1 = nl_g<T, T2>(p, u);
   const T2 k2 = nl_g<T, T2>(p, caxpy(u, h, k1));
@@ -127,11 +149,11 @@ template <class T, class T2>
 __device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2* z) {
   switch (o.pro) {
     case PRO_FLOW:
-      z[0] = nl_flow<T, T2>(o.nl, in[0], T(o.t0));
+      z[0] = nl_flow<T, T2>(o.nl, in[0], pv<T>(o.t0, o.t0f));
       break;
     case PRO_FLOW2:
-      z[0] = nl_flow<T, T2>(o.nl, in[0], T(o.t0));
-      z[1] = nl_flow<T, T2>(o.nl, in[0], T(o.t1));
+      z[0] = nl_flow<T, T2>(o.nl, in[0], pv<T>(o.t0, o.t0f));
+      z[1] = nl_flow<T, T2>(o.nl, in[0], pv<T>(o.t1, o.t1f));
       break;
     case PRO_LAW4:
       z[0] = in[0];
@@ -139,7 +161,7 @@ __device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2
       break;
     case PRO_LAW2: {
       const T2 gn = nl_g<T, T2>(o.nl, in[0]);
-      const T tau = T(o.nl.tau);
+      const T tau = pv<T>(o.nl.tau, o.nl.tauf);
       z[0] = caxpy(in[0], tau, gn);
       z[1] = caxpy(in[0], tau * T(0.5), gn);
       break;
@@ -157,7 +179,7 @@ __device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2
 //   RK2 s=1   : acc = k; x_next = u_n + tau k ; s=2: u_n + tau/2 (acc + k)
 template <class T, class T2>
 __device__ __forceinline__ int rk_stage(const OpArgs& o, T2 y, const T2* e, T2* out) {
-  const T tau = T(o.nl.tau);
+  const T tau = pv<T>(o.nl.tau, o.nl.tauf);
   const T2 k = cadd(y, nl_g<T, T2>(o.nl, e[0]));
   if (o.rk_scheme == 4) {
     switch (o.rk_stage) {
@@ -175,17 +197,17 @@ __device__ __forceinline__ int rk_stage(const OpArgs& o, T2 y, const T2* e, T2* 
 // Returns the number of outputs written.
 template <class T, class T2>
 __device__ __forceinline__ int apply_epilogue(const OpArgs& o, const T2* y, const T2* e, T2* out) {
-  const T tau = T(o.nl.tau);
+  const T tau = pv<T>(o.nl.tau, o.nl.tauf);
   switch (o.epi) {
     case EPI_FLOW:
-      out[0] = nl_flow<T, T2>(o.nl, y[0], T(o.te));
+      out[0] = nl_flow<T, T2>(o.nl, y[0], pv<T>(o.te, o.tef));
       return 1;
     case EPI_FLOW2:
-      out[0] = nl_flow<T, T2>(o.nl, y[0], T(o.te));
-      out[1] = nl_flow<T, T2>(o.nl, y[1], T(o.te));
+      out[0] = nl_flow<T, T2>(o.nl, y[0], pv<T>(o.te, o.tef));
+      out[1] = nl_flow<T, T2>(o.nl, y[1], pv<T>(o.te, o.tef));
       return 2;
     case EPI_SPLIT4: {
-      const T2 f = nl_flow<T, T2>(o.nl, y[0], T(o.te));
+      const T2 f = nl_flow<T, T2>(o.nl, y[0], pv<T>(o.te, o.tef));
       out[0] = mk<T2>(fma(T(4) / T(3), f.x, -(T(1) / T(3)) * e[0].x),
                       fma(T(4) / T(3), f.y, -(T(1) / T(3)) * e[0].y));
       return 1;

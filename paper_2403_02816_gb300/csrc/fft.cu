@@ -467,23 +467,50 @@ __global__ void __launch_bounds__(kFftThreads) fft4_pass_kernel(const FftPassArg
 #pragma unroll
     for (int r = 0; r < B; ++r) v[rr][r] = mk<T2>(0, 0);
   if (live) {
-    if (a.flags & PASS_PRO) {
-      T2 in0[B], in1[B];
+    if ((a.flags & PASS_PRO) && a.op.pro != PRO_NONE) {
+      // an operator prologue (one input field): all loads first, parked in
+      // this thread's own slots of the exchange buffer (free until the first
+      // transpose, whose opening barrier orders these reads before its
+      // writes); then the operator as a rolled loop over chunks of four
+      // elements, each chunk appended at the top of v while v shifts down
+      // by four, for the reason given at the store
+      constexpr int CH = B < 4 ? B : 4;
+      T2* park = ex + pp * PS;
+      {
+        T2 in0[B];
 #pragma unroll
-      for (int r = 0; r < B; ++r) in0[r] = ldf<T2>(a.f.in[0], base + P * (t + A * r));
-      if (a.f.nin > 1) {
+        for (int r = 0; r < B; ++r) in0[r] = ldf<T2>(a.f.in[0], base + P * (t + A * r));
 #pragma unroll
-        for (int r = 0; r < B; ++r) in1[r] = ldf<T2>(a.f.in[1], base + P * (t + A * r));
-      } else {
-#pragma unroll
-        for (int r = 0; r < B; ++r) in1[r] = in0[r];
+        for (int r = 0; r < B; ++r) park[t + A * r] = in0[r];
       }
+#pragma unroll 1
+      for (int r0 = 0; r0 < B; r0 += CH) {
+        T2 z0[CH], z1[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const T2 x = park[t + A * (r0 + c)];
+          T2 in[2] = {x, x}, z[2];
+          apply_prologue<T, T2>(a.op, in, z);
+          z0[c] = z[0];
+          z1[c] = z[1];
+        }
+#pragma unroll
+        for (int r = 0; r + CH < B; ++r) {
+          v[0][r] = v[0][r + CH];
+          if (NR > 1) v[NR - 1][r] = v[NR - 1][r + CH];
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          v[0][B - CH + c] = z0[c];
+          if (NR > 1) v[NR - 1][B - CH + c] = z1[c];
+        }
+      }
+    } else if (a.flags & PASS_PRO) {
+      // copy prologue: z_r = in_r
 #pragma unroll
       for (int r = 0; r < B; ++r) {
-        T2 in[2] = {in0[r], in1[r]}, z[2];
-        apply_prologue<T, T2>(a.op, in, z);
-        v[0][r] = z[0];
-        if (NR > 1) v[NR - 1][r] = z[1];
+        v[0][r] = ldf<T2>(a.f.in[0], base + P * (t + A * r));
+        if (NR > 1) v[NR - 1][r] = ldf<T2>(a.f.in[a.f.nin > 1 ? 1 : 0], base + P * (t + A * r));
       }
     } else {
 #pragma unroll
@@ -510,12 +537,16 @@ __global__ void __launch_bounds__(kFftThreads) fft4_pass_kernel(const FftPassArg
   }
   if (a.flags & PASS_INV) four_step<T, T2, NR, LOGN>(v, ex, pp, t, tt + 3 * n, tf + n, tw + n, true);
 
-  // ---- store (+ epilogue), four elements at a time with their extra inputs loaded first
+  // ---- store (+ epilogue).  The epilogue runs as a rolled loop over chunks
+  // of four elements (extra inputs of a chunk loaded first); after each chunk
+  // the register arrays shift down by four, so the loop body addresses fixed
+  // registers and holds one short copy of the operator code: unrolled over
+  // all B elements that code outgrew the instruction cache.
   if (!live) return;
   bool bad = false;
   if (a.flags & PASS_EPI) {
     constexpr int CH = B < 4 ? B : 4;
-#pragma unroll
+#pragma unroll 1
     for (int r0 = 0; r0 < B; r0 += CH) {
       T2 ex4[CH][kMaxExtra];
 #pragma unroll
@@ -526,7 +557,7 @@ __global__ void __launch_bounds__(kFftThreads) fft4_pass_kernel(const FftPassArg
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const int64_t off = base + P * (t + A * (r0 + c));
-        T2 y[2] = {v[0][r0 + c], v[NR - 1][r0 + c]}, o[2];
+        T2 y[2] = {v[0][c], v[NR - 1][c]}, o[2];
         const int no = apply_epilogue<T, T2>(a.op, y, ex4[c], o);
 #pragma unroll
         for (int x = 0; x < 2; ++x) {
@@ -536,6 +567,10 @@ __global__ void __launch_bounds__(kFftThreads) fft4_pass_kernel(const FftPassArg
           }
         }
       }
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+        for (int r = 0; r + CH < B; ++r) v[rr][r] = v[rr][r + CH];
     }
   } else {
 #pragma unroll
