@@ -163,7 +163,11 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
         const int rr = r < sw.nrhs ? r : 0;
         L.tmA[r] = p->tmA[mu][rr];
         L.tmB[r] = p->tmB[sw.fac[rr]][mu];
-        L.out[r] = (mu == p->d - 1) ? p->planes[rr] : p->splits[rr];
+        // mode mu reads splits (mu even) or splits_alt (mu odd) and writes the
+        // other set: the row blocks of one fiber tile are separate work
+        // items, so an in-place pass would overwrite input that the tile's
+        // other items still read
+        L.out[r] = (mu == p->d - 1) ? p->planes[rr] : ((mu & 1) ? p->splits[rr] : p->splits_alt[rr]);
       }
       L.out_fp32 = mu == p->d - 1;
       L.status = p->status;
@@ -625,10 +629,11 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
     const int nr = scheme == CGL_STRANG ? 1 : 2;
     for (int r = 0; !st && r < nr; ++r) {
       st = dev_alloc(p, &p->splits[r], 12 * (size_t)p->N);
+      if (!st && d > 1) st = dev_alloc(p, &p->splits_alt[r], 12 * (size_t)p->N);
       if (!st) st = dev_alloc(p, &p->planes[r], 8 * (size_t)p->N);
       for (int mu = 0; !st && mu < d; ++mu) {
         const int64_t P = axis_P(p, mu), Q = p->N / (P * p->n[mu]);
-        e = make_state_tmap(p->tmA[mu][r], p->splits[r], (int)p->n[mu], P, Q, p->N);
+        e = make_state_tmap(p->tmA[mu][r], (mu & 1) ? p->splits_alt[r] : p->splits[r], (int)p->n[mu], P, Q, p->N);
         if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("tensor map: ") + cudaGetErrorString(e));
       }
     }

@@ -24,7 +24,8 @@
 // timeout the kernel sets bit 1 of the status word, skips its stores, waits
 // (bounded) for its own copies, frees its TMEM and returns.
 //
-// Each CTA owns whole fibers, so a pass may write its output over its input.
+// A pass must not write over its input: the CTAs of one fiber tile (its
+// components and row blocks) all read the tile's whole input.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>

@@ -70,6 +70,7 @@ struct cgl_plan {
   // BF16x3 tensor-core path: per-rhs BF16x3 state planes and FP32 output
   // planes, per-(factor, mode) BF16x3 factor splits, and their TMA maps.
   void* splits[2] = {nullptr, nullptr};
+  void* splits_alt[2] = {nullptr, nullptr};  // second set: mode passes alternate, none writes over its input
   void* planes[2] = {nullptr, nullptr};
   void* fsplit[2][3] = {{nullptr}};
   alignas(64) unsigned char tmA[3][2][cgl::kTensorMapBytes];

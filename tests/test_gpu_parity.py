@@ -116,10 +116,11 @@ def test_linear_flow(n, bc, prec):
 
 # shapes the tcgen05 path takes: n_mu multiple of 16 and <= 256, n_1 a
 # multiple of 128 for d >= 2; several 128-fiber tiles and a ragged last tile
-# of mode-1 fibers (Q not a multiple of 128) included
+# of mode-1 fibers (Q not a multiple of 128) included, and row blocks of
+# 16 (n = 208), 80 (n = 240) and 128 (n = 256) output rows
 MMA_SHAPES = [((16,), (0,)), ((48,), (1,)), ((256,), (0,)), ((128, 16), (0, 1)), ((128, 48), (1, 0)),
               ((256, 64), (0, 0)), ((128, 32, 16), (1, 0, 1)), ((128, 16, 80), (0, 1, 1)),
-              ((256, 256, 3 * 16), (1, 1, 0))]
+              ((256, 256, 3 * 16), (1, 1, 0)), ((240,), (1,)), ((128, 208), (0, 1))]
 
 
 @pytest.mark.parametrize("n,bc", MMA_SHAPES)
@@ -137,6 +138,18 @@ def test_linear_flow_tensor_cores(n, bc):
             torch.cuda.synchronize()
             assert plan.device_status() == nat.CGL_OK
             check(nat.from_device(u), L.expK(U, c), "bf16x3", "c=%g" % c)
+
+
+def test_tensor_core_path_is_deterministic():
+    """Two runs of a multi-mode BF16x3 scheme give identical bytes and no
+    value strays far from the oracle (relative inf norm): a pass that read
+    input another work item had already overwritten would show in either."""
+    p, rng = rand_problem(8, (128, 64, 48), (1, 0, 1), cubic=True)
+    U0 = smooth_data(p, rng, amp=0.8)
+    runs = [run_gpu(p, U0, 0.004, 4, "lawson4", "bf16x3") for _ in range(2)]
+    assert runs[0].tobytes() == runs[1].tobytes()
+    ref = O.integrate(oprob(p), U0, 0.004, 4, "lawson4")
+    assert O.rel_inf(runs[0], ref) <= 10 * TOL["bf16x3"]
 
 
 @pytest.mark.parametrize("n,bc", [((64, 64), (0, 0)), ((24,), (0,)), ((128, 300), (0, 0)), ((8, 8), (2, 2))])
