@@ -391,6 +391,31 @@ def step_rk2(L: LinearOperator, u):
     return u + (tau / 2) * (f1 + f2)
 
 
+def strang3t_step(L: LinearOperator, u, h: float):
+    """The three-term Strang step S^3_h of Sec. 4.3 (cubic and quintic parts
+    of the nonlinearity split apart, each with its exact flow):
+    S^3_h(u) = phi^q_{h/2}(phi^c_{h/2}(e^{hK} phi^c_{h/2}(phi^q_{h/2}(u)))).
+    h is tau or tau/2 (the linear flows the operator holds)."""
+    p = L.p
+    v = phi_cubic(p, phi_quintic(p, u, h / 2), h / 2)
+    v = L.expK(v, h / L.tau)
+    return phi_quintic(p, phi_cubic(p, v, h / 2), h / 2)
+
+
+def step_strang3t(L: LinearOperator, u):
+    """strang_3t (Sec. 4.3): u_{n+1} = S^3_tau(u_n)."""
+    return strang3t_step(L, u, L.tau)
+
+
+def step_split4_3t(L: LinearOperator, u):
+    """split4_3t (Sec. 4.3): the Richardson extrapolation of S^3, as printed
+    (the two half steps applied in turn, no flows merged):
+    u_{n+1} = 4/3 S^3_{tau/2}(S^3_{tau/2}(u_n)) - 1/3 S^3_tau(u_n)."""
+    tau = L.tau
+    half = strang3t_step(L, strang3t_step(L, u, tau / 2), tau / 2)
+    return (4.0 / 3.0) * half - (1.0 / 3.0) * strang3t_step(L, u, tau)
+
+
 SCHEMES = {
     "strang": step_strang,
     "split4": step_split4,
@@ -398,9 +423,11 @@ SCHEMES = {
     "lawson2": step_lawson2,
     "rk4": step_rk4,
     "rk2": step_rk2,
+    "strang3t": step_strang3t,
+    "split4_3t": step_split4_3t,
 }
 
-ORDERS = {"strang": 2, "split4": 4, "lawson4": 4, "lawson2": 2, "rk4": 4, "rk2": 2}
+ORDERS = {"strang": 2, "split4": 4, "lawson4": 4, "lawson2": 2, "rk4": 4, "rk2": 2, "strang3t": 2, "split4_3t": 4}
 
 
 def integrate(prob, U0: np.ndarray, tau: float, nsteps: int, scheme: str) -> np.ndarray:

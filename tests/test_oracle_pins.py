@@ -324,7 +324,7 @@ def test_plane_wave_residual_vanishes():
         np.testing.assert_allclose(L.K(U0) + O.g(p, U0), -1j * w * U0, atol=1e-12)
 
 
-@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2", "rk4", "rk2"])
+@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2", "rk4", "rk2", "strang3t", "split4_3t"])
 @pytest.mark.parametrize("cubic", [True, False])
 def test_plane_wave_orders(scheme, cubic):
     """Temporal order on an exact solution (no spatial error): 2 for
@@ -342,7 +342,7 @@ def test_plane_wave_orders(scheme, cubic):
 
 # ---------------------------------- schemes: FD Neumann, spatially uniform
 
-@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2", "rk4"])
+@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2", "rk4", "strang3t", "split4_3t"])
 def test_neumann_uniform_solution_orders(scheme):
     """With Neumann conditions a constant field stays constant (the FD rows sum
     to zero) and solves u' = a2 u + (a3+ib3)|u|^2 u, whose closed form is
@@ -360,7 +360,38 @@ def test_neumann_uniform_solution_orders(scheme):
     assert abs(order - O.ORDERS[scheme]) < 0.1, (errs, order)
 
 
-@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2"])
+def test_three_term_splittings_reduce_to_two_term_for_cubic():
+    """With a4 = b4 = 0 the quintic flow is the identity and the cubic flow is
+    exact, so strang_3t is strang, and split4_3t is split4 (its two middle
+    quarter flows compose to the half flow of split4's explicit form by the
+    semigroup property of the exact flow) up to rounding."""
+    p = O.OracleProblem((9, 6), (O.DIRICHLET, O.NEUMANN), (-3.0, -2.0), (3.0, 2.0), 0.8, 0.4, 0.5,
+                        -1.1, 0.7, 0.0, 0.0)
+    rng = np.random.default_rng(31)
+    U0 = 0.5 * (rng.standard_normal(p.n) + 1j * rng.standard_normal(p.n))
+    for a, b in (("strang3t", "strang"), ("split4_3t", "split4")):
+        ua = O.integrate(p, U0, 0.03, 5, a)
+        ub = O.integrate(p, U0, 0.03, 5, b)
+        assert O.rel_l2(ua, ub) < 1e-13, (a, O.rel_l2(ua, ub))
+
+
+def test_three_term_nonlinear_parts_do_not_commute():
+    """The cubic and quintic flows do not commute (already their radial parts
+    r' = 2 a3 r^2 and r' = 2 a4 r^3 have the nonzero commutator 4 a3 a4 r^4),
+    so the ordering inside strang_3t matters: phi^c o phi^q and phi^q o phi^c
+    differ by O(t^2), a difference that quarters when t halves."""
+    p = O.OracleProblem((4,), (O.PERIODIC,), (0.0,), (1.0,), 1.0, 0.0, 0.0, -0.9, 1.3, -0.4, 0.6)
+    u = np.array([0.9 + 0.2j, -0.5 + 0.6j, 0.3 - 0.8j, 1.1 + 0.0j])
+    d = []
+    for t in (0.002, 0.001):
+        cq = O.phi_cubic(p, O.phi_quintic(p, u, t), t)
+        qc = O.phi_quintic(p, O.phi_cubic(p, u, t), t)
+        d.append(np.abs(cq - qc).max())
+    assert d[0] > 1e-6
+    assert abs(np.log2(d[0] / d[1]) - 2.0) < 0.1
+
+
+@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t"])
 def test_linear_problem_is_integrated_exactly(scheme):
     """With g = 0 every exponential scheme reproduces exp(tK) u0; a product of
     sine eigenvectors (Dirichlet) and cosine eigenvectors (Neumann) then
