@@ -657,7 +657,7 @@ def main():
     info = plan.info()
     extras = {}
     if not args.no_extras:
-        for s in ("strang", "rk4", "lawson4"):
+        for s in ("strang", "rk4", "lawson4", "strang3t", "split4_3t"):
             if s == args.scheme:
                 continue
             with nat.Plan(w.prob, w.tau, s, "f64") as p2:

@@ -52,7 +52,10 @@ enum cgl_scheme {
     CGL_LAWSON4 = 2,  /* eq. lawson4 (if4), order 4                                         */
     CGL_RK4 = 3,      /* eq. RK4 on u' = K u + g(u); periodic problems only                 */
     CGL_LAWSON2 = 4,  /* eq. lawson2b (if2), order 2                                        */
-    CGL_RK2 = 5       /* eq. RK2 (Heun); periodic problems only                             */
+    CGL_RK2 = 5,      /* eq. RK2 (Heun); periodic problems only                             */
+    CGL_STRANG3T = 6, /* strang_3t (Sec. 4.3): phi^q phi^c e^{tau K} phi^c phi^q, exact      */
+                      /* cubic and quintic sub-flows, order 2                                */
+    CGL_SPLIT4_3T = 7 /* split4_3t (Sec. 4.3): Richardson extrapolation of strang_3t, order 4 */
 };
 
 /* Arithmetic of the state and of the time-stepping kernels.  The factors
@@ -80,7 +83,8 @@ enum cgl_status {
  * Create a plan: validates the problem, builds A_mu = (a1+i b1) D2_mu + a2/d
  * (Sec. 1 after eq. 2; 2nd-order FD or Fourier symbol, Sec. 3.2), computes the
  * factors exp(c tau A_mu) in FP64 on the GPU for every distinct c the scheme
- * needs (Strang/Lawson2: c = 1; split4: 1 and 1/2; Lawson4: 1/2), and sizes
+ * needs (Strang/Lawson2/strang_3t: c = 1; split4/split4_3t: 1 and 1/2;
+ * Lawson4: 1/2), and sizes
  * the workspace.
  *   out        receives the plan (set to NULL on failure).
  *   d          1, 2 or 3.
@@ -201,7 +205,7 @@ typedef struct cgl_batch cgl_batch;
 /*
  * Create a batch of `count` finite-difference problems (Dirichlet/Neumann;
  * periodic -> EUNSUPPORTED) sharing one step size and scheme (strang,
- * split4, lawson4, lawson2) in CGL_F64 or CGL_F32.  Each instance gets its own
+ * split4, lawson4, lawson2, strang_3t, split4_3t) in CGL_F64 or CGL_F32.  Each instance gets its own
  * FP64 factors exp(c tau A_mu) (Sec. 3.1).  Every mu-mode pass of a time step
  * is ONE persistent launch over all instances: a fixed grid of CTAs pulls
  * (instance, fiber tile) work items, largest first, from a device queue; the

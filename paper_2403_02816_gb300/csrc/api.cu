@@ -55,7 +55,8 @@ PassGeom geom(const cgl_plan* p, int axis) {
 
 // Algorithmic flop count per grid point of the pointwise operators (real
 // flops, transcendental calls not counted): g = 15, exact flow = 20,
-// one RK4 step of u' = g(u) = 84, complex axpy = 4.
+// one RK4 step of u' = g(u) = 84, complex axpy = 4; the three-term
+// operators compose two (prologue, end of step) or three (middle) exact flows.
 double flow_flops(const cgl_plan* p) { return p->cubic ? 20.0 : 84.0; }
 double pro_flops(const cgl_plan* p, const OpArgs& o) {
   switch (o.pro) {
@@ -63,6 +64,8 @@ double pro_flops(const cgl_plan* p, const OpArgs& o) {
     case PRO_FLOW2: return 2 * flow_flops(p);
     case PRO_LAW4: return 15;
     case PRO_LAW2: return 23;
+    case PRO_CQ: return 40;
+    case PRO_CQ2: return 80;
     default: return 0;
   }
 }
@@ -75,6 +78,9 @@ double epi_flops(const cgl_plan* p, const OpArgs& o) {
     case EPI_LAW4B: return 19;
     case EPI_LAW2: return 19;
     case EPI_RK: return 25;
+    case EPI_QC: return 40;
+    case EPI_QC2: return 100;
+    case EPI_SPLIT4_3T: return 44;
     default: return 0;
   }
 }
@@ -405,6 +411,32 @@ void build_program(cgl_plan* p) {
       p->sweeps.push_back(s);
       break;
     }
+    case CGL_STRANG3T: {  // strang_3t (Sec. 4.3): P*_{tau/2} e^{tau K} P_{tau/2}
+      Sweep s = base();
+      s.op.pro = PRO_CQ; s.op.t0 = tau / 2;
+      s.op.epi = EPI_QC; s.op.te = tau / 2;
+      s.fac[0] = 0;
+      p->sweeps.push_back(s);
+      break;
+    }
+    case CGL_SPLIT4_3T: {  // split4_3t (Sec. 4.3); factor 0: c = 1, factor 1: c = 1/2
+      // sweep 1: [E_1 P_{tau/2} u, E_{1/2} P_{tau/4} u] -> (u_{n2} = P*_{tau/2}(.),
+      //          v = P_{tau/4} P*_{tau/4}(.), quintic quarter flows merged);
+      // sweep 2: E_{1/2} v -> 4/3 P*_{tau/4}(.) - 1/3 u_{n2}
+      Sweep s1 = base();
+      s1.op.pro = PRO_CQ2; s1.op.t0 = tau / 2; s1.op.t1 = tau / 4;
+      s1.nrhs = 2; s1.fac[0] = 0; s1.fac[1] = 1; s1.work[0] = BUF_W0; s1.work[1] = BUF_W1;
+      s1.op.epi = EPI_QC2; s1.op.te = tau / 2;
+      s1.nout = 2; s1.out[0] = BUF_W0; s1.out[1] = BUF_W1;
+      Sweep s2 = base();
+      s2.in[0] = BUF_W1; s2.fac[0] = 1; s2.work[0] = BUF_W1;
+      s2.op.epi = EPI_SPLIT4_3T; s2.op.te = tau / 4;
+      s2.nextra = 1; s2.extra[0] = BUF_W0;
+      s2.out[0] = BUF_U;
+      p->sweeps.push_back(s1);
+      p->sweeps.push_back(s2);
+      break;
+    }
     case CGL_SPLIT4: {  // eq. Richardson; factor 0: c = 1, factor 1: c = 1/2
       Sweep s1 = base();
       s1.op.pro = PRO_FLOW2; s1.op.t0 = tau / 2; s1.op.t1 = tau / 4;
@@ -551,7 +583,7 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   if (!finite_all({a1, b1, a2, a3, b3, a4, b4, tau})) return fail(CGL_EINVAL, "parameters must be finite");
   if (!(a1 > 0)) return fail(CGL_EINVAL, "alpha1 must be positive");
   if (!(tau > 0)) return fail(CGL_EINVAL, "tau must be positive");
-  if (scheme < CGL_STRANG || scheme > CGL_RK2) return fail(CGL_EINVAL, "unknown scheme");
+  if (scheme < CGL_STRANG || scheme > CGL_SPLIT4_3T) return fail(CGL_EINVAL, "unknown scheme");
   if (precision != CGL_F64 && precision != CGL_F32 && precision != CGL_BF16X3)
     return fail(CGL_EINVAL, "unknown precision");
   int nper = 0;
@@ -600,13 +632,16 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   p->elem = precision == CGL_F64 ? sizeof(double2) : sizeof(float2);  // F32 and BF16x3: complex64
   switch (scheme) {
     case CGL_STRANG:
+    case CGL_STRANG3T:
     case CGL_LAWSON2: p->nfac = 1; p->cval[0] = 1.0; break;
-    case CGL_SPLIT4: p->nfac = 2; p->cval[0] = 1.0; p->cval[1] = 0.5; break;
+    case CGL_SPLIT4:
+    case CGL_SPLIT4_3T: p->nfac = 2; p->cval[0] = 1.0; p->cval[1] = 0.5; break;
     case CGL_LAWSON4: p->nfac = 1; p->cval[0] = 0.5; break;
     default: p->nfac = 0;
   }
   switch (scheme) {
-    case CGL_STRANG: p->nwork = 0; break;
+    case CGL_STRANG:
+    case CGL_STRANG3T: p->nwork = 0; break;
     case CGL_RK4:
     case CGL_RK2: p->nwork = 3; break;
     default: p->nwork = 2;

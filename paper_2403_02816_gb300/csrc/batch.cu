@@ -282,8 +282,9 @@ int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, doubl
   if (count < 1 || !probs) return fail(CGL_EINVAL, "count must be >= 1 and probs non-NULL");
   if (precision != CGL_F64 && precision != CGL_F32)
     return fail(CGL_EUNSUPPORTED, "batches run in CGL_F64 or CGL_F32");
-  if (scheme != CGL_STRANG && scheme != CGL_SPLIT4 && scheme != CGL_LAWSON4 && scheme != CGL_LAWSON2)
-    return fail(scheme < CGL_STRANG || scheme > CGL_RK2 ? CGL_EINVAL : CGL_EUNSUPPORTED,
+  if (scheme != CGL_STRANG && scheme != CGL_SPLIT4 && scheme != CGL_LAWSON4 && scheme != CGL_LAWSON2 &&
+      scheme != CGL_STRANG3T && scheme != CGL_SPLIT4_3T)
+    return fail(scheme < CGL_STRANG || scheme > CGL_SPLIT4_3T ? CGL_EINVAL : CGL_EUNSUPPORTED,
                 "batches support the exponential schemes strang, split4, lawson4, lawson2");
   for (int i = 0; i < count; ++i)
     for (int m = 0; m < probs[i].d && m < 3; ++m)

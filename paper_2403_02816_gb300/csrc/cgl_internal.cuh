@@ -51,7 +51,9 @@ enum ProOp : int {
   PRO_FLOW = 1,    // z0 = phi_{t0}(in0)                              (Strang)
   PRO_FLOW2 = 2,   // z0 = phi_{t0}(in0), z1 = phi_{t1}(in0)           (split4, first sweep)
   PRO_LAW4 = 3,    // z0 = in0, z1 = g(in0)                            (Lawson4, first sweep)
-  PRO_LAW2 = 4     // z0 = in0 + tau g(in0), z1 = in0 + tau/2 g(in0)   (Lawson2)
+  PRO_LAW2 = 4,    // z0 = in0 + tau g(in0), z1 = in0 + tau/2 g(in0)   (Lawson2)
+  PRO_CQ = 5,      // z0 = phi^c_{t0}(phi^q_{t0}(in0))                 (strang_3t)
+  PRO_CQ2 = 6      // z0 = phi^c_{t0}(phi^q_{t0}(in0)), z1 likewise t1 (split4_3t, first sweep)
 };
 enum EpiOp : int {
   EPI_NONE = 0,    // out_r = y_r
@@ -61,7 +63,11 @@ enum EpiOp : int {
   EPI_LAW4A = 4,   // (a, b) -> (p, w)                                 (Lawson4, first sweep)
   EPI_LAW4B = 5,   // (q, r) -> r + tau/6 g(q)                         (Lawson4, second sweep)
   EPI_LAW2 = 6,    // (v, w) -> w + tau/2 g(v)                         (Lawson2)
-  EPI_RK = 7       // Runge-Kutta stage, see rk_stage()
+  EPI_RK = 7,      // Runge-Kutta stage, see rk_stage()
+  EPI_QC = 8,      // out0 = phi^q_t(phi^c_t(y0))                      (strang_3t)
+  EPI_QC2 = 9,     // out0 = phi^q_t(phi^c_t(y0)),                     (split4_3t, first sweep)
+                   // out1 = phi^c_{t/2}(phi^q_t(phi^c_{t/2}(y1)))
+  EPI_SPLIT4_3T = 10  // out0 = 4/3 phi^q_t(phi^c_t(y0)) - 1/3 e0      (split4_3t, second sweep)
 };
 
 // Nonlinear model parameters (eq. 1) and the per-pass operator constants.
@@ -145,6 +151,17 @@ template <class T, class T2> __device__ __forceinline__ T2 nl_flow(const NlParam
   return caxpy(u, t * (T(1) / T(6)), s);
 }
 
+// Three-term splitting (Sec. 4.3): the cubic and quintic parts of g with
+// their exact flows, phi^c (eq. exsolcub) and phi^q, composed as
+// P_t = phi^c_t o phi^q_t before the linear flow and P*_t = phi^q_t o phi^c_t
+// after it.
+template <class T, class T2> __device__ __forceinline__ T2 flow_c(const NlParams& p, T2 u, T t) {
+  return exact_power_flow<T, T2>(u, pv<T>(p.a3, p.a3f), pv<T>(p.b3, p.b3f), 1, t);
+}
+template <class T, class T2> __device__ __forceinline__ T2 flow_q(const NlParams& p, T2 u, T t) {
+  return exact_power_flow<T, T2>(u, pv<T>(p.a4, p.a4f), pv<T>(p.b4, p.b4f), 2, t);
+}
+
 template <class T, class T2>
 __device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2* z) {
   switch (o.pro) {
@@ -158,6 +175,13 @@ __device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2
     case PRO_LAW4:
       z[0] = in[0];
       z[1] = nl_g<T, T2>(o.nl, in[0]);
+      break;
+    case PRO_CQ:
+      z[0] = flow_c<T, T2>(o.nl, flow_q<T, T2>(o.nl, in[0], pv<T>(o.t0, o.t0f)), pv<T>(o.t0, o.t0f));
+      break;
+    case PRO_CQ2:
+      z[0] = flow_c<T, T2>(o.nl, flow_q<T, T2>(o.nl, in[0], pv<T>(o.t0, o.t0f)), pv<T>(o.t0, o.t0f));
+      z[1] = flow_c<T, T2>(o.nl, flow_q<T, T2>(o.nl, in[0], pv<T>(o.t1, o.t1f)), pv<T>(o.t1, o.t1f));
       break;
     case PRO_LAW2: {
       const T2 gn = nl_g<T, T2>(o.nl, in[0]);
@@ -206,6 +230,25 @@ __device__ __forceinline__ int apply_epilogue(const OpArgs& o, const T2* y, cons
       out[0] = nl_flow<T, T2>(o.nl, y[0], pv<T>(o.te, o.tef));
       out[1] = nl_flow<T, T2>(o.nl, y[1], pv<T>(o.te, o.tef));
       return 2;
+    case EPI_QC:
+      out[0] = flow_q<T, T2>(o.nl, flow_c<T, T2>(o.nl, y[0], pv<T>(o.te, o.tef)), pv<T>(o.te, o.tef));
+      return 1;
+    case EPI_QC2: {
+      // end of S^3_tau, and the middle P*_{tau/4} P_{tau/4} of the two half
+      // steps with its two quintic quarter flows merged into one of tau/2
+      // (exact flows: semigroup)
+      const T te = pv<T>(o.te, o.tef);
+      out[0] = flow_q<T, T2>(o.nl, flow_c<T, T2>(o.nl, y[0], te), te);
+      out[1] = flow_c<T, T2>(o.nl, flow_q<T, T2>(o.nl, flow_c<T, T2>(o.nl, y[1], te * T(0.5)), te), te * T(0.5));
+      return 2;
+    }
+    case EPI_SPLIT4_3T: {
+      const T te = pv<T>(o.te, o.tef);
+      const T2 f = flow_q<T, T2>(o.nl, flow_c<T, T2>(o.nl, y[0], te), te);
+      out[0] = mk<T2>(fma(T(4) / T(3), f.x, -(T(1) / T(3)) * e[0].x),
+                      fma(T(4) / T(3), f.y, -(T(1) / T(3)) * e[0].y));
+      return 1;
+    }
     case EPI_SPLIT4: {
       const T2 f = nl_flow<T, T2>(o.nl, y[0], pv<T>(o.te, o.tef));
       out[0] = mk<T2>(fma(T(4) / T(3), f.x, -(T(1) / T(3)) * e[0].x),

@@ -23,11 +23,12 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "cgl.h")
 
 CGL_BC_DIRICHLET, CGL_BC_NEUMANN, CGL_BC_PERIODIC = 0, 1, 2
 CGL_STRANG, CGL_SPLIT4, CGL_LAWSON4, CGL_RK4, CGL_LAWSON2, CGL_RK2 = 0, 1, 2, 3, 4, 5
+CGL_STRANG3T, CGL_SPLIT4_3T = 6, 7
 CGL_F64, CGL_F32, CGL_BF16X3 = 0, 1, 2
 CGL_OK, CGL_EINVAL, CGL_ENOMEM, CGL_ECUDA, CGL_EUNSUPPORTED, CGL_ETIMEOUT, CGL_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 
 SCHEMES = {"strang": CGL_STRANG, "split4": CGL_SPLIT4, "lawson4": CGL_LAWSON4, "rk4": CGL_RK4,
-           "lawson2": CGL_LAWSON2, "rk2": CGL_RK2}
+           "lawson2": CGL_LAWSON2, "rk2": CGL_RK2, "strang3t": CGL_STRANG3T, "split4_3t": CGL_SPLIT4_3T}
 PRECISIONS = {"f64": CGL_F64, "f32": CGL_F32, "bf16x3": CGL_BF16X3}
 
 

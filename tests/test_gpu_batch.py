@@ -42,7 +42,7 @@ def mixed_instances(seed=11):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("scheme", ["lawson4", "strang", "split4", "lawson2"])
+@pytest.mark.parametrize("scheme", ["lawson4", "strang", "split4", "lawson2", "split4_3t"])
 def test_batch_equals_single_plans_and_oracle(prec, scheme):
     probs, fields = mixed_instances()
     tau, nsteps = 0.01, 4

@@ -164,12 +164,12 @@ def test_tensor_core_path_rejects_unsupported_shapes(n, bc):
 
 SCHEME_CASES = [
     # (n, bc, schemes)
-    ((24, 40), (0, 1), ("strang", "split4", "lawson4", "lawson2")),
-    ((9, 6, 11), (1, 0, 1), ("strang", "split4", "lawson4", "lawson2")),
-    ((37,), (0,), ("strang", "split4", "lawson4", "lawson2")),
-    ((32, 16), (2, 2), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2")),
-    ((8, 16, 4), (2, 2, 2), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2")),
-    ((64,), (2,), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2")),
+    ((24, 40), (0, 1), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t")),
+    ((9, 6, 11), (1, 0, 1), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t")),
+    ((37,), (0,), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t")),
+    ((32, 16), (2, 2), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2", "strang3t", "split4_3t")),
+    ((8, 16, 4), (2, 2, 2), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2", "strang3t", "split4_3t")),
+    ((64,), (2,), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2", "strang3t", "split4_3t")),
 ]
 
 
@@ -195,7 +195,7 @@ def test_schemes_match_oracle_tensor_cores(n, bc, cubic):
     p, rng = rand_problem(6, n, bc, cubic=cubic)
     U0 = smooth_data(p, rng, amp=0.8)
     tau, nsteps = 0.004, 5
-    for s in ("strang", "split4", "lawson4", "lawson2"):
+    for s in ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t"):
         ref = O.integrate(oprob(p), U0, tau, nsteps, s)
         got = run_gpu(p, U0, tau, nsteps, s, "bf16x3")
         check(got, ref, "bf16x3", "%s cubic=%s" % (s, cubic))
@@ -210,7 +210,8 @@ def test_plane_wave_orders_on_gpu():
     w = b1 * k2 - b3 * a * a - b4 * a ** 4
     p = I.Problem((8, 8), (2, 2), (-np.pi,) * 2, (np.pi,) * 2, a1, b1, a2, a3, b3, a4, b4)
     U0 = I.plane_wave_data(p, k, a)
-    for s, order in [("strang", 2), ("split4", 4), ("lawson4", 4), ("rk4", 4), ("lawson2", 2), ("rk2", 2)]:
+    for s, order in [("strang", 2), ("split4", 4), ("lawson4", 4), ("rk4", 4), ("lawson2", 2), ("rk2", 2),
+                     ("strang3t", 2), ("split4_3t", 4)]:
         errs = [O.rel_l2(run_gpu(p, U0, 1.0 / m, m, s), U0 * np.exp(-1j * w)) for m in (40, 80)]
         assert abs(O.observed_order(40, errs[0], 80, errs[1]) - order) < 0.1, (s, errs)
 
