@@ -50,9 +50,9 @@ enum cgl_scheme {
     CGL_STRANG = 0,   /* eq. Strang: phi_{tau/2} e^{tau K} phi_{tau/2}, order 2            */
     CGL_SPLIT4 = 1,   /* eq. Richardson: 4/3 S_{tau/2}S_{tau/2} - 1/3 S_tau, order 4        */
     CGL_LAWSON4 = 2,  /* eq. lawson4 (if4), order 4                                         */
-    CGL_RK4 = 3,      /* eq. RK4 on u' = K u + g(u); periodic problems only                 */
+    CGL_RK4 = 3,      /* eq. RK4 on u' = K u + g(u)                                         */
     CGL_LAWSON2 = 4,  /* eq. lawson2b (if2), order 2                                        */
-    CGL_RK2 = 5,      /* eq. RK2 (Heun); periodic problems only                             */
+    CGL_RK2 = 5,      /* eq. RK2 (Heun)                                                     */
     CGL_STRANG3T = 6, /* strang_3t (Sec. 4.3): phi^q phi^c e^{tau K} phi^c phi^q, exact      */
                       /* cubic and quintic sub-flows, order 2                                */
     CGL_SPLIT4_3T = 7 /* split4_3t (Sec. 4.3): Richardson extrapolation of strang_3t, order 4 */
@@ -97,7 +97,10 @@ enum cgl_status {
  *              nonlinear flow is exact (eq. exsolcub); otherwise the flow is
  *              one RK4 step of u' = g(u) (Sec. 4.3).
  *   tau        constant step, > 0 and finite.
- *   scheme     cgl_scheme; CGL_RK4/CGL_RK2 need periodic directions.
+ *   scheme     cgl_scheme.  CGL_RK4/CGL_RK2 apply K directly: a pseudospectral
+ *              multiply (periodic) or the finite-difference stencil of
+ *              eq. kronsumv; explicit, so tau must respect their stability
+ *              limit (about 2.8 / |lambda_max(K)| for RK4).
  *   precision  cgl_precision.
  *   stream     stream used for the set-up work; the call returns after it
  *              has completed.

@@ -149,6 +149,39 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
   const double es = (double)p->elem;
   const bool f64 = p->precision == CGL_F64;
 
+  if (sw.stencil) {
+    StencilArgs a{};
+    a.d = p->d;
+    for (int mu = 0; mu < 3; ++mu) {
+      a.n[mu] = p->n[mu];
+      a.bc[mu] = p->bc[mu];
+      if (mu < p->d) {
+        const double L = p->hi[mu] - p->lo[mu];
+        const double h = (p->bc[mu] == CGL_BC_DIRICHLET) ? L / (p->n[mu] + 1) : L / (p->n[mu] - 1);
+        a.cr[mu] = p->a1 / (h * h);
+        a.ci[mu] = p->b1 / (h * h);
+        a.crf[mu] = (float)a.cr[mu];
+        a.cif[mu] = (float)a.ci[mu];
+      }
+    }
+    a.a2 = p->a2;
+    a.a2f = (float)p->a2;
+    a.x = f.in[0];
+    for (int x = 0; x < kMaxExtra; ++x) a.extra[x] = f.extra[x];
+    a.nextra = sw.nextra;
+    a.out[0] = f.out[0];
+    a.out[1] = f.out[1];
+    a.nout = sw.nout;
+    a.op = sw.op;
+    a.status = p->status;
+    Timer tm(p, s);
+    cudaError_t e = f64 ? launch_kron_stencil<double>(a, s) : launch_kron_stencil<float>(a, s);
+    if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("stencil: ") + cudaGetErrorString(e));
+    tm.done(f64 ? "kron_stencil_f64" : "kron_stencil_f32", (8.0 * p->d + 4 + epi_flops(p, sw.op)) * Nd,
+            (1.0 + sw.nextra + sw.nout) * Nd * es);
+    return CGL_OK;
+  }
+
   if (p->precision == CGL_BF16X3) {
     // split prologue -> d tensor-core mode passes -> plane epilogue
     {
@@ -264,6 +297,7 @@ int enqueue_step(cgl_plan* p, void* u, cudaStream_t s) {
 }
 
 int launches_per_step(const cgl_plan* p) {
+  if (!p->periodic && (p->scheme == CGL_RK4 || p->scheme == CGL_RK2)) return (int)p->sweeps.size();  // stencils
   int per = p->periodic ? 2 * p->d - 1 : p->d;
   if (p->precision == CGL_BF16X3) per = p->d + 2;  // split prologue + d mode passes + plane epilogue
   return (int)p->sweeps.size() * per;
@@ -479,6 +513,28 @@ void build_program(cgl_plan* p) {
     case CGL_RK4:
     case CGL_RK2: {  // eq. RK4 / eq. RK2: stage s computes K x_s with x_1 = u
       const int stages = p->scheme == CGL_RK4 ? 4 : 2;
+      if (!p->periodic) {
+        // finite differences: one stencil launch per stage (eq. kronsumv);
+        // the stage arguments alternate between W1 and W0 because a stencil
+        // reads neighbours and cannot write over its input
+        int xb = BUF_U;
+        for (int st = 1; st <= stages; ++st) {
+          Sweep s = base();
+          s.stencil = true;
+          s.in[0] = xb;
+          s.op.epi = EPI_RK; s.op.rk_scheme = stages; s.op.rk_stage = st;
+          s.nextra = 3; s.extra[0] = xb; s.extra[1] = BUF_U; s.extra[2] = BUF_W2;
+          if (st < stages) {
+            const int nb = (xb == BUF_W1) ? BUF_W0 : BUF_W1;
+            s.nout = 2; s.out[0] = nb; s.out[1] = BUF_W2;
+            xb = nb;
+          } else {
+            s.nout = 1; s.out[0] = BUF_U;
+          }
+          p->sweeps.push_back(s);
+        }
+        break;
+      }
       for (int st = 1; st <= stages; ++st) {
         Sweep s = base();
         s.in[0] = (st == 1) ? BUF_U : BUF_W1;  // x_s
@@ -602,8 +658,6 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
       return fail(CGL_EUNSUPPORTED, "periodic sizes must be powers of two <= 2048");
     if (!periodic && n[m] > 1024) return fail(CGL_EUNSUPPORTED, "finite-difference sizes must be <= 1024");
   }
-  if (!periodic && (scheme == CGL_RK4 || scheme == CGL_RK2))
-    return fail(CGL_EUNSUPPORTED, "Runge-Kutta schemes need periodic directions");
   if (precision == CGL_BF16X3) {
     if (periodic) return fail(CGL_EUNSUPPORTED, "BF16x3 applies to the finite-difference mode products only");
     for (int m = 0; m < d; ++m)

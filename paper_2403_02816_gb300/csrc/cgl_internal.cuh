@@ -362,6 +362,25 @@ cudaError_t launch_batched_mode_pass(const ModePassArgs* table, const BatchItem*
                                      int nrhs, size_t smem, int grid, cudaStream_t s);
 template <class T> int batched_mode_blocks_per_sm(int nrhs, size_t smem);
 
+// stencil.cu: K x on finite-difference directions (eq. kronsumv as a
+// stencil) fused with a Runge-Kutta stage epilogue; out must not alias x.
+struct StencilArgs {
+  int d;
+  int64_t n[3];
+  int bc[3];
+  double cr[3], ci[3];  // (a1 + i b1) / h_mu^2
+  double a2;
+  float crf[3], cif[3], a2f;  // FP32 copies
+  const void* x;              // stage argument
+  const void* extra[kMaxExtra];
+  int nextra;
+  void* out[2];
+  int nout;
+  OpArgs op;
+  int* status;
+};
+template <class T> cudaError_t launch_kron_stencil(const StencilArgs& a, cudaStream_t s);
+
 // expm.cu: FP64 complex n x n exponential of (scale * A) on the device.
 // dA: n x n column-major double2 (device); dOut: same layout.  work: 3*n*n double2.
 cudaError_t expm_device(const double2* dA, double scale, int n, double2* dOut, double2* work,

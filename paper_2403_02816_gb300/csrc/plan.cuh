@@ -23,6 +23,7 @@ struct Sweep {
   int nextra = 0, extra[3] = {BUF_U, BUF_U, BUF_U};
   int nout = 1, out[2] = {BUF_U, BUF_U};
   OpArgs op{};
+  bool stencil = false;  // FD Runge-Kutta stage: K x as a stencil + epilogue, one launch
 };
 
 struct KernelStat {

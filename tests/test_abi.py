@@ -59,7 +59,9 @@ def create(**kw):
     (dict(bc=[2, 2], n=[8, 12]), nat.CGL_EUNSUPPORTED),
     (dict(bc=[2, 2], n=[8, 4096]), nat.CGL_EUNSUPPORTED),
     (dict(n=[8, 2048]), nat.CGL_EUNSUPPORTED),
-    (dict(scheme=nat.CGL_RK4), nat.CGL_EUNSUPPORTED),
+    (dict(scheme=8), nat.CGL_EINVAL),
+    (dict(bc=[2, 2], precision=nat.CGL_BF16X3), nat.CGL_EUNSUPPORTED),
+    (dict(n=[24, 128], precision=nat.CGL_BF16X3), nat.CGL_EUNSUPPORTED),
 ])
 def test_invalid_arguments_are_rejected_before_any_cuda_call(lib, kw, status):
     st, h = create(**kw)

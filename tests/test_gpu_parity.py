@@ -164,9 +164,9 @@ def test_tensor_core_path_rejects_unsupported_shapes(n, bc):
 
 SCHEME_CASES = [
     # (n, bc, schemes)
-    ((24, 40), (0, 1), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t")),
-    ((9, 6, 11), (1, 0, 1), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t")),
-    ((37,), (0,), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t")),
+    ((24, 40), (0, 1), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t", "rk4", "rk2")),
+    ((9, 6, 11), (1, 0, 1), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t", "rk4", "rk2")),
+    ((37,), (0,), ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t", "rk4", "rk2")),
     ((32, 16), (2, 2), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2", "strang3t", "split4_3t")),
     ((8, 16, 4), (2, 2, 2), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2", "strang3t", "split4_3t")),
     ((64,), (2,), ("strang", "split4", "lawson4", "lawson2", "rk4", "rk2", "strang3t", "split4_3t")),
