@@ -58,6 +58,9 @@ class OracleProblem:
     b3: float
     a4: float = 0.0
     b4: float = 0.0
+    # optional caller-supplied direction matrices A_mu (complex n_mu x n_mu),
+    # replacing (a1 + i b1) D2_mu + a2/d; e.g. the paper's 4th-order FD
+    mats: tuple = None
 
     @property
     def d(self) -> int:
@@ -126,6 +129,46 @@ def fd_laplacian(n: int, lo: float, hi: float, bc: int) -> np.ndarray:
     return L / (h * h)
 
 
+def fd4_laplacian(n: int, lo: float, hi: float, right: int = DIRICHLET) -> np.ndarray:
+    """The paper's 4th-order finite-difference d^2/dx^2 matrices, as printed.
+
+      * right = DIRICHLET (Sec. 4.1.1): homogeneous Dirichlet at both ends, n
+        internal nodes x_j = lo + j h, j = 1..n, h = (hi-lo)/(n+1); centred
+        rows (-1, 16, -30, 16, -1)/(12 h^2), and in the first and last rows
+        the one-sided (-15, -4, 14, -6, 1)/(12 h^2) (the boundary value, zero,
+        drops out) and its mirror image.
+      * right = NEUMANN (Sec. 4.2, "semi-internal nodes"): Dirichlet at lo,
+        homogeneous Neumann at hi, nodes x_j = lo + j h, j = 1..n, h =
+        (hi-lo)/n (x_n = hi); first row as above, the last two rows
+        (1, -6, 14, -4, -15, 10)/(12 h^2) and (1, -8/3, -6, 56, -145/3)/(12 h^2)
+        on the last six and five nodes.
+    """
+    if n < 6:
+        raise ValueError("fd4_laplacian needs n >= 6")
+    if right == DIRICHLET:
+        h = (hi - lo) / (n + 1)
+    elif right == NEUMANN:
+        h = (hi - lo) / n
+    else:
+        raise ValueError("fd4_laplacian: right must be DIRICHLET or NEUMANN")
+    A = np.zeros((n, n))
+    for i in range(n):
+        for off, c in zip(range(-2, 3), (-1.0, 16.0, -30.0, 16.0, -1.0)):
+            if 0 <= i + off < n:
+                A[i, i + off] = c
+    A[0, :] = 0.0
+    A[0, :5] = [-15.0, -4.0, 14.0, -6.0, 1.0]
+    if right == DIRICHLET:
+        A[n - 1, :] = 0.0
+        A[n - 1, n - 5:] = [1.0, -6.0, 14.0, -4.0, -15.0]
+    else:
+        A[n - 2, :] = 0.0
+        A[n - 2, n - 6:] = [1.0, -6.0, 14.0, -4.0, -15.0, 10.0]
+        A[n - 1, :] = 0.0
+        A[n - 1, n - 5:] = [1.0, -8.0 / 3.0, -6.0, 56.0, -145.0 / 3.0]
+    return A / (12.0 * h * h)
+
+
 def wavenumbers(n: int, lo: float, hi: float) -> np.ndarray:
     """Signed Fourier wavenumbers kappa_m = 2 pi m / (hi - lo) in FFT order
     m = 0..n/2-1, -n/2..-1.  Sec. 3.2 writes (j-1)^2 on (0, 2 pi); the signed
@@ -139,6 +182,8 @@ def direction_matrix(p: OracleProblem, mu: int) -> np.ndarray:
     """A_mu ~ (a1 + i b1) d_{x_mu x_mu} + a2/d (Sec. 1, after eq. (2)).
     FD: a dense n_mu x n_mu complex matrix.  Periodic: the diagonal of A_mu in
     Fourier space (Sec. 3.2), returned as a vector."""
+    if getattr(p, "mats", None) is not None:
+        return np.array(p.mats[mu], dtype=complex)
     n, lo, hi, bc = p.n[mu], p.lo[mu], p.hi[mu], p.bc[mu]
     c = complex(p.a1, p.b1)
     if bc == PERIODIC:

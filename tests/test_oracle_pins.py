@@ -61,6 +61,67 @@ def test_fd_neumann_eigenpairs(n):
         np.testing.assert_allclose(L @ v, lam * v, rtol=0, atol=1e-12 * (4 / h**2) * n)
 
 
+def _poly_d2(coef, x):
+    import numpy.polynomial.polynomial as P
+    return P.polyval(x, coef), P.polyval(x, P.polyder(coef, 2))
+
+
+@pytest.mark.parametrize("deg", [2, 3, 4, 5])
+def test_fd4_dirichlet_exact_on_quintics(deg):
+    """The 4th-order Dirichlet matrix (Sec. 4.1.1) differentiates every
+    polynomial of degree <= 5 that vanishes at both ends exactly (centred and
+    one-sided rows alike), and no longer does so at degree 6."""
+    import numpy.polynomial.polynomial as P
+    lo, hi, n = -1.5, 2.0, 23
+    h = (hi - lo) / (n + 1)
+    x = lo + h * np.arange(1, n + 1)
+    A = O.fd4_laplacian(n, lo, hi, O.DIRICHLET)
+    for extra in (deg - 2, deg - 2 + 4):
+        coef = P.polymul(P.polymul([-lo, 1.0], [hi, -1.0]), [0.3] * extra + [1.0])
+        p, d2 = _poly_d2(coef, x)
+        err = np.abs(A @ p - d2).max() / np.abs(d2).max()
+        if extra + 2 <= 5:
+            assert err < 1e-12, err
+        else:
+            assert err > 1e-6, err
+
+
+@pytest.mark.parametrize("deg", [2, 3, 4])
+def test_fd4_dirichlet_neumann_exact_on_quartics(deg):
+    """The 4th-order mixed matrix (Sec. 4.2: Dirichlet at lo, Neumann at hi,
+    semi-internal nodes) differentiates every polynomial of degree <= 4 with
+    p(lo) = 0 and p'(hi) = 0 exactly, its two modified last rows included."""
+    import numpy.polynomial.polynomial as P
+    lo, hi, n = 0.5, 3.0, 19
+    h = (hi - lo) / n
+    x = lo + h * np.arange(1, n + 1)
+    A = O.fd4_laplacian(n, lo, hi, O.NEUMANN)
+    k = deg - 1
+    base = [0.0] * k + [1.0] + [0.0] * 0  # x^k
+    # p = (x - lo)(x^k + c), c chosen so that p'(hi) = 0
+    c = -(hi ** k + (hi - lo) * k * hi ** (k - 1))
+    q = list(base)
+    q[0] += c
+    coef = P.polymul([-lo, 1.0], q)
+    p, d2 = _poly_d2(coef, x)
+    assert abs(P.polyval(hi, P.polyder(coef, 1))) < 1e-12
+    assert np.abs(A @ p - d2).max() / np.abs(d2).max() < 1e-12
+
+
+def test_fd4_direction_matrices_override():
+    """A problem carrying its own direction matrices uses them as given."""
+    A = [O.fd4_laplacian(8, 0.0, 1.0, O.DIRICHLET) * complex(0.7, 0.2) + 0.1 * np.eye(8),
+         O.fd4_laplacian(7, 0.0, 2.0, O.NEUMANN) * complex(0.7, 0.2) + 0.1 * np.eye(7)]
+    p = O.OracleProblem((8, 7), (O.DIRICHLET, O.NEUMANN), (0.0, 0.0), (1.0, 2.0), 1.0, 0.0, 0.0, -1.0, 0.5,
+                        mats=tuple(A))
+    for mu in range(2):
+        np.testing.assert_array_equal(O.direction_matrix(p, mu), A[mu])
+    L = O.LinearOperator(p, 0.05)
+    U = np.arange(56, dtype=complex).reshape(8, 7) / 56
+    dense = O.expm(0.05 * O.kron_sum_dense(A)) @ O.to_vec(U)
+    np.testing.assert_allclose(O.to_vec(L.expK(U, 1.0)), dense, atol=1e-13)
+
+
 def test_fd_row_sums():
     """Neumann rows sum to zero (constants are in the kernel); Dirichlet
     first/last rows lose one neighbour."""
