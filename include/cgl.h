@@ -113,6 +113,39 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc,
                     void* stream);
 
 /*
+ * Create a plan whose linear part K = A_d (+) ... (+) A_1 uses caller-supplied
+ * direction matrices (finite differences of any order or stencil, e.g. the
+ * paper's fourth-order matrices of cgl_fd4_matrix scaled by (a1 + i b1) plus
+ * a2/d, Sec. 4.1.1 and 4.2); the factors exp(c tau A_mu) are computed as in
+ * cgl_plan_create.
+ *   A[d]       host pointers; A[mu] holds the complex n_mu x n_mu matrix in
+ *              column-major order as (re, im) doubles (2 n_mu^2 doubles),
+ *              copied during the call.  Finite entries.
+ *   a3..b4, tau, precision, stream: as cgl_plan_create.
+ *   scheme     an exponential scheme (strang, split4, lawson4, lawson2,
+ *              strang_3t, split4_3t); CGL_RK4/CGL_RK2 give EUNSUPPORTED.
+ * Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA.
+ */
+int cgl_plan_create_ex(cgl_plan** out, int d, const int64_t* n, const double* const* A,
+                       double a3, double b3, double a4, double b4, double tau, int scheme,
+                       int precision, void* stream);
+
+/*
+ * The paper's fourth-order finite-difference d^2/dx^2 matrix on (lo, hi),
+ * real n x n, column-major, written to host memory `out` (n*n doubles).
+ *   right_bc = CGL_BC_DIRICHLET (Sec. 4.1.1): homogeneous Dirichlet at both
+ *     ends, internal nodes lo + j h, j = 1..n, h = (hi - lo)/(n + 1); centred
+ *     rows (-1, 16, -30, 16, -1)/(12 h^2), one-sided first row
+ *     (-15, -4, 14, -6, 1)/(12 h^2) and its mirror image as the last row.
+ *   right_bc = CGL_BC_NEUMANN (Sec. 4.2): Dirichlet at lo, homogeneous
+ *     Neumann at hi, semi-internal nodes lo + j h, j = 1..n, h = (hi - lo)/n;
+ *     first row as above, last rows (1, -6, 14, -4, -15, 10)/(12 h^2) and
+ *     (1, -8/3, -6, 56, -145/3)/(12 h^2).
+ * Host only (no device work).  Errors: EINVAL (n < 6, lo >= hi, other bc).
+ */
+int cgl_fd4_matrix(int n, double lo, double hi, int right_bc, double* out);
+
+/*
  * Advance the caller-owned device field u (N complex values, layout above)
  * by nsteps constant steps of the plan's scheme, in place.  Asynchronous on
  * `stream`.  The step sequence is recorded once per (plan, u) pair into a

@@ -374,9 +374,18 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
     for (int c = 0; c < p->nfac; ++c) {
       for (int mu = 0; mu < p->d; ++mu) {
         int same = -1;
-        for (int nu = 0; nu < mu; ++nu)
-          if (p->n[nu] == p->n[mu] && p->bc[nu] == p->bc[mu] && p->lo[nu] == p->lo[mu] && p->hi[nu] == p->hi[mu])
+        for (int nu = 0; nu < mu; ++nu) {
+          if (p->n[nu] != p->n[mu]) continue;
+          if (p->user_mats) {
+            const auto& x = p->userA[nu];
+            const auto& y = p->userA[mu];
+            bool eq = true;
+            for (size_t k = 0; eq && k < x.size(); ++k) eq = x[k].x == y[k].x && x[k].y == y[k].y;
+            if (eq) same = nu;
+          } else if (p->bc[nu] == p->bc[mu] && p->lo[nu] == p->lo[mu] && p->hi[nu] == p->hi[mu]) {
             same = nu;
+          }
+        }
         if (same >= 0) {
           p->fac64[c][mu] = p->fac64[c][same];
           p->fac[c][mu] = p->fac[c][same];
@@ -385,7 +394,7 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
           continue;
         }
         const int n = (int)p->n[mu];
-        std::vector<double2> A = fd_direction_matrix(p, mu);
+        std::vector<double2> A = p->user_mats ? p->userA[mu] : fd_direction_matrix(p, mu);
         CUDA_TRY(cudaMemcpyAsync(dA, A.data(), A.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
         if ((st = dev_alloc(p, (void**)&p->fac64[c][mu], (size_t)n * n * sizeof(double2)))) return st;
         CUDA_TRY(expm_device(dA, p->cval[c] * p->tau, n, p->fac64[c][mu], dW, norm1(A, n), s));
@@ -630,7 +639,7 @@ namespace cgl {
 
 int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
                      double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
-                     int scheme, int precision, void* stream, bool minimal) {
+                     int scheme, int precision, void* stream, bool minimal, const double* const* A) {
   g_last_error.clear();
   if (!out) return fail(CGL_EINVAL, "out is NULL");
   *out = nullptr;
@@ -658,6 +667,16 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
       return fail(CGL_EUNSUPPORTED, "periodic sizes must be powers of two <= 2048");
     if (!periodic && n[m] > 1024) return fail(CGL_EUNSUPPORTED, "finite-difference sizes must be <= 1024");
   }
+  if (A) {
+    if (periodic) return fail(CGL_EINVAL, "caller-supplied direction matrices need non-periodic directions");
+    if (scheme == CGL_RK4 || scheme == CGL_RK2)
+      return fail(CGL_EUNSUPPORTED, "caller-supplied direction matrices support the exponential schemes only");
+    for (int m = 0; m < d; ++m) {
+      if (!A[m]) return fail(CGL_EINVAL, "every direction matrix must be non-NULL");
+      for (int64_t k = 0; k < 2 * n[m] * n[m]; ++k)
+        if (!std::isfinite(A[m][k])) return fail(CGL_EINVAL, "direction matrices must be finite");
+    }
+  }
   if (precision == CGL_BF16X3) {
     if (periodic) return fail(CGL_EUNSUPPORTED, "BF16x3 applies to the finite-difference mode products only");
     for (int m = 0; m < d; ++m)
@@ -669,6 +688,13 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   cgl_plan* p = new cgl_plan();
   cudaGetDevice(&p->dev);
   p->d = d;
+  if (A) {
+    p->user_mats = true;
+    for (int m = 0; m < d; ++m) {
+      p->userA[m].resize((size_t)n[m] * n[m]);
+      for (size_t k = 0; k < p->userA[m].size(); ++k) p->userA[m][k] = make_double2(A[m][2 * k], A[m][2 * k + 1]);
+    }
+  }
   p->N = 1;
   for (int m = 0; m < d; ++m) {
     p->n[m] = n[m];
@@ -749,6 +775,50 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, cons
                     double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
                     int scheme, int precision, void* stream) {
   return plan_create_impl(out, d, n, bc, lo, hi, a1, b1, a2, a3, b3, a4, b4, tau, scheme, precision, stream, false);
+}
+
+int cgl_plan_create_ex(cgl_plan** out, int d, const int64_t* n, const double* const* A, double a3, double b3,
+                       double a4, double b4, double tau, int scheme, int precision, void* stream) {
+  if (!out) return fail(CGL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!A) return fail(CGL_EINVAL, "A is NULL");
+  if (d < 1 || d > 3) return fail(CGL_EINVAL, "d must be 1, 2 or 3");
+  // the boundary labels, domain and a1, b1, a2 are not used with caller-supplied matrices
+  const int bc[3] = {CGL_BC_DIRICHLET, CGL_BC_DIRICHLET, CGL_BC_DIRICHLET};
+  const double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  return plan_create_impl(out, d, n, bc, lo, hi, 1.0, 0.0, 0.0, a3, b3, a4, b4, tau, scheme, precision, stream, false,
+                          A);
+}
+
+int cgl_fd4_matrix(int n, double lo, double hi, int right_bc, double* out) {
+  if (!out) return fail(CGL_EINVAL, "out is NULL");
+  if (n < 6) return fail(CGL_EINVAL, "n must be >= 6");
+  if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo)) return fail(CGL_EINVAL, "need lo < hi (finite)");
+  if (right_bc != CGL_BC_DIRICHLET && right_bc != CGL_BC_NEUMANN)
+    return fail(CGL_EINVAL, "right_bc must be CGL_BC_DIRICHLET or CGL_BC_NEUMANN");
+  const double h = right_bc == CGL_BC_DIRICHLET ? (hi - lo) / (n + 1) : (hi - lo) / n;
+  const double s = 1.0 / (12.0 * h * h);
+  auto at = [&](int i, int j) -> double& { return out[(size_t)i + (size_t)j * n]; };
+  for (size_t k = 0; k < (size_t)n * n; ++k) out[k] = 0.0;
+  const double centred[5] = {-1, 16, -30, 16, -1};
+  for (int i = 1; i < n - 1; ++i)
+    for (int o = -2; o <= 2; ++o)
+      if (i + o >= 0 && i + o < n) at(i, i + o) = centred[o + 2] * s;
+  // first internal node: one-sided fourth-order row (the zero boundary value drops out)
+  const double first[5] = {-15, -4, 14, -6, 1};
+  for (int j = 0; j < 5; ++j) at(0, j) = first[j] * s;
+  if (right_bc == CGL_BC_DIRICHLET) {
+    for (int j = 0; j < n; ++j) at(n - 1, j) = 0.0;
+    for (int j = 0; j < 5; ++j) at(n - 1, n - 1 - j) = first[j] * s;
+  } else {
+    // last two nodes: Neumann closure of the semi-internal grid
+    const double penult[6] = {1, -6, 14, -4, -15, 10};
+    const double last[5] = {1, -8.0 / 3.0, -6, 56, -145.0 / 3.0};
+    for (int j = 0; j < n; ++j) at(n - 2, j) = at(n - 1, j) = 0.0;
+    for (int j = 0; j < 6; ++j) at(n - 2, n - 6 + j) = penult[j] * s;
+    for (int j = 0; j < 5; ++j) at(n - 1, n - 5 + j) = last[j] * s;
+  }
+  return CGL_OK;
 }
 
 int cgl_plan_destroy(cgl_plan* p) {

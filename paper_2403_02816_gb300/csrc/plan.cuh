@@ -49,6 +49,8 @@ struct cgl_plan {
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   double a1 = 0, b1 = 0, a2 = 0, a3 = 0, b3 = 0, a4 = 0, b4 = 0, tau = 0;
   int scheme = 0, precision = 0, periodic = 0, cubic = 0;
+  bool user_mats = false;            // direction matrices supplied by the caller
+  std::vector<double2> userA[3];     // their host copies (n_mu x n_mu, column-major)
   int64_t N = 0;
   size_t elem = 0;
 
@@ -97,8 +99,10 @@ void free_plan(cgl_plan* p);
 ModePassArgs make_mode_args(const cgl_plan* p, const Sweep& sw, int mu, void* const* bufs);
 // Plan construction; `minimal` skips the workspace, the capture stream and
 // the tensor-core buffers (factors only, for batches).
+// A (optional): caller-supplied direction matrices A_mu, complex n_mu x n_mu
+// column-major as (re, im) doubles, replacing (a1 + i b1) D2_mu + a2/d.
 int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
                      double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
-                     int scheme, int precision, void* stream, bool minimal);
+                     int scheme, int precision, void* stream, bool minimal, const double* const* A = nullptr);
 
 }  // namespace cgl

@@ -80,6 +80,9 @@ def load() -> ctypes.CDLL:
     sig = {
         "cgl_plan_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(D),
                                 ctypes.POINTER(D), D, D, D, D, D, D, D, D, I, I, VP]),
+        "cgl_plan_create_ex": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I64), ctypes.POINTER(VP), D, D, D, D, D, I,
+                                   I, VP]),
+        "cgl_fd4_matrix": (I, [I, D, D, I, ctypes.POINTER(D)]),
         "cgl_step": (I, [P, VP, I64, VP]),
         "cgl_step_host": (I, [P, VP, I64, VP]),
         "cgl_plan_destroy": (I, [P]),
@@ -159,6 +162,29 @@ def cgl_plan_create(d, n, bc, lo, hi, a1, b1, a2, a3, b3, a4, b4, tau, scheme, p
     return st, h
 
 
+def cgl_plan_create_ex(mats, a3, b3, a4, b4, tau, scheme, precision, stream=None):
+    """Plan with caller-supplied direction matrices (complex n_mu x n_mu numpy
+    arrays); returns (status, handle)."""
+    import numpy as np
+    lib = load()
+    h = ctypes.c_void_p()
+    cols = [np.asfortranarray(np.asarray(A, dtype=np.complex128)) for A in mats]
+    bufs = [np.frombuffer(c.tobytes(order="F"), dtype=np.float64).copy() for c in cols]
+    ptrs = (ctypes.c_void_p * len(bufs))(*[b.ctypes.data for b in bufs])
+    n = (ctypes.c_int64 * len(cols))(*[c.shape[0] for c in cols])
+    st = lib.cgl_plan_create_ex(ctypes.byref(h), len(cols), n, ptrs, a3, b3, a4, b4, tau, int(scheme), int(precision),
+                                _stream_handle(stream))
+    return st, h
+
+
+def cgl_fd4_matrix(n, lo, hi, right_bc):
+    """The paper's fourth-order d^2/dx^2 matrix (n x n numpy array)."""
+    import numpy as np
+    out = (ctypes.c_double * (n * n))()
+    check(load().cgl_fd4_matrix(int(n), float(lo), float(hi), int(right_bc), out), "cgl_fd4_matrix")
+    return np.frombuffer(out, dtype=np.float64).reshape((n, n), order="F").copy()
+
+
 def cgl_rel_error(x, y, precision, stream=None):
     """Relative L2 and inf errors of device tensor x against y (FP64 accumulation)."""
     out = (ctypes.c_double * 3)()
@@ -187,6 +213,21 @@ class Plan:
                                           prob.a3, prob.b3, prob.a4, prob.b4, tau, SCHEMES[scheme], self.prec,
                                           stream)
         check(st, "cgl_plan_create")
+
+    @classmethod
+    def from_matrices(cls, mats, a3, b3, a4, b4, tau: float, scheme: str, precision: str = "f64", stream=None):
+        """Plan whose direction matrices A_mu are given (cgl_plan_create_ex)."""
+        from . import inputs
+        self = cls.__new__(cls)
+        d = len(mats)
+        n = tuple(int(A.shape[0]) for A in mats)
+        self.prob = inputs.Problem(n, (CGL_BC_DIRICHLET,) * d, (0.0,) * d, (1.0,) * d, 1.0, 0.0, 0.0, a3, b3, a4, b4)
+        self.scheme = scheme
+        self.precision = precision
+        self.prec = PRECISIONS[precision]
+        st, self.handle = cgl_plan_create_ex(mats, a3, b3, a4, b4, tau, SCHEMES[scheme], self.prec, stream)
+        check(st, "cgl_plan_create_ex")
+        return self
 
     # torch helpers -------------------------------------------------------
     @property

@@ -320,3 +320,85 @@ def test_fma_peak_microbenchmark():
     f32 = nat.cgl_measure_fma_peak("f32", 8192)
     assert 0.3 < f64 < 1.4
     assert 20.0 < f32 < 90.0
+
+
+# ------------------------------------------------------------ caller-supplied matrices (fourth-order FD)
+
+def fd4_mats(n, rights, lo, hi, a1, b1, a2):
+    """A_mu = (a1 + i b1) D4_mu + a2/d with the paper's fourth-order matrices."""
+    d = len(n)
+    return tuple(complex(a1, b1) * O.fd4_laplacian(m, l, h, r) + (a2 / d) * np.eye(m)
+                 for m, r, l, h in zip(n, rights, lo, hi))
+
+
+def run_gpu_mats(mats, p, U0, tau, nsteps, scheme, prec):
+    with nat.Plan.from_matrices(mats, p.a3, p.b3, p.a4, p.b4, tau, scheme, prec) as plan:
+        u = nat.to_device(U0, DT[prec])
+        plan.step(u, nsteps)
+        torch.cuda.synchronize()
+        assert plan.device_status() == nat.CGL_OK
+        return nat.from_device(u)
+
+
+FD4_CASES = [((32, 24), (O.DIRICHLET, O.DIRICHLET)), ((12, 16, 10), (O.NEUMANN, O.DIRICHLET, O.NEUMANN)),
+             ((40,), (O.NEUMANN,))]
+
+
+@pytest.mark.parametrize("n,rights", FD4_CASES)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fd4_schemes_match_oracle(n, rights, prec):
+    """Plans built from the paper's fourth-order matrices (Sec. 4.1.1, 4.2)
+    through cgl_plan_create_ex against the oracle with the same matrices."""
+    p, rng = rand_problem(11, n, (0,) * len(n), cubic=False)
+    mats = fd4_mats(n, rights, p.lo, p.hi, p.a1, p.b1, p.a2)
+    op = O.OracleProblem(p.n, p.bc, p.lo, p.hi, p.a1, p.b1, p.a2, p.a3, p.b3, p.a4, p.b4, mats=mats)
+    U0 = smooth_data(p, rng, amp=0.6)
+    for s in ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t"):
+        ref = O.integrate(op, U0, 0.004, 4, s)
+        check(run_gpu_mats(mats, p, U0, 0.004, 4, s, prec), ref, prec, s)
+
+
+def test_fd4_tensor_cores_match_oracle():
+    n, rights = (128, 32), (O.DIRICHLET, O.NEUMANN)
+    p, rng = rand_problem(12, n, (0, 0), cubic=True)
+    mats = fd4_mats(n, rights, p.lo, p.hi, p.a1, p.b1, p.a2)
+    op = O.OracleProblem(p.n, p.bc, p.lo, p.hi, p.a1, p.b1, p.a2, p.a3, p.b3, p.a4, p.b4, mats=mats)
+    U0 = smooth_data(p, rng, amp=0.6)
+    for s in ("lawson4", "split4"):
+        ref = O.integrate(op, U0, 0.004, 4, s)
+        check(run_gpu_mats(mats, p, U0, 0.004, 4, s, "bf16x3"), ref, "bf16x3", s)
+
+
+def test_create_ex_reproduces_second_order_plan():
+    """Given the second-order matrices the plan builds itself, cgl_plan_create_ex
+    gives the same result as cgl_plan_create."""
+    p, rng = rand_problem(13, (24, 20), (0, 1))
+    op = oprob(p)
+    mats = tuple(O.direction_matrix(op, mu) for mu in range(2))
+    U0 = smooth_data(p, rng)
+    a = run_gpu(p, U0, 0.01, 5, "lawson4")
+    b = run_gpu_mats(mats, p, U0, 0.01, 5, "lawson4", "f64")
+    assert O.rel_l2(b, a) < 1e-13
+
+
+@pytest.mark.parametrize("scheme,order", [("lawson4", 4), ("split4", 4), ("strang", 2)])
+def test_fd4_temporal_orders_on_gpu(scheme, order):
+    """Temporal orders on a fourth-order FD Dirichlet problem (the setting of
+    the paper's Sec. 4.1.1 experiments), errors at T against a run with 1/8
+    of the smallest step, all on the GPU in FP64 (which matches the oracle to
+    1e-11).  As in the paper's table for this setting, the observed order of
+    the fourth-order schemes (and of Strang) rises towards its nominal value
+    as the step count grows (order reduction at large steps under Dirichlet
+    conditions): it increases pair by pair and is within 0.15 of nominal for
+    the finest pair."""
+    n = (48, 48)
+    p, rng = rand_problem(14, n, (0, 0), cubic=True, lo=-10.0, hi=10.0)
+    mats = fd4_mats(n, (O.DIRICHLET, O.DIRICHLET), p.lo, p.hi, p.a1, p.b1, p.a2)
+    U0 = smooth_data(p, rng, amp=0.5)
+    T = 0.4
+    ms = (20, 40, 80)
+    ref = run_gpu_mats(mats, p, U0, T / 640, 640, scheme, "f64")
+    errs = [O.rel_l2(run_gpu_mats(mats, p, U0, T / m, m, scheme, "f64"), ref) for m in ms]
+    orders = [O.observed_order(ms[i], errs[i], ms[i + 1], errs[i + 1]) for i in range(2)]
+    assert orders[1] > orders[0], (errs, orders)
+    assert abs(orders[1] - order) < 0.15, (errs, orders)
