@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--corr-traj", type=int, default=96, help="corrector: training trajectories")
     ap.add_argument("--corr-iters", type=int, default=3000, help="corrector: training iterations")
     ap.add_argument("--corr-test", type=int, default=8, help="corrector: held-out trajectories")
+    ap.add_argument("--corr-sub", type=int, default=8, help="corrector: fine steps per coarse step")
+    ap.add_argument("--corr-coarse-steps", type=int, default=312, help="corrector: coarse steps per trajectory")
     return ap.parse_args()
 
 
@@ -200,7 +202,8 @@ def run_corrector(args):
 
     nat.load()
     ntraj, iters, batch = args.corr_traj, args.corr_iters, 32
-    data = Lm.Dataset(ntraj=ntraj, snaps=8)
+    sub, csteps = args.corr_sub, args.corr_coarse_steps
+    data = Lm.Dataset(ntraj=ntraj, snaps=8, sub=sub, coarse_steps=csteps)
     corr = nat.Corrector(Lm.N, Lm.N, 32, 6, max_batch=batch)
     losses, train_s = Lm.train(corr, data, iters=iters, batch=batch, lr=1e-3, log_every=max(1, iters // 4))
     # throughput of one corrected coarse step vs 8 fine steps (one instance, 128^2)
@@ -208,7 +211,7 @@ def run_corrector(args):
     rng = np.random.default_rng(0)
     U0 = I.u0_bumps(p, rng)
     stream = torch.cuda.current_stream()
-    with nat.Plan(p, Lm.FINE_TAU, "lawson4", "f64") as fine, nat.Plan(p, Lm.COARSE_TAU, "lawson4", "f32") as crs:
+    with nat.Plan(p, Lm.FINE_TAU, "lawson4", "f64") as fine, nat.Plan(p, Lm.FINE_TAU * sub, "lawson4", "f32") as crs:
         uf = nat.to_device(U0, torch.complex128)
         uc = nat.to_device(U0, torch.complex64).reshape(1, Lm.N, Lm.N)
         prev = torch.empty_like(uc)
@@ -221,7 +224,7 @@ def run_corrector(args):
                 crs.step(uc, 1)
                 corr.apply(uc, prev, prm, uc)
 
-        for fn, key in ((lambda k: fine.step(uf, Lm.SUB * k), "fine_8_steps_f64"),
+        for fn, key in ((lambda k: fine.step(uf, sub * k), "fine_steps_f64"),
                         (lambda k: crs.step(uc, k), "coarse_step_f32"), (corrected, "corrected_coarse_step")):
             fn(3)
             torch.cuda.synchronize()
@@ -231,16 +234,16 @@ def run_corrector(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            if key == "fine_8_steps_f64":
+            if key == "fine_steps_f64":
                 t_fine = ms
             elif key == "coarse_step_f32":
                 t_coarse = ms
             else:
                 t_corr = ms
-    rows = Lm.evaluate(corr, ntraj=args.corr_test, seed=Lm.SEED + 7777)
+    rows = Lm.evaluate(corr, ntraj=args.corr_test, seed=Lm.SEED + 7777, sub=sub, coarse_steps=csteps)
     e_c = float(np.mean([r["coarse"] for r in rows]))
     e_l = float(np.mean([r["corrected"] for r in rows]))
-    held = Lm.Dataset(ntraj=args.corr_test, snaps=8, seed=Lm.SEED + 7777)
+    held = Lm.Dataset(ntraj=args.corr_test, snaps=8, seed=Lm.SEED + 7777, sub=sub, coarse_steps=csteps)
     one_step = {}
     for name, ds in (("train_pairs", data), ("held_out_pairs", held)):
         c, l = Lm.one_step_errors(corr, ds)
@@ -252,12 +255,16 @@ def run_corrector(args):
         "warmup": 3, "ms_per_step": t_corr, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+bf16", "data": "synthetic",
         "config": {"workload": "learned_corrector_2d_periodic_128^2", "fine_tau": Lm.FINE_TAU,
-                   "coarse_tau": Lm.COARSE_TAU, "train_trajectories": ntraj, "pairs": data.size,
-                   "iterations": iters, "batch": batch, "test_trajectories": args.corr_test,
-                   "t_final": Lm.COARSE_STEPS * Lm.COARSE_TAU},
+                   "coarse_tau": Lm.FINE_TAU * sub, "fine_steps_per_coarse": sub, "train_trajectories": ntraj,
+                   "pairs": data.size, "iterations": iters, "batch": batch, "test_trajectories": args.corr_test,
+                   "t_final": csteps * sub * Lm.FINE_TAU},
+        "correction_rms": {"complex64_coarse_vs_fine": data.correction_rms,
+                           "complex128_coarse_vs_fine": data.coarse64_rms,
+                           "note": "the complex128 coarse step's difference is the truncation part of the "
+                                   "target; the rest of the complex64 difference is FP32 rounding"},
         "dataset_seconds": data.seconds, "train_seconds": train_s,
         "train_samples_per_s": iters * batch / train_s, "losses": losses,
-        "ms": {"fine_8_steps_f64": t_fine, "coarse_step_f32": t_coarse, "corrected_coarse_step": t_corr},
+        "ms": {"fine_steps_f64": t_fine, "coarse_step_f32": t_coarse, "corrected_coarse_step": t_corr},
         "speedup_corrected_vs_fine_f64": t_fine / t_corr,
         "held_out_rel_l2_vs_fine": {"coarse": e_c, "corrected": e_l, "gain": e_c / e_l, "rows": rows},
         "one_step_rel_l2_vs_fine": one_step,

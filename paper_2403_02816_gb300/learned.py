@@ -50,9 +50,14 @@ def sample(rng, n=N):
 class Dataset:
     """Device tensors: un, coarse, target (complex64 [P, n, n]), params (float32 [P, 5])."""
 
-    def __init__(self, ntraj, snaps=8, seed=SEED, n=N, device="cuda", concurrency=32):
+    def __init__(self, ntraj, snaps=8, seed=SEED, n=N, device="cuda", concurrency=32, sub=SUB,
+                 coarse_steps=COARSE_STEPS):
         """Trajectories run `concurrency` at a time, each on its own CUDA stream
-        (one 128^2 instance fills only a few SMs)."""
+        (one 128^2 instance fills only a few SMs).  The coarse step is `sub`
+        fine steps long; snapshots are spread over `coarse_steps` coarse steps.
+        Besides the complex64 coarse step, `coarse64_rms` records the RMS of
+        the complex128 coarse step's difference to the fine result (the part
+        of the correction that does not come from FP32 rounding)."""
         import torch
         P = ntraj * snaps
         self.n = n
@@ -60,7 +65,9 @@ class Dataset:
         self.coarse = torch.empty_like(self.un)
         self.target = torch.empty_like(self.un)
         host_params = np.empty((P, 5), dtype=np.float32)
-        stride = COARSE_STEPS * SUB // snaps
+        stride = coarse_steps * sub // snaps
+        self.sub = sub
+        tru_parts = []  # device scalars, summed after the last synchronisation
         streams = [torch.cuda.Stream() for _ in range(min(concurrency, ntraj))]
         t0 = time.perf_counter()
         for g0 in range(0, ntraj, len(streams)):
@@ -70,36 +77,44 @@ class Dataset:
                 rng = np.random.Generator(np.random.PCG64(seed + 1000 * i))
                 par, p, U0 = sample(rng, n)
                 fine = nat.Plan(p, FINE_TAU, "lawson4", "f64", stream=s)
-                crs = nat.Plan(p, COARSE_TAU, "lawson4", "f32", stream=s)
+                crs = nat.Plan(p, FINE_TAU * sub, "lawson4", "f32", stream=s)
+                crs64 = nat.Plan(p, FINE_TAU * sub, "lawson4", "f64", stream=s)
                 with torch.cuda.stream(s):
                     u = nat.to_device(U0, torch.complex128, device)
                     v = torch.empty_like(u)
                     c = torch.empty((n, n), dtype=torch.complex64, device=device)
-                group.append((s, fine, crs, u, v, c, i))
+                    w = torch.empty_like(u)
+                group.append((s, fine, crs, crs64, u, v, c, w, i))
                 host_params[i * snaps:(i + 1) * snaps] = par
             for sn in range(snaps):
-                for s, fine, crs, u, v, c, i in group:
+                for s, fine, crs, crs64, u, v, c, w, i in group:
                     k = i * snaps + sn
                     with torch.cuda.stream(s):
                         if sn > 0:
                             fine.step(u, stride, stream=s)
                         self.un[k].copy_(u)
                         v.copy_(u)
-                        fine.step(v, SUB, stream=s)
+                        fine.step(v, sub, stream=s)
                         self.target[k].copy_(v)
                         c.copy_(self.un[k])
                         crs.step(c, 1, stream=s)
                         self.coarse[k].copy_(c)
+                        w.copy_(u)
+                        crs64.step(w, 1, stream=s)
+                        w.sub_(v)
+                        tru_parts.append(w.abs().pow(2).mean())
             torch.cuda.synchronize()
-            for s, fine, crs, *_ in group:
+            for s, fine, crs, crs64, *_ in group:
                 fine.close()
                 crs.close()
+                crs64.close()
         self.params = torch.from_numpy(host_params).to(device)
         torch.cuda.synchronize()
         self.seconds = time.perf_counter() - t0
         self.size = P
         # typical size of the correction: the network's output scale
         self.correction_rms = float((self.target - self.coarse).abs().pow(2).mean().sqrt())
+        self.coarse64_rms = float(np.sqrt(sum(float(x) for x in tru_parts) / max(len(tru_parts), 1)))
 
 
 def train(corr, data, iters, batch, lr=1e-3, seed=SEED, log_every=0):
@@ -138,23 +153,24 @@ def one_step_errors(corr, data, batch=16):
     return np.array(coarse_err), np.array(corr_err)
 
 
-def evaluate(corr, ntraj, seed, n=N, device="cuda"):
-    """Relative L2 errors at t = 4.992 of the coarse method with and without
-    the correction against the fine method, one held-out trajectory at a time."""
+def evaluate(corr, ntraj, seed, n=N, device="cuda", sub=SUB, coarse_steps=COARSE_STEPS):
+    """Relative L2 errors at t = coarse_steps * sub * FINE_TAU (4.992 for the
+    defaults) of the coarse method with and without the correction against the
+    fine method, one held-out trajectory at a time."""
     import torch
     rows = []
     for i in range(ntraj):
         rng = np.random.Generator(np.random.PCG64(seed + 1000 * i))
         par, p, U0 = sample(rng, n)
         prm = torch.tensor([par], dtype=torch.float32, device=device)
-        with nat.Plan(p, FINE_TAU, "lawson4", "f64") as fine, nat.Plan(p, COARSE_TAU, "lawson4", "f32") as crs:
+        with nat.Plan(p, FINE_TAU, "lawson4", "f64") as fine, nat.Plan(p, FINE_TAU * sub, "lawson4", "f32") as crs:
             uf = nat.to_device(U0, torch.complex128, device)
-            fine.step(uf, COARSE_STEPS * SUB)
+            fine.step(uf, coarse_steps * sub)
             uc = nat.to_device(U0, torch.complex64, device)
-            crs.step(uc, COARSE_STEPS)
+            crs.step(uc, coarse_steps)
             ul = nat.to_device(U0, torch.complex64, device).reshape(1, n, n)
             prev = torch.empty_like(ul)
-            for _ in range(COARSE_STEPS):
+            for _ in range(coarse_steps):
                 prev.copy_(ul)
                 crs.step(ul, 1)
                 corr.apply(ul, prev, prm, ul)
