@@ -291,8 +291,11 @@ int cgl_autotune_mode_tile(int n, int contiguous, int precision, int nrhs, int* 
  * eq. lawson4, in CGL_F32) and N a residual CNN: 3x3 convolutions with
  * circular padding, 9 -> hidden -> ... -> hidden -> 2 channels, ReLU between
  * layers; x = 9 planes (Re, Im of C(u_n); Re, Im of u_n; a1, b1, a2, a3, b3 as
- * constant planes).  BF16 weights in every convolution (FP32 masters), FP32
- * accumulation, Adam on the masters.  The paper has no learned part; this
+ * constant planes).  The forward and input-gradient convolutions run on the
+ * tensor cores with BF16 operands (weights, and each convolution's input
+ * activations or incoming gradients rounded to nearest even) and FP32
+ * accumulation; weight gradients in FP32 from the unrounded values; FP32
+ * masters, Adam on the masters.  The paper has no learned part; this
  * follows the fine method (the plain integrator at a smaller step) as the
  * training target and as the judge of the corrected error.
  *
@@ -335,6 +338,24 @@ int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, co
  * typical size of the correction (fine minus coarse) so that the network's
  * own outputs stay of order one.  EINVAL unless scale > 0 and finite. */
 int cgl_corrector_set_output_scale(cgl_corrector* c, float scale);
+/*
+ * One 3x3 convolution with circular padding on the tensor cores, the building
+ * block of the corrector: y = conv(x, w) + bias, optionally ReLU.
+ *   x      device float [B][Cin][H][W]; rounded to BF16 (nearest even) as the
+ *          MMA operand.
+ *   w      device BF16 bit patterns (uint16) [Cout][Cin][3][3].
+ *   bias   device float [Cout] or NULL.
+ *   y      device float [B][Cout][H][W]; must not overlap x.
+ *   1 <= Cin, Cout <= 32.  Products accumulate in FP32.
+ *   status optional device int; bit 1 is set if a bounded wait gave up.
+ * Asynchronous on `stream`.  Errors: EINVAL, ECUDA.
+ */
+int cgl_conv3x3(const float* x, const uint16_t* w, const float* bias, float* y, int B, int cin,
+                int cout, int H, int W, int relu, int* status, void* stream);
+
+/* Read (synchronising `stream`) and clear the corrector's device status word:
+ * CGL_ETIMEOUT if a bounded tensor-core wait gave up since the last read. */
+int cgl_corrector_last_device_status(cgl_corrector* c, void* stream);
 int cgl_corrector_destroy(cgl_corrector* c);
 
 /*

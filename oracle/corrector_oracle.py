@@ -88,27 +88,32 @@ def features(coarse: np.ndarray, un: np.ndarray, params: np.ndarray) -> np.ndarr
     return x
 
 
-def forward(weights, x, round_weights=True):
+def forward(weights, x, round_weights=True, round_acts=False):
     """weights: list of (w, b) FP32 masters.  Returns the activations
     [x, a_1, ..., a_L] (a_L = last convolution, no ReLU) using BF16-rounded w
-    (unrounded when round_weights is False).  The correction is
-    N(x) = out_scale * a_L."""
+    (unrounded when round_weights is False) and, with round_acts, each
+    convolution's input rounded to BF16 as well (the operands of a BF16
+    tensor-core convolution; the activations kept are the unrounded sums).
+    The correction is N(x) = out_scale * a_L."""
     acts = [x]
     for l, (w, b) in enumerate(weights):
-        y = conv3x3(acts[-1], bf16_round(w) if round_weights else w, b)
+        inp = bf16_round(acts[-1]) if round_acts else acts[-1]
+        y = conv3x3(inp, bf16_round(w) if round_weights else w, b)
         if l < len(weights) - 1:
             y = np.maximum(y, 0.0)
         acts.append(y)
     return acts
 
 
-def loss_and_grads(weights, x, coarse, target, round_weights=True, out_scale=1.0):
+def loss_and_grads(weights, x, coarse, target, round_weights=True, out_scale=1.0, round_acts=False):
     """Mean squared difference between C(u_n) + N(x), N(x) = out_scale * a_L,
     and the fine result over all B x 2 x H x W real values, measured in units
     of out_scale (i.e. the mean of ((C + N - F) / out_scale)^2); gradients by
     backpropagation (BF16 weights in the forward pass, gradients taken with
-    respect to those weights).  Returns (loss, grads, N(x))."""
-    acts = forward(weights, x, round_weights)
+    respect to those weights; with round_acts the incoming gradient of each
+    input-gradient convolution is rounded to BF16 too, the weight gradients
+    use the unrounded activations and gradients).  Returns (loss, grads, N(x))."""
+    acts = forward(weights, x, round_weights, round_acts)
     out = out_scale * acts[-1]
     pred_re = coarse.real + out[:, 0]
     pred_im = coarse.imag + out[:, 1]
@@ -124,7 +129,7 @@ def loss_and_grads(weights, x, coarse, target, round_weights=True, out_scale=1.0
         dw, db = conv3x3_weight_grad(acts[l], dy)
         grads[l] = (dw, db)
         if l > 0:
-            dy = conv3x3_adjoint(dy, bf16_round(w) if round_weights else w)
+            dy = conv3x3_adjoint(bf16_round(dy) if round_acts else dy, bf16_round(w) if round_weights else w)
     return loss, grads, out
 
 

@@ -7,6 +7,8 @@
 // Each CTA owns whole pencils, so every pass may run in place.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -380,6 +382,12 @@ struct StencilArgs {
   int* status;
 };
 template <class T> cudaError_t launch_kron_stencil(const StencilArgs& a, cudaStream_t s);
+
+// conv_mma.cu: 3x3 circular convolution on the tensor cores (BF16 operands,
+// FP32 accumulation), y = conv(x, w) + bias (optional ReLU); Cin, Cout <= 32.
+cudaError_t prepare_conv_mma();
+cudaError_t launch_conv_mma(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int B, int cin,
+                            int cout, int H, int W, int relu, int* status, cudaStream_t s);
 
 // expm.cu: FP64 complex n x n exponential of (scale * A) on the device.
 // dA: n x n column-major double2 (device); dOut: same layout.  work: 3*n*n double2.

@@ -9,15 +9,13 @@
 // convolution, FP32 accumulation; Adam (Kingma & Ba 2015) on the masters.
 //
 // Activations are NCHW FP32 (W fastest).  A 3x3 convolution is an implicit
-// GEMM per 16x16 pixel tile: the tile and its one-pixel circular halo for all
-// input channels, and the weights of all output channels (as FP32, output
-// channel fastest for 128-bit loads), sit in shared memory; each thread owns
-// one pixel and accumulates every output channel.  The backward pass w.r.t.
-// the input is the same convolution with the kernel flipped and the channel
-// roles swapped; the weight gradient is a per-tile reduction finished with
-// atomics.  The layers here are 9..32 channels wide: about 144 flop per byte
-// of activation traffic, so these convolutions are bounded by memory and
-// shared-memory bandwidth, not by arithmetic.
+// GEMM on the tensor cores (conv_mma.cu: per 128-pixel tile, nine
+// accumulating 128 x Cout x Cin MMAs with BF16 operands, FP32 accumulation).
+// The backward pass w.r.t. the input is the same convolution with the kernel
+// flipped and the channel roles swapped; the weight gradient (SIMT, FP32) is
+// a per-tile reduction over pixels finished with atomics.  The layers here
+// are 9..32 channels wide: about 144 flop per byte of activation traffic, so
+// these convolutions are bounded by memory, not by arithmetic.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -34,7 +32,6 @@ namespace cgl {
 
 constexpr int kTile = 16;
 constexpr int kHalo = kTile + 2;
-constexpr int kConvThreads = kTile * kTile;
 constexpr int kMaxCh = 32;
 
 // ------------------------------------------------------------------ kernels
@@ -58,60 +55,6 @@ __global__ void features_kernel(const float2* __restrict__ coarse, const float2*
     xb[2 * HW] = u.x;
     xb[3 * HW] = u.y;
     for (int k = 0; k < 5; ++k) xb[(4 + k) * HW] = params[(int64_t)src * 5 + k];
-  }
-}
-
-// y = conv3x3(x, w) + bias (optional ReLU).  w: BF16 [Cout][Cin][3][3].
-// Grid: (W/16, H/16, B).  COUTP = Cout rounded up to a multiple of 4.
-template <int COUTP>
-__global__ void __launch_bounds__(kConvThreads) conv3x3_kernel(const float* __restrict__ x,
-                                                               const __nv_bfloat16* __restrict__ w,
-                                                               const float* __restrict__ bias, float* __restrict__ y,
-                                                               int Cin, int Cout, int H, int W, int relu) {
-  extern __shared__ __align__(16) float smem[];
-  float* sw = smem;                        // [Cin][9][COUTP]
-  float* sx = smem + Cin * 9 * COUTP;      // [Cin][18][18]
-  const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
-  const int j0 = blockIdx.x * kTile, i0 = blockIdx.y * kTile, b = blockIdx.z;
-  const int64_t HW = (int64_t)H * W;
-  for (int e = threadIdx.x; e < Cin * 9 * COUTP; e += kConvThreads) {
-    const int co = e % COUTP, k = (e / COUTP) % 9, ci = e / (9 * COUTP);
-    sw[e] = co < Cout ? __bfloat162float(w[((int64_t)co * Cin + ci) * 9 + k]) : 0.f;
-  }
-  const float* xb = x + (int64_t)b * Cin * HW;
-  for (int e = threadIdx.x; e < Cin * kHalo * kHalo; e += kConvThreads) {
-    const int c = e % kHalo, r = (e / kHalo) % kHalo, ci = e / (kHalo * kHalo);
-    const int gi = (i0 + r - 1 + H) % H, gj = (j0 + c - 1 + W) % W;
-    sx[e] = xb[ci * HW + (int64_t)gi * W + gj];
-  }
-  __syncthreads();
-  float acc[COUTP];
-#pragma unroll
-  for (int o = 0; o < COUTP; ++o) acc[o] = 0.f;
-  for (int ci = 0; ci < Cin; ++ci) {
-    const float* sxc = sx + ci * kHalo * kHalo;
-    const float4* swc = reinterpret_cast<const float4*>(sw + ci * 9 * COUTP);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const float xv = sxc[(ty + k / 3) * kHalo + tx + k % 3];
-#pragma unroll
-      for (int o4 = 0; o4 < COUTP / 4; ++o4) {
-        const float4 wv = swc[k * (COUTP / 4) + o4];
-        acc[4 * o4 + 0] = fmaf(xv, wv.x, acc[4 * o4 + 0]);
-        acc[4 * o4 + 1] = fmaf(xv, wv.y, acc[4 * o4 + 1]);
-        acc[4 * o4 + 2] = fmaf(xv, wv.z, acc[4 * o4 + 2]);
-        acc[4 * o4 + 3] = fmaf(xv, wv.w, acc[4 * o4 + 3]);
-      }
-    }
-  }
-  float* yb = y + (int64_t)b * Cout * HW + (int64_t)(i0 + ty) * W + (j0 + tx);
-#pragma unroll
-  for (int o = 0; o < COUTP; ++o) {
-    if (o < Cout) {
-      float v = acc[o] + (bias ? bias[o] : 0.f);
-      if (relu) v = fmaxf(v, 0.f);
-      yb[o * HW] = v;
-    }
   }
 }
 
@@ -305,6 +248,7 @@ struct cgl_corrector {
   std::vector<float*> acts;  // acts[0] = features, acts[l+1] = output of layer l
   float* dbuf[2] = {nullptr, nullptr};
   double* loss = nullptr;
+  int* status = nullptr;  // device word: bit 1 = a bounded tensor-core wait gave up
   std::vector<void*> allocations;
 };
 
@@ -328,29 +272,14 @@ void free_corrector(cgl_corrector* c) {
 
 int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 32); }
 
-size_t conv_smem(int cin, int coutp) { return (size_t)(cin * 9 * coutp + cin * kHalo * kHalo) * sizeof(float); }
-
 cudaError_t launch_conv(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int B, int cin, int cout,
-                        int H, int W, int relu, cudaStream_t s) {
-  dim3 grid(W / kTile, H / kTile, B);
-  if (cout <= 4) {
-    conv3x3_kernel<4><<<grid, kConvThreads, conv_smem(cin, 4), s>>>(x, w, bias, y, cin, cout, H, W, relu);
-  } else if (cout <= 12) {
-    conv3x3_kernel<12><<<grid, kConvThreads, conv_smem(cin, 12), s>>>(x, w, bias, y, cin, cout, H, W, relu);
-  } else {
-    conv3x3_kernel<32><<<grid, kConvThreads, conv_smem(cin, 32), s>>>(x, w, bias, y, cin, cout, H, W, relu);
-  }
-  return cudaGetLastError();
+                        int H, int W, int relu, int* status, cudaStream_t s) {
+  return launch_conv_mma(x, w, bias, y, B, cin, cout, H, W, relu, status, s);
 }
 
 cudaError_t prepare_corrector_kernels() {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(conv3x3_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)))
-    return e;
-  if ((e = cudaFuncSetAttribute(conv3x3_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)))
-    return e;
-  if ((e = cudaFuncSetAttribute(conv3x3_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)))
-    return e;
+  cudaError_t e = prepare_conv_mma();
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(conv3x3_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
@@ -367,7 +296,7 @@ int forward_pass(cgl_corrector* c, int B, cudaStream_t s) {
   for (int l = 0; l < c->nlayers; ++l) {
     const auto& L = c->layers[l];
     cudaError_t e = launch_conv(c->acts[l], c->wbf + L.w_off, c->master + L.b_off, c->acts[l + 1], B, L.cin, L.cout,
-                                c->H, c->W, L.relu, s);
+                                c->H, c->W, L.relu, c->status, s);
     if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("conv forward: ") + cudaGetErrorString(e));
   }
   return CGL_OK;
@@ -411,7 +340,7 @@ int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const vo
     if (l > 0) {
       flip_weights_kernel<<<grid_for(L.cin * L.cout * 9), 256, 0, s>>>(c->wbf + L.w_off, c->wflip, L.cin, L.cout);
       CUDA_TRY(cudaGetLastError());
-      CUDA_TRY(launch_conv(dy, c->wflip, nullptr, c->dbuf[1 - cur], B, L.cout, L.cin, c->H, c->W, 0, s));
+      CUDA_TRY(launch_conv(dy, c->wflip, nullptr, c->dbuf[1 - cur], B, L.cout, L.cin, c->H, c->W, 0, c->status, s));
       cur = 1 - cur;
     }
   }
@@ -467,6 +396,8 @@ int cgl_corrector_create(cgl_corrector** out, int height, int width, int hidden,
   if (!st) st = corr_alloc(c, (void**)&c->m, off * sizeof(float));
   if (!st) st = corr_alloc(c, (void**)&c->v, off * sizeof(float));
   if (!st) st = corr_alloc(c, (void**)&c->loss, sizeof(double));
+  if (!st) st = corr_alloc(c, (void**)&c->status, sizeof(int));
+  if (!st && cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) st = fail(CGL_ECUDA, "memset status");
   for (int l = 0; !st && l <= layers; ++l) {
     const int ch = l == 0 ? 9 : c->layers[l - 1].cout;
     float* a = nullptr;
@@ -598,6 +529,17 @@ int cgl_corrector_set_output_scale(cgl_corrector* c, float scale) {
   if (!c || !(scale > 0.f) || !std::isfinite(scale)) return fail(CGL_EINVAL, "scale must be positive and finite");
   c->out_scale = scale;
   return CGL_OK;
+}
+
+int cgl_corrector_last_device_status(cgl_corrector* c, void* stream) {
+  if (!c) return fail(CGL_EINVAL, "corrector is NULL");
+  CUDA_TRY(cudaSetDevice(c->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return (h & 2) ? CGL_ETIMEOUT : CGL_OK;
 }
 
 int cgl_corrector_destroy(cgl_corrector* c) {

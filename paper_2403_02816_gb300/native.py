@@ -111,6 +111,8 @@ def load() -> ctypes.CDLL:
         "cgl_corrector_train_step": (I, [P, VP, VP, VP, VP, VP, I, ctypes.c_float, ctypes.POINTER(D), VP]),
         "cgl_corrector_apply": (I, [P, VP, VP, VP, I, VP, VP]),
         "cgl_corrector_destroy": (I, [P]),
+        "cgl_corrector_last_device_status": (I, [P, VP]),
+        "cgl_conv3x3": (I, [VP, VP, VP, VP, I, I, I, I, I, I, VP, VP]),
         "cgl_corrector_set_output_scale": (I, [P, ctypes.c_float]),
         "cgl_strerror": (ctypes.c_char_p, [I]),
         "cgl_last_error": (ctypes.c_char_p, []),
@@ -183,6 +185,18 @@ def cgl_fd4_matrix(n, lo, hi, right_bc):
     out = (ctypes.c_double * (n * n))()
     check(load().cgl_fd4_matrix(int(n), float(lo), float(hi), int(right_bc), out), "cgl_fd4_matrix")
     return np.frombuffer(out, dtype=np.float64).reshape((n, n), order="F").copy()
+
+
+def cgl_conv3x3(x, w_bf16, bias, y, relu, status=None, stream=None):
+    """One tensor-core 3x3 circular convolution: x float32 [B][Cin][H][W],
+    w_bf16 int16/uint16 bit patterns [Cout][Cin][3][3], bias float32 [Cout]
+    or None, y float32 [B][Cout][H][W] (device tensors)."""
+    B, cin, H, W = x.shape
+    cout = w_bf16.shape[0]
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    check(load().cgl_conv3x3(ptr(x), ptr(w_bf16), ptr(bias), ptr(y), B, cin, cout, H, W, int(relu), ptr(status),
+                             _stream_handle(stream)), "cgl_conv3x3")
+    return y
 
 
 def cgl_rel_error(x, y, precision, stream=None):
@@ -471,6 +485,9 @@ class Corrector:
         check(load().cgl_corrector_apply(self.handle, _ptr(coarse), _ptr(un), _ptr(params), int(coarse.shape[0]),
                                          _ptr(out), _stream_handle(stream)), "cgl_corrector_apply")
         return out
+
+    def device_status(self, stream=None) -> int:
+        return load().cgl_corrector_last_device_status(self.handle, _stream_handle(stream))
 
     def close(self):
         if getattr(self, "handle", None):
