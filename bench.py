@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="periodic128",
-                    choices=["periodic128", "periodic256_f32", "neumann256", "batch512", "corrector"],
+                    choices=["periodic128", "periodic256_f32", "neumann256", "stencil256", "batch512", "corrector"],
                     help="periodic128: the headline 3D periodic workload; periodic256_f32: the same "
                          "problem at 256^3 in complex64 (HBM roofline, cuFFT yardstick); neumann256: the 3D "
                          "Neumann precision study (FP64 / FP32 / BF16x3 tensor cores)")
@@ -457,6 +457,65 @@ def run_periodic_f32(args):
     print(json.dumps(line))
 
 
+def run_stencil256(args):
+    """Runge-Kutta (RK4, eq. RK4) on the 3D Neumann 256^3 finite-difference
+    problem (the precision-study workload's grid and parameters) with a step
+    below RK4's stability limit: each stage is one launch of the eq. kronsumv
+    stencil fused with the stage epilogue, an HBM-bound kernel; FP64 and FP32."""
+    import torch
+    from paper_2403_02816_gb300 import native as nat
+
+    dev = torch.device("cuda", 0)
+    nat.load()
+    w = I.workload_3d_neumann(256)
+    U0 = I.u0_3d_neumann(w)
+    N = w.prob.N
+    tau = 2e-4  # below 2.8 / |lambda_max(K)| for this grid
+    chunk = args.chunk
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6790.0))
+    res, prof = {}, {}
+    with Clocks(0) as clk:
+        for prec in ("f64", "f32"):
+            dt = torch.complex128 if prec == "f64" else torch.complex64
+            with nat.Plan(w.prob, tau, "rk4", prec) as plan:
+                u = nat.to_device(U0, dt, dev)
+                for _ in range(max(args.warmup, 3)):
+                    plan.step(u, 1)
+                torch.cuda.synchronize()
+                ms = 0.0
+                for _ in range(args.steps):
+                    flush.fill_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    plan.step(u, chunk)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                res[prec] = {"grid_pt_steps_per_s": N * chunk * args.steps / (ms / 1e3),
+                             "ms_per_time_step": ms / (chunk * args.steps), "device_status": plan.device_status()}
+                prof[prec] = plan.profile(u, 1)
+    rl = {}
+    for prec in ("f64", "f32"):
+        k = [r for r in prof[prec] if r["name"].startswith("kron_stencil")][0]
+        gbs = k["bytes"] / (k["total_ms"] / 1e3) / 1e9
+        rl[prec] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "kernel": k["name"], "launches_profiled": k["launches"],
+                    "avg_launch_ms": k["total_ms"] / k["launches"],
+                    "bytes_counted": "per stage: the stage argument, 3 extra inputs and 1-2 outputs per point"}
+    line = {
+        "metric": METRIC, "value": res["f32"]["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": res["f32"]["ms_per_time_step"] * chunk,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3d_cubic_neumann_fd2_256^3_rk4", "scheme": "rk4", "tau": tau, "grid": [256] * 3,
+                   "time_steps_per_bench_step": chunk, "l2": "flushed (256 MiB write) between timed iterations"},
+        "precisions": res, "roofline": rl["f32"], "roofline_f64": rl["f64"], "kernels": prof, "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def measured_fma_peaks():
     """FP64 / FP32 FMA throughput measured by the library's microbenchmark."""
     from paper_2403_02816_gb300 import native as nat
@@ -568,6 +627,9 @@ def main():
         return
     if args.workload == "periodic256_f32":
         run_periodic_f32(args)
+        return
+    if args.workload == "stencil256":
+        run_stencil256(args)
         return
     if args.workload == "batch512":
         run_batch512(args)
