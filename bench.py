@@ -591,6 +591,24 @@ def cpu_oracle_steps(w, U0, scheme, nsteps):
     return time.perf_counter() - t0, U
 
 
+def over_ranks(ms_local, units_local, dist=None, device="cpu"):
+    """Whole-job timing of replicas (one per rank): the slowest rank's time and
+    the work of all ranks, value = total units / slowest time.  `dist` is
+    torch.distributed with an initialised process group, or None for one
+    process."""
+    import torch
+    t = torch.tensor([float(ms_local), float(units_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        ms_t = t[:1].clone()
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        u_t = t[1:].clone()
+        dist.all_reduce(u_t, op=dist.ReduceOp.SUM)
+        ms_max, units = float(ms_t.item()), float(u_t.item())
+    else:
+        ms_max, units = float(ms_local), float(units_local)
+    return ms_max, units, units / (ms_max / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -686,12 +704,7 @@ def main():
     with Clocks(local) as clk:
         ms = timed(plan, u, args.steps, max(args.warmup, 3))
     clocks = clk.summary()
-    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    units = N * chunk * args.steps * world
-    value = units / (ms_max / 1e3)
+    ms_max, units, value = over_ranks(ms, N * chunk * args.steps, dist, device=dev)
     status = plan.device_status()
 
     # per-kernel timing for the roofline (CUDA events around every launch)
