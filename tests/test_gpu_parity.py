@@ -402,3 +402,43 @@ def test_fd4_temporal_orders_on_gpu(scheme, order):
     orders = [O.observed_order(ms[i], errs[i], ms[i + 1], errs[i + 1]) for i in range(2)]
     assert orders[1] > orders[0], (errs, orders)
     assert abs(orders[1] - order) < 0.15, (errs, orders)
+
+
+# ------------------------------------------------------------ maximum sizes and degenerate cases
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_largest_periodic_and_fd_sizes(prec):
+    """The largest supported pencils: periodic n = 2048 (the Stockham pass in
+    both precisions) and finite differences n = 1024 (one mode product over a
+    1024 x 1024 factor), one and two dimensions."""
+    cases = [((2048,), (2,)), ((2048, 4), (2, 2)), ((1024,), (0,)), ((1024, 3), (1, 0))]
+    for n, bc in cases:
+        p, rng = rand_problem(21, n, bc, cubic=False)
+        U0 = smooth_data(p, rng, amp=0.6)
+        for s in ("lawson4", "split4"):
+            ref = O.integrate(oprob(p), U0, 0.002, 2, s)
+            check(run_gpu(p, U0, 0.002, 2, s, prec), ref, prec, "%s %s" % (n, s))
+
+
+def test_cubic_flow_at_alpha3_zero():
+    """a3 = 0 (allowed, although the paper assumes a3 != 0): the exact cubic
+    flow's closed form is singular there, its Lambda form is not."""
+    p = I.Problem((24, 20), (0, 1), (-5.0, -4.0), (5.0, 4.0), 0.9, 0.3, 0.4, 0.0, 1.1, 0.0, 0.0)
+    rng = np.random.default_rng(22)
+    U0 = smooth_data(p, rng)
+    for s in ("strang", "split4", "strang3t"):
+        ref = O.integrate(oprob(p), U0, 0.01, 5, s)
+        check(run_gpu(p, U0, 0.01, 5, s), ref, "f64", s)
+
+
+def test_zero_field_stays_zero():
+    """u = 0 is a fixed point of every scheme (g(0) = 0, the flows are linear
+    maps on it): the GPU returns exactly zero."""
+    for n, bc, schemes in (((16, 12), (0, 1), ("strang", "split4", "lawson4", "lawson2", "rk4")),
+                           ((16, 8), (2, 2), ("strang", "split4", "lawson4", "rk4", "rk2", "split4_3t"))):
+        p, _ = rand_problem(23, n, bc)
+        U0 = np.zeros(p.n, dtype=complex)
+        for s in schemes:
+            for prec in ("f64", "f32"):
+                got = run_gpu(p, U0, 0.003, 3, s, prec)
+                assert not np.any(got), (n, s, prec)
