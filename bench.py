@@ -38,6 +38,9 @@ UNIT = "grid-pt·steps/s"
 FP64_FMA_PER_CLK_PER_SM = 2
 N_SM = 152
 SM_MAX_MHZ = 2070.0
+# The paper's 3D cubic-quintic periodic 128^3 split4 run (Sec. 4.3 table): 900
+# steps in 842.6 s, i.e. 128^3 * 900 / 842.6 grid-pt.steps/s (context only).
+PAPER_E4_SPLIT4 = 128 ** 3 * 900 / 842.6
 # FP32: 128 FP32 FMA per clock per SM.
 FP32_PEAK_TFLOPS = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -774,6 +777,10 @@ def main():
             "gpu_launches": info["launches_per_step"] * chunk * args.steps,
             "clocks": clocks, "device_status": status,
             "rel_l2_vs_oracle_1step": parity, "schemes_grid_pt_steps_per_s": extras,
+            "paper_context": {
+                "note": "the paper's nearest run (3D cubic-quintic, periodic Fourier 128^3, split4; other domain "
+                        "and parameters, so not vs_baseline); MATLAB FP64 on a 6-core laptop CPU",
+                "grid_pt_steps_per_s": PAPER_E4_SPLIT4, "ratio": value / PAPER_E4_SPLIT4},
             "kernels": prof,
         }
         print(json.dumps(line))
