@@ -16,11 +16,15 @@
 // output rows of one component (re or im; nc = n or n/2 <= 128 rows, so that
 // two CTAs share an SM and one's epilogue overlaps the other's MMAs), with the
 // (h,h) product and the five correction products in separate TMEM
-// accumulators that the epilogue adds in FP32; K advances 16 per pipeline
-// stage, four stages, filled by TMA
-// (A: K-major for mode 1 whose fibers are contiguous, MN-major
-// for the other modes; B: K-major), consumed by tcgen05.mma issued by one
-// thread, freed by tcgen05.commit.  Every mbarrier wait is bounded: on
+// accumulators that the epilogue adds in FP32.  K advances kStageK per
+// pipeline stage, two stages within half an SM's shared memory; one thread
+// fills a stage with one TMA copy for the three A splits and one for the
+// three B splits (A: K-major for mode 1 whose fibers are contiguous, MN-major
+// for the other modes; B: K-major), another issues its tcgen05.mma and frees
+// it with tcgen05.commit.  The copy engine's cost goes with the number of
+// copies and the issuing threads' with their instruction count, so both are
+// kept minimal: a few large boxes, incremental slot / phase / descriptor
+// arithmetic.  Every mbarrier wait is bounded: on
 // timeout the kernel sets bit 1 of the status word, skips its stores, waits
 // (bounded) for its own copies, frees its TMEM and returns.
 //
@@ -38,9 +42,18 @@
 namespace cgl {
 
 constexpr int kMmaThreads = 128;
-constexpr int kMmaStages = 4;
 constexpr int kMmaM = 128;
-constexpr int kMmaK = 16;
+constexpr int kMmaK = 16;  // K of one tcgen05.mma
+// K per pipeline stage (one copy per operand) and stages per CTA.  Measured on
+// the 256^3 mode passes (ms per pass, two CTAs per SM unless noted): K 16 x 4
+// stages 0.390, K 32 x 2 stages 0.332, K 32 x 3 stages (one CTA per SM)
+// 0.469, K 32 x 4 / K 64 x 2 (one CTA per SM, issue on one thread) 0.56.
+constexpr int kStageK = 32;
+constexpr int kMaxStages = 2;
+constexpr int kSmemPerCta = 113 * 1024;  // two CTAs per SM
+// K-major rows of kStageK BF16 values: swizzle span = row bytes
+constexpr uint32_t kKRowBytes = kStageK * 2;
+constexpr uint32_t kKSwizzleDesc = kKRowBytes == 32 ? 6 : kKRowBytes == 64 ? 4 : 2;
 
 
 __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
@@ -63,13 +76,14 @@ struct MmaPassArgs {
   int nc;            // outputs (rows i) of one component per CTA: n or n/2
   int nsub;          // n / nc
   int tmem_cols;     // power of two >= 2 nc
+  int stages;        // pipeline depth
   int* status;
 };
 
-// One pipeline stage: three A splits (128 fibers x 16) and three B splits
-// (n output rows of one half x 16).
+// One pipeline stage: three A splits (128 fibers x kStageK) and three B
+// splits (nc output rows x kStageK).
 static __host__ __device__ constexpr uint32_t mma_stage_bytes(int nc) {
-  return 3u * (kMmaM * kMmaK * 2u) + 3u * (static_cast<uint32_t>(nc) * kMmaK * 2u);
+  return 3u * (kMmaM * kStageK * 2u) + 3u * (static_cast<uint32_t>(nc) * kStageK * 2u);
 }
 
 // CTA (tile, half): 128 fibers x the n outputs of component c' = half.
@@ -86,14 +100,18 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   const int rhs = blockIdx.y;
   const CUtensorMap* tmA = rhs ? &tmA1 : &tmA0;
   const CUtensorMap* tmB = rhs ? &tmB1 : &tmB0;
-  const int nk = (2 * n) / kMmaK;
-  const uint32_t a_bytes = kMmaM * kMmaK * 2;
+  // K = 2n runs over (component c, position j); a stage holds kStageK values
+  // of j of one component (the copies fill j >= n with zeros)
+  const int nkc = (n + kStageK - 1) / kStageK;
+  const int nk = 2 * nkc;
+  const int S = a.stages;
+  const uint32_t a_bytes = kMmaM * kStageK * 2;
   const int nc = a.nc;
-  const uint32_t b_bytes = static_cast<uint32_t>(nc) * kMmaK * 2;
+  const uint32_t b_bytes = static_cast<uint32_t>(nc) * kStageK * 2;
   const uint32_t stage_bytes = mma_stage_bytes(nc);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + kMmaStages * stage_bytes);
-  uint64_t* empty = full + kMmaStages;
-  uint64_t* accum = empty + kMmaStages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* accum = empty + S;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5;
@@ -116,7 +134,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   }
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kMmaStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
@@ -131,67 +149,87 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const uint32_t d_main = tmem, d_corr = tmem + nc;
 
+  // thread 32 copies stages in as slots free up; thread 0 issues the MMAs
+  // of each stage as it lands and frees the slot with tcgen05.commit.  Slot
+  // and phase advance incrementally (no divisions on the issuing threads).
+  int* counters = abort_flag + 1;  // stages loaded / consumed / committed
+  if (threadIdx.x == 32) {
+    int slot = 0, c = 0, j0 = 0, loaded = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    const int rowB = half * n + sub * nc, pq = (int)(p0 / 64);
+    for (int kb = 0; kb < nk; ++kb) {
+      // the slot's previous stage (kb - S) must have been consumed
+      if (kb >= S && !mbar_wait(smem_u32(&empty[slot]), phase ^ 1u)) { ok = false; break; }
+      const uint32_t st = smem_u32(base + slot * stage_bytes), bar = smem_u32(&full[slot]);
+      mbar_expect_tx(bar, stage_bytes);
+      // one box each for the three A splits and the three B splits
+      if (a.a_mn)
+        tma_load_5d(st, tmA, bar, 0, j0, pq, (int)(q0 + a.Q * c), 0);
+      else
+        tma_load_4d(st, tmA, bar, j0, (int)q0, c, 0);
+      tma_load_4d(st + 3 * a_bytes, tmB, bar, j0, rowB, c, 0);
+      loaded = kb + 1;
+      if (++slot == S) { slot = 0; phase ^= 1u; }
+      j0 += kStageK;
+      if (j0 >= n) { j0 = 0; ++c; }
+    }
+    counters[0] = loaded;
+    if (!ok) *abort_flag = 1;
+  }
   if (threadIdx.x == 0) {
     const uint32_t idesc = idesc_bf16(kMmaM, nc, a.a_mn);
-    auto issue_load = [&](int kb, int slot) {
-      uint8_t* st = base + slot * stage_bytes;
-      const uint32_t bar = smem_u32(&full[slot]);
-      mbar_expect_tx(bar, stage_bytes);
-      const int k0 = kb * kMmaK;
-      const int c = k0 / n, j0 = k0 - c * n;
-      for (int s = 0; s < 3; ++s) {
-        const uint32_t dA = smem_u32(st + s * a_bytes);
-        const int plane = s * 2 + c;
-        if (a.a_mn) {
-          tma_load_4d(dA, tmA, bar, (int)p0, j0, (int)q0, plane);
-          tma_load_4d(dA + 2048, tmA, bar, (int)p0 + 64, j0, (int)q0, plane);
-        } else {
-          tma_load_3d(dA, tmA, bar, j0, (int)q0, plane);
-        }
-        tma_load_3d(smem_u32(st + 3 * a_bytes + s * b_bytes), tmB, bar, k0, half * n + sub * nc, s);
-      }
-    };
+    // descriptors of slot 0 / split 0 / K step 0; the other operands differ
+    // only in the start address (16-byte units in the low bits).  MN-major A:
+    // two 64-fiber halves of kStageK rows of 128 B, 8-row groups 1024 B
+    // apart, one K step = 16 rows = 2048 B.  K-major A / B: rows of
+    // kKRowBytes, 8-row groups 8 rows apart, one K step = 32 B along the
+    // (swizzled) row.
+    const uint64_t a0 = a.a_mn ? smem_desc(smem_u32(base), kStageK * 128u, 1024, 2)
+                               : smem_desc(smem_u32(base), 16, 8 * kKRowBytes, kKSwizzleDesc);
+    const uint64_t b0 = smem_desc(smem_u32(base + 3 * a_bytes), 16, 8 * kKRowBytes, kKSwizzleDesc);
+    const uint32_t a_ks = a.a_mn ? 2048u / 16 : 32u / 16, b_ks = 32u / 16;
+    const uint32_t a_sp = a_bytes / 16, b_sp = b_bytes / 16;
     // split products: five corrections (l,h) (h,l) (m,m) (m,h) (h,m), then (h,h)
-    const int pa[6] = {2, 0, 1, 1, 0, 0};
-    const int pb[6] = {0, 2, 1, 0, 1, 0};
-    int loaded = 0;
-    for (; loaded < kMmaStages && loaded < nk; ++loaded) issue_load(loaded, loaded);
-    int consumed = 0, committed = 0;
+    constexpr uint32_t pa[6] = {2, 0, 1, 1, 0, 0};
+    constexpr uint32_t pb[6] = {0, 2, 1, 0, 1, 0};
+    int slot = 0, j0 = 0, consumed = 0, committed = 0;
+    uint32_t phase = 0;
     bool ok = true;
     for (int kb = 0; kb < nk; ++kb) {
-      const int slot = kb % kMmaStages;
-      if (!mbar_wait(smem_u32(&full[slot]), (kb / kMmaStages) & 1)) { ok = false; break; }
+      if (!mbar_wait(smem_u32(&full[slot]), phase)) { ok = false; break; }
       consumed = kb + 1;
       tc_fence_after();
-      uint8_t* st = base + slot * stage_bytes;
-      for (int pr = 0; pr < 6; ++pr) {
-        const uint32_t aaddr = smem_u32(st + pa[pr] * a_bytes);
-        const uint64_t adesc = a.a_mn ? smem_desc(aaddr, 2048, 1024, 2) : smem_desc(aaddr, 16, 256, 6);
-        const uint64_t bdesc = smem_desc(smem_u32(st + 3 * a_bytes + pb[pr] * b_bytes), 16, 256, 6);
-        if (pr < 5) mma_bf16(d_corr, adesc, bdesc, idesc, (kb > 0 || pr > 0) ? 1u : 0u);
-        else mma_bf16(d_main, adesc, bdesc, idesc, kb > 0 ? 1u : 0u);
+      const uint32_t so = slot * (stage_bytes / 16);
+      const int ksteps = min(kStageK, n - j0) / kMmaK;
+      for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr) {
+          const uint64_t ad = a0 + (so + pa[pr] * a_sp + ks * a_ks);
+          const uint64_t bd = b0 + (so + pb[pr] * b_sp + ks * b_ks);
+          const bool first = kb == 0 && ks == 0;
+          if (pr < 5) mma_bf16(d_corr, ad, bd, idesc, (!first || pr > 0) ? 1u : 0u);
+          else mma_bf16(d_main, ad, bd, idesc, first ? 0u : 1u);
+        }
       }
       mma_commit(smem_u32(&empty[slot]));
       committed = kb + 1;
-      // refill the slot consumed one iteration ago
-      if (kb >= 1 && loaded < nk) {
-        const int ps = (kb - 1) % kMmaStages;
-        if (!mbar_wait(smem_u32(&empty[ps]), ((kb - 1) / kMmaStages) & 1)) { ok = false; break; }
-        issue_load(loaded, ps);
-        ++loaded;
-      }
+      if (++slot == S) { slot = 0; phase ^= 1u; }
+      j0 += kStageK;
+      if (j0 >= n) j0 = 0;
     }
-    if (ok) {
-      mma_commit(smem_u32(accum));
-    } else {
-      // give up: wait (bounded) for this CTA's own copies and MMAs in flight
-      atomicOr(a.status, 2);
-      *abort_flag = 1;
-      for (int kb = consumed; kb < loaded; ++kb)
-        mbar_wait(smem_u32(&full[kb % kMmaStages]), (kb / kMmaStages) & 1);
-      if (committed > 0)
-        mbar_wait(smem_u32(&empty[(committed - 1) % kMmaStages]), ((committed - 1) / kMmaStages) & 1);
-    }
+    counters[1] = consumed;
+    counters[2] = committed;
+    if (ok) mma_commit(smem_u32(accum));
+    else *abort_flag = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    // give up: wait (bounded) for this CTA's own copies and MMAs in flight
+    atomicOr(a.status, 2);
+    const int loaded = counters[0], consumed = counters[1], committed = counters[2];
+    for (int kb = consumed; kb < loaded; ++kb) mbar_wait(smem_u32(&full[kb % S]), (kb / S) & 1);
+    if (committed > 0) mbar_wait(smem_u32(&empty[(committed - 1) % S]), ((committed - 1) / S) & 1);
   }
   __syncthreads();
 
@@ -205,23 +243,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   tc_fence_after();
   if (good) {
     const int m = threadIdx.x;  // TMEM lane = fiber of the tile
-    bool valid;
-    int64_t obase, ostride;     // output index of row i = obase + ostride * i
-    if (a.a_mn) {
-      valid = true;
-      obase = (p0 + m) + a.P * (int64_t)n * q0;
-      ostride = a.P;
-    } else {
-      const int64_t q = q0 + m;
-      valid = q < a.Q;
-      obase = (int64_t)n * q;
-      ostride = 1;
-    }
     const uint32_t lane_addr = static_cast<uint32_t>(warp * 32) << 16;
     // strided fibers (modes > 1): stage 16 output rows x 128 fibers in the
     // (now idle) pipeline buffers and store them as 16-byte chunks along the
-    // contiguous fiber index
+    // contiguous fiber index.  Contiguous fibers (mode 1): stage the whole
+    // FP32 tile [128 fibers][nc] (pitch nc + 4 floats: conflict-free 16-byte
+    // stores) and write each fiber's nc outputs as one contiguous run.
     const int64_t tile0 = p0 + a.P * (int64_t)n * q0;
+    const int pitch = nc + 4;
     for (int c0 = 0; c0 < nc; c0 += 16) {
       const int i0 = sub * nc + c0;  // first output row of this chunk
       uint32_t rm[16], rc[16];
@@ -230,76 +259,84 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       float v[16];
 #pragma unroll
       for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(rm[t]) + __uint_as_float(rc[t]);
-      if (a.a_mn) {
-        if (a.out_fp32) {
-          float* so = reinterpret_cast<float*>(base);  // [16 rows][128 fibers]
+      if (!a.a_mn) {
+        float4* so = reinterpret_cast<float4*>(reinterpret_cast<float*>(base) + m * pitch + c0);
 #pragma unroll
-          for (int t = 0; t < 16; ++t) so[t * kMmaM + m] = v[t];
-          __syncthreads();
-          float* o = reinterpret_cast<float*>(a.out[rhs]) + (int64_t)half * a.N + tile0;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int c = threadIdx.x + k * kMmaThreads;  // float4 chunk: row c / 32, column (c % 32) * 4
-            const int row = c >> 5, col = (c & 31) * 4;
-            *reinterpret_cast<float4*>(o + a.P * (i0 + row) + col) =
-                *reinterpret_cast<const float4*>(so + row * kMmaM + col);
-          }
-          __syncthreads();
-        } else {
-          __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(base);  // [3 splits][16 rows][128 fibers]
-#pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            __nv_bfloat16 sh, sm, sl;
-            split3(v[t], sh, sm, sl);
-            so[(0 * 16 + t) * kMmaM + m] = sh;
-            so[(1 * 16 + t) * kMmaM + m] = sm;
-            so[(2 * 16 + t) * kMmaM + m] = sl;
-          }
-          __syncthreads();
-          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out[rhs]);
-#pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            const int c = threadIdx.x + k * kMmaThreads;  // 16-byte chunk of 8 fibers
-            const int s = c >> 8, row = (c >> 4) & 15, col = (c & 15) * 8;
-            *reinterpret_cast<uint4*>(o + (int64_t)(s * 2 + half) * a.N + tile0 + a.P * (i0 + row) + col) =
-                *reinterpret_cast<const uint4*>(so + (s * 16 + row) * kMmaM + col);
-          }
-          __syncthreads();
-        }
+        for (int t = 0; t < 4; ++t) so[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
         continue;
       }
-      if (!valid) continue;
       if (a.out_fp32) {
-        float* o = reinterpret_cast<float*>(a.out[rhs]) + (int64_t)half * a.N;
-        if (!a.a_mn) {
-          float4* d4 = reinterpret_cast<float4*>(o + obase + i0);
+        float* so = reinterpret_cast<float*>(base);  // [16 rows][128 fibers]
 #pragma unroll
-          for (int t = 0; t < 4; ++t) d4[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
-        } else {
+        for (int t = 0; t < 16; ++t) so[t * kMmaM + m] = v[t];
+        __syncthreads();
+        float* o = reinterpret_cast<float*>(a.out[rhs]) + (int64_t)half * a.N + tile0;
 #pragma unroll
-          for (int t = 0; t < 16; ++t) o[obase + ostride * (i0 + t)] = v[t];
+        for (int k = 0; k < 4; ++k) {
+          const int c = threadIdx.x + k * kMmaThreads;  // float4 chunk: row c / 32, column (c % 32) * 4
+          const int row = c >> 5, col = (c & 31) * 4;
+          *reinterpret_cast<float4*>(o + a.P * (i0 + row) + col) =
+              *reinterpret_cast<const float4*>(so + row * kMmaM + col);
         }
+        __syncthreads();
       } else {
+        __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(base);  // [3 splits][16 rows][128 fibers]
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          __nv_bfloat16 sh, sm, sl;
+          split3(v[t], sh, sm, sl);
+          so[(0 * 16 + t) * kMmaM + m] = sh;
+          so[(1 * 16 + t) * kMmaM + m] = sm;
+          so[(2 * 16 + t) * kMmaM + m] = sl;
+        }
+        __syncthreads();
         __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out[rhs]);
-        __nv_bfloat16 sp[3][16];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) split3(v[t], sp[0][t], sp[1][t], sp[2][t]);
+        for (int k = 0; k < 6; ++k) {
+          const int c = threadIdx.x + k * kMmaThreads;  // 16-byte chunk of 8 fibers
+          const int s = c >> 8, row = (c >> 4) & 15, col = (c & 15) * 8;
+          *reinterpret_cast<uint4*>(o + (int64_t)(s * 2 + half) * a.N + tile0 + a.P * (i0 + row) + col) =
+              *reinterpret_cast<const uint4*>(so + (s * 16 + row) * kMmaM + col);
+        }
+        __syncthreads();
+      }
+    }
+    if (!a.a_mn) {
+      __syncthreads();
+      // 8 outputs per thread and pass; a warp covers two fibers' runs
+      const int cpf = nc / 8;
+      const float* so = reinterpret_cast<const float*>(base);
+      for (int e = threadIdx.x; e < kMmaM * cpf; e += kMmaThreads) {
+        const int f = e / cpf, ch = e - f * cpf;
+        const int64_t q = q0 + f;
+        if (q >= a.Q) continue;
+        const float4 x0 = *reinterpret_cast<const float4*>(so + f * pitch + ch * 8);
+        const float4 x1 = *reinterpret_cast<const float4*>(so + f * pitch + ch * 8 + 4);
+        const int64_t off = (int64_t)n * q + sub * nc + ch * 8;
+        if (a.out_fp32) {
+          float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out[rhs]) + (int64_t)half * a.N + off);
+          d4[0] = x0;
+          d4[1] = x1;
+        } else {
+          const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+          uint32_t w[3][4];
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          __nv_bfloat16* plane = o + (int64_t)(s * 2 + half) * a.N;
-          if (!a.a_mn) {
-            uint32_t w[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              w[k] = static_cast<uint32_t>(__bfloat16_as_ushort(sp[s][2 * k])) |
-                     (static_cast<uint32_t>(__bfloat16_as_ushort(sp[s][2 * k + 1])) << 16);
-            uint4* d4 = reinterpret_cast<uint4*>(plane + obase + i0);
-            d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
-            d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
-          } else {
-#pragma unroll
-            for (int t = 0; t < 16; ++t) plane[obase + ostride * (i0 + t)] = sp[s][t];
+          for (int k = 0; k < 4; ++k) {
+            __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+            split3(x[2 * k], h0, m0, l0);
+            split3(x[2 * k + 1], h1, m1, l1);
+            w[0][k] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+                      (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+            w[1][k] = static_cast<uint32_t>(__bfloat16_as_ushort(m0)) |
+                      (static_cast<uint32_t>(__bfloat16_as_ushort(m1)) << 16);
+            w[2][k] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
+                      (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
           }
+          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out[rhs]);
+#pragma unroll
+          for (int sp = 0; sp < 3; ++sp)
+            *reinterpret_cast<uint4*>(o + (int64_t)(sp * 2 + half) * a.N + off) =
+                make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
         }
       }
     }
@@ -393,54 +430,89 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+static CUtensorMapSwizzle k_major_swizzle() {
+  return kKRowBytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                          : (kKRowBytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
 // A operand map of one rhs for mode geometry (n, P, Q) over a buffer of six
-// BF16 planes of N values each.
+// BF16 planes of N values each, plane 2 s + c = split s of component c.  One
+// box holds a whole pipeline stage of A, the three splits one after another
+// (4 KB apart), so a stage takes one copy instruction:
+//   P == 1 (mode 1, K-major): dims (j, q, c, s), box (K, 128, 1, 3), swizzle
+//     span = K values: [s][128 fibers][K j];
+//   P > 1 (MN-major): dims (p mod 64, j, p / 64, q + Q c, s), box
+//     (64, K, 2, 1, 3), 128-byte swizzle: [s][two 64-fiber halves][K j][64],
+// K = kStageK; positions j >= n of a ragged last stage read as zero.
 cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_out);
   std::memset(m, 0, sizeof(CUtensorMap));
   CUresult r;
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   if (P == 1) {
-    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)Q, 6};
-    const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)N * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kMmaK, (cuuint32_t)kMmaM, 1};
-    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(splits), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)Q, 2, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)n * 2, (cuuint64_t)N * 2, (cuuint64_t)N * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)kStageK, (cuuint32_t)kMmaM, 1, 3};
+    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(splits), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, k_major_swizzle(), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {
-    const cuuint64_t dims[4] = {(cuuint64_t)P, (cuuint64_t)n, (cuuint64_t)Q, 6};
-    const cuuint64_t strides[3] = {(cuuint64_t)P * 2, (cuuint64_t)P * n * 2, (cuuint64_t)N * 2};
-    const cuuint32_t box[4] = {64, (cuuint32_t)kMmaK, 1, 1};
-    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(splits), dims, strides, box, estr,
+    const cuuint64_t dims[5] = {64, (cuuint64_t)n, (cuuint64_t)(P / 64), (cuuint64_t)(2 * Q), 3};
+    const cuuint64_t strides[4] = {(cuuint64_t)P * 2, 128, (cuuint64_t)P * n * 2, (cuuint64_t)N * 4};
+    const cuuint32_t box[5] = {64, (cuuint32_t)kStageK, 2, 1, 3};
+    r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(splits), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// B operand map over three (2n x 2n) BF16 factor splits.
+// B operand map over three (2n x 2n) BF16 factor splits, the K index of a
+// row split as (j, c): dims (j, row, c, s) (the copy engine walks a box in
+// planes of its first two dimensions, so these are the large ones); one box =
+// nc output rows x kStageK positions j of one component, all three splits
+// ([s][nc rows][K]), zero for j >= n.
 cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n) {
   const int nc = n / mma_row_blocks(n);
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_out);
   std::memset(m, 0, sizeof(CUtensorMap));
-  const cuuint64_t dims[3] = {(cuuint64_t)2 * n, (cuuint64_t)2 * n, 3};
-  const cuuint64_t strides[2] = {(cuuint64_t)4 * n, (cuuint64_t)8 * n * n};
-  const cuuint32_t box[3] = {(cuuint32_t)kMmaK, (cuuint32_t)nc, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fsplit), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)2 * n, 2, 3};
+  const cuuint64_t strides[3] = {(cuuint64_t)4 * n, (cuuint64_t)2 * n, (cuuint64_t)8 * n * n};
+  const cuuint32_t box[4] = {(cuuint32_t)kStageK, (cuuint32_t)nc, 1, 3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(fsplit), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, k_major_swizzle(), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-static size_t mma_smem_bytes(int nc) { return (size_t)kMmaStages * mma_stage_bytes(nc) + 1024 + 256; }
+// Pipeline depth: up to kMaxStages stages within kSmemPerCta (two CTAs per
+// SM, so that one's epilogue runs under the other's MMAs), at least two.
+static int mma_stages(int nc) {
+  const int fit = (int)((kSmemPerCta - 1024 - 256) / mma_stage_bytes(nc));
+  return fit < 2 ? 2 : (fit > kMaxStages ? kMaxStages : fit);
+}
+static size_t mma_smem_bytes(int nc) { return (size_t)mma_stages(nc) * mma_stage_bytes(nc) + 1024 + 256; }
+
+constexpr size_t kMaxDynSmem = 227 * 1024;
+
+// Largest shared-memory need over the supported mode lengths (multiples of
+// 16 up to 256), within the per-CTA limit.
+static size_t mma_smem_limit() {
+  size_t m = 0;
+  for (int n = 16; n <= 256; n += 16) {
+    const size_t b = mma_smem_bytes(n / mma_row_blocks(n));
+    if (b <= kMaxDynSmem && b > m) m = b;
+  }
+  return m;
+}
 
 cudaError_t prepare_mma_pass() {
-  return cudaFuncSetAttribute(mma_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mma_smem_bytes(240));
+  return cudaFuncSetAttribute(mma_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mma_smem_limit());
 }
 
 cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
@@ -459,11 +531,16 @@ cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
   a.nc = L.n / a.nsub;
   while (cols < 2 * a.nc) cols *= 2;
   a.tmem_cols = cols;
+  a.stages = mma_stages(a.nc);
   a.status = L.status;
   const CUtensorMap* A0 = reinterpret_cast<const CUtensorMap*>(L.tmA[0]);
   const CUtensorMap* A1 = reinterpret_cast<const CUtensorMap*>(L.tmA[L.nrhs > 1 ? 1 : 0]);
   const CUtensorMap* B0 = reinterpret_cast<const CUtensorMap*>(L.tmB[0]);
   const CUtensorMap* B1 = reinterpret_cast<const CUtensorMap*>(L.tmB[L.nrhs > 1 ? 1 : 0]);
+  if (mma_smem_bytes(a.nc) > mma_smem_limit()) return cudaErrorInvalidValue;
+  // mode 1 stages its FP32 tile [128][nc + 4] in the pipeline buffers
+  if (!a.a_mn && (size_t)kMmaM * (a.nc + 4) * 4 > (size_t)a.stages * mma_stage_bytes(a.nc))
+    return cudaErrorInvalidValue;
   dim3 grid((unsigned)(2 * a.nsub * mtiles), (unsigned)L.nrhs);  // (fiber tile, component, row block)
   mma_mode_kernel<<<grid, kMmaThreads, mma_smem_bytes(a.nc), s>>>(*A0, *A1, *B0, *B1, a);
   return cudaGetLastError();
