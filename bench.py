@@ -329,8 +329,9 @@ def run_neumann256(args):
     mma = [r for r in prof["bf16x3"] if r["name"] == "mma_mode_bf16x3"][0]
     achieved = mma["flops"] / (mma["total_ms"] / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops", 1948.7))
+    traffic = profiled_traffic("mma_mode_bf16x3_ncu_neumann256.md", ["mma_mode.cu", "tc_ptx.cuh", "cgl_internal.cuh"])
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "mma_mode_bf16x3", "launches_profiled": mma["launches"],
+                "traffic": traffic, "kernel": "mma_mode_bf16x3", "launches_profiled": mma["launches"],
                 "avg_launch_ms": mma["total_ms"] / mma["launches"],
                 "flops_counted": "issued: 6 split products x 8 n real flops per point per mode",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
