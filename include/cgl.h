@@ -65,8 +65,9 @@ enum cgl_scheme {
  *   CGL_BF16X3 complex64 state; the mu-mode products run on the tensor cores
  *              with each operand split into three BF16 parts and FP32
  *              accumulation (about FP32 accuracy); pointwise work in FP32.
- *              Finite differences only, every n_mu a multiple of 16 and
- *              <= 256, and n_1 a multiple of 128 when d >= 2. */
+ *              Finite differences only, every n_mu <= 256 (internally the
+ *              factors are zero-padded to a multiple of 16 and the BF16
+ *              planes' first direction to a multiple of 64). */
 enum cgl_precision { CGL_F64 = 0, CGL_F32 = 1, CGL_BF16X3 = 2 };
 
 enum cgl_status {

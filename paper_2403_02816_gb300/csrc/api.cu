@@ -42,6 +42,20 @@ int64_t axis_P(const cgl_plan* p, int axis) {
   return P;
 }
 
+// Tensor-core planes: the faster product with the first direction padded to
+// the plane pitch, and the slower product.
+int64_t mma_axis_P(const cgl_plan* p, int axis) {
+  if (axis == 0) return 1;
+  int64_t P = p->pitch;
+  for (int m = 1; m < axis; ++m) P *= p->n[m];
+  return P;
+}
+int64_t mma_axis_Q(const cgl_plan* p, int axis) {
+  int64_t Q = 1;
+  for (int m = axis + 1; m < p->d; ++m) Q *= p->n[m];
+  return Q;
+}
+
 PassGeom geom(const cgl_plan* p, int axis) {
   PassGeom g{};
   g.d = p->d;
@@ -186,17 +200,28 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
     // split prologue -> d tensor-core mode passes -> plane epilogue
     {
       Timer tm(p, s);
-      cudaError_t e = launch_split_prologue(f.in[0], f.in[1], sw.nin, sw.op, p->splits[0], p->splits[1], sw.nrhs,
-                                            p->N, s);
+      SplitSeg g{};
+      g.in[0] = static_cast<const float2*>(f.in[0]);
+      g.in[1] = static_cast<const float2*>(f.in[1]);
+      g.nin = sw.nin;
+      g.op = sw.op;
+      g.dst[0] = p->splits[0];
+      g.dst[1] = p->splits[1];
+      g.N = p->N;
+      g.n1 = p->n[0];
+      g.pitch = p->pitch;
+      g.Npad = p->Npad;
+      cudaError_t e = launch_split_prologue(g, nullptr, 1, p->N, sw.nrhs, s);
       if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("split prologue: ") + cudaGetErrorString(e));
       tm.done("split_prologue", pro_flops(p, sw.op) * Nd, (sw.nin * 8.0 + sw.nrhs * 12.0) * Nd);
     }
     for (int mu = 0; mu < p->d; ++mu) {
       MmaLaunch L{};
       L.n = (int)p->n[mu];
-      L.P = axis_P(p, mu);
-      L.Q = p->N / (L.P * p->n[mu]);
-      L.N = p->N;
+      L.P = mma_axis_P(p, mu);
+      L.Q = mma_axis_Q(p, mu);
+      L.N = p->Npad;
+      L.pitch = p->pitch;
       L.nrhs = sw.nrhs;
       for (int r = 0; r < 2; ++r) {
         const int rr = r < sw.nrhs ? r : 0;
@@ -219,9 +244,20 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
     }
     {
       Timer tm(p, s);
-      void* ex[3] = {f.extra[0], f.extra[1], f.extra[2]};
-      cudaError_t e = launch_plane_epilogue(p->planes[0], p->planes[1], sw.nrhs, ex, sw.nextra, sw.op, f.out[0],
-                                            f.out[1], sw.nout, p->N, p->status, s);
+      EpiSeg g{};
+      g.y[0] = static_cast<const float*>(p->planes[0]);
+      g.y[1] = static_cast<const float*>(p->planes[1]);
+      for (int x = 0; x < kMaxExtra; ++x) g.ex[x] = static_cast<const float2*>(f.extra[x]);
+      g.nextra = sw.nextra;
+      g.op = sw.op;
+      g.out[0] = static_cast<float2*>(f.out[0]);
+      g.out[1] = static_cast<float2*>(f.out[1]);
+      g.nout = sw.nout;
+      g.N = p->N;
+      g.n1 = p->n[0];
+      g.pitch = p->pitch;
+      g.Npad = p->Npad;
+      cudaError_t e = launch_plane_epilogue(g, nullptr, 1, p->N, sw.nrhs, p->status, s);
       if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("plane epilogue: ") + cudaGetErrorString(e));
       tm.done("plane_epilogue", epi_flops(p, sw.op) * Nd, (sw.nrhs * 8.0 + (sw.nextra + sw.nout) * 8.0) * Nd);
     }
@@ -400,7 +436,7 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
         CUDA_TRY(expm_device(dA, p->cval[c] * p->tau, n, p->fac64[c][mu], dW, norm1(A, n), s));
         if ((st = make_working(p, p->fac64[c][mu], (int64_t)n * n, &p->fac[c][mu], s))) return st;
         if (p->precision == CGL_BF16X3) {
-          if ((st = dev_alloc(p, &p->fsplit[c][mu], 3 * 4 * (size_t)n * n * 2))) return st;
+          if ((st = dev_alloc(p, &p->fsplit[c][mu], mma_factor_bytes(n)))) return st;
           CUDA_TRY(launch_factor_split(p->fac64[c][mu], n, p->fsplit[c][mu], s));
           CUDA_TRY(make_factor_tmap(p->tmB[c][mu], p->fsplit[c][mu], n));
         }
@@ -680,9 +716,7 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   if (precision == CGL_BF16X3) {
     if (periodic) return fail(CGL_EUNSUPPORTED, "BF16x3 applies to the finite-difference mode products only");
     for (int m = 0; m < d; ++m)
-      if (n[m] % 16 != 0 || n[m] > 256)
-        return fail(CGL_EUNSUPPORTED, "BF16x3 needs every n_mu a multiple of 16 and <= 256");
-    if (d >= 2 && n[0] % 128 != 0) return fail(CGL_EUNSUPPORTED, "BF16x3 needs n_1 a multiple of 128 when d >= 2");
+      if (n[m] > 256) return fail(CGL_EUNSUPPORTED, "BF16x3 needs every n_mu <= 256");
   }
 
   cgl_plan* p = new cgl_plan();
@@ -741,14 +775,22 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   if (!st && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) st = fail(CGL_ECUDA, "memset status");
   for (int w = 0; !st && !minimal && w < p->nwork; ++w) st = dev_alloc(p, &p->work[w], p->N * p->elem);
   if (!st && precision == CGL_BF16X3) {
+    // planes with the first direction padded to a multiple of 64, zeroed once:
+    // the padding is never written afterwards (mode passes store rows i < n)
+    p->pitch = mma_pitch(p->n[0]);
+    p->Npad = p->N / p->n[0] * p->pitch;
     const int nr = scheme == CGL_STRANG ? 1 : 2;
     for (int r = 0; !st && r < nr; ++r) {
-      st = dev_alloc(p, &p->splits[r], 12 * (size_t)p->N);
-      if (!st && d > 1) st = dev_alloc(p, &p->splits_alt[r], 12 * (size_t)p->N);
-      if (!st) st = dev_alloc(p, &p->planes[r], 8 * (size_t)p->N);
+      st = dev_alloc(p, &p->splits[r], 12 * (size_t)p->Npad);
+      if (!st && d > 1) st = dev_alloc(p, &p->splits_alt[r], 12 * (size_t)p->Npad);
+      if (!st) st = dev_alloc(p, &p->planes[r], 8 * (size_t)p->Npad);
+      void* bufs[3] = {p->splits[r], p->splits_alt[r], p->planes[r]};
+      const size_t sizes[3] = {12 * (size_t)p->Npad, 12 * (size_t)p->Npad, 8 * (size_t)p->Npad};
+      for (int k = 0; !st && k < 3; ++k)
+        if (bufs[k] && cudaMemsetAsync(bufs[k], 0, sizes[k], s) != cudaSuccess) st = fail(CGL_ECUDA, "memset planes");
       for (int mu = 0; !st && mu < d; ++mu) {
-        const int64_t P = axis_P(p, mu), Q = p->N / (P * p->n[mu]);
-        e = make_state_tmap(p->tmA[mu][r], (mu & 1) ? p->splits_alt[r] : p->splits[r], (int)p->n[mu], P, Q, p->N);
+        e = make_state_tmap(p->tmA[mu][r], (mu & 1) ? p->splits_alt[r] : p->splits[r], (int)p->n[mu],
+                            mma_axis_P(p, mu), mma_axis_Q(p, mu), p->Npad, p->pitch);
         if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("tensor map: ") + cudaGetErrorString(e));
       }
     }

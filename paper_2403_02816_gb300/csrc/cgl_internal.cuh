@@ -406,8 +406,9 @@ cudaError_t convert_f64_to_f32(const double2* src, float2* dst, int64_t count, c
 
 // mma_mode.cu: BF16x3 mu-mode product on tcgen05 (complex64 state).
 struct MmaLaunch {
-  int n;              // mode length
-  int64_t P, Q, N;    // faster / slower products, field size
+  int n;              // mode length n_mu (<= 256)
+  int64_t P, Q, N;    // faster (first direction padded) / slower products, plane length
+  int64_t pitch;      // mode 1: distance between fibers in the planes
   int nrhs;
   const void* tmA[kMaxRhs];  // CUtensorMap (128 bytes) of each rhs's BF16x3 planes
   const void* tmB[kMaxRhs];  // CUtensorMap of each rhs's factor splits
@@ -415,19 +416,73 @@ struct MmaLaunch {
   void* out[kMaxRhs];
   int* status;
 };
+struct MmaPassArgs {
+  int n;             // mode length n_mu (<= 256)
+  int np;            // n rounded up to a multiple of 16: size of the padded factor
+  int64_t P, Q;      // products of the faster (first one padded) / slower sizes
+  int64_t pitch;     // mode 1: distance between fibers in the planes (>= np)
+  int64_t per_q;     // MN-major: fiber tiles per slab, ceil(P / 128)
+  int a_mn;          // 1: A is MN-major (P > 1, P % 64 == 0); 0: K-major (mode 1)
+  int out_fp32;      // 1: FP32 planes (re, im); 0: BF16x3 planes (6)
+  void* out[kMaxRhs];
+  int64_t N;         // plane length (padded field size)
+  int nc;            // output rows of one component per CTA (multiple of 16, <= 128 when np > 128)
+  int nsub;          // row blocks per component: ceil(np / nc)
+  int tmem_cols;     // power of two >= 2 nc
+  int stages;        // pipeline depth
+  int* status;
+};
 constexpr size_t kTensorMapBytes = 128;
-// Output rows of one component are split over this many CTAs (n >= 64 and a
-// multiple of 32: two blocks of n/2 rows, so two CTAs fit on an SM).
-inline int mma_row_blocks(int n) { return (n >= 64 && n % 32 == 0) ? 2 : 1; }
-cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N);
+// Padded sizes of the tensor-core path: factors to a multiple of 16, the
+// planes' first direction to a multiple of 64.
+inline int mma_pad16(int n) { return (n + 15) / 16 * 16; }
+inline int64_t mma_pitch(int64_t n1) { return (n1 + 63) / 64 * 64; }
+// Output rows of one component per CTA: half of np when np >= 64 is a
+// multiple of 32, else np up to 128, else np / 2 rounded up to 16 (two
+// CTAs per SM in every case but np <= 128 odd multiples of 16).
+inline int mma_rows_per_cta(int np) {
+  if (np >= 64 && np % 32 == 0) return np / 2;
+  if (np <= 128) return np;
+  return (np / 2 + 15) / 16 * 16;
+}
+cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N,
+                            int64_t pitch);
 cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n);
+size_t mma_factor_bytes(int n);
+size_t mma_smem_bytes(int nc);
 cudaError_t prepare_mma_pass();
+// Fills the pass arguments; returns the CTAs per rhs, or -1 for an
+// unsupported geometry.
+int64_t mma_build_args(const MmaLaunch& L, MmaPassArgs* out);
 cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s);
-cudaError_t launch_split_prologue(const void* in0, const void* in1, int nin, const OpArgs& op, void* s0, void* s1,
-                                  int nrhs, int64_t N, cudaStream_t s);
-cudaError_t launch_plane_epilogue(const void* y0, const void* y1, int nrhs, void* const* extra, int nextra,
-                                  const OpArgs& op, void* o0, void* o1, int nout, int64_t N, int* status,
+// One launch over a group of passes: device arrays of MmaPassArgs, of four
+// CUtensorMaps per pass (A rhs 0 / 1, B rhs 0 / 1) and of npass + 1 CTA
+// prefix sums; smem = the largest mma_smem_bytes(nc) of the group.
+cudaError_t launch_mma_group(const void* passes, const void* maps, const int* start, int npass, int64_t ctas,
+                             int nrhs, size_t smem, cudaStream_t s);
+// Pointwise stages around the tensor-core passes, one field per segment
+// (planes: first direction padded to `pitch`, Npad values per plane).
+struct SplitSeg {
+  const float2* in[2];
+  int nin;
+  OpArgs op;
+  void* dst[2];        // six BF16 planes per rhs
+  int64_t N, n1, pitch, Npad;
+};
+struct EpiSeg {
+  const float* y[2];   // FP32 planes (re, im) per rhs
+  const float2* ex[kMaxExtra];
+  int nextra;
+  OpArgs op;
+  float2* out[2];
+  int nout;
+  int64_t N, n1, pitch, Npad;
+};
+// segs == nullptr: the single segment `one`; else nseg device segments.
+cudaError_t launch_split_prologue(const SplitSeg& one, const SplitSeg* segs, int nseg, int64_t max_n, int nrhs,
                                   cudaStream_t s);
+cudaError_t launch_plane_epilogue(const EpiSeg& one, const EpiSeg* segs, int nseg, int64_t max_n, int nrhs,
+                                  int* status, cudaStream_t s);
 cudaError_t launch_factor_split(const double2* F, int n, void* out, cudaStream_t s);
 
 // norms.cu

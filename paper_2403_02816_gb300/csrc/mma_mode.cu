@@ -66,18 +66,13 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
 
 // ------------------------------------------------------------------ the GEMM pass
 
-struct MmaPassArgs {
-  int n;             // mode length (multiple of 16, <= 256)
-  int64_t P, Q;      // products of the faster / slower sizes
-  int a_mn;          // 1: A is MN-major (P > 1, P % 128 == 0); 0: K-major (mode 1)
-  int out_fp32;      // 1: FP32 planes (re, im); 0: BF16x3 planes (6)
-  void* out[kMaxRhs];
-  int64_t N;         // plane length (field size)
-  int nc;            // outputs (rows i) of one component per CTA: n or n/2
-  int nsub;          // n / nc
-  int tmem_cols;     // power of two >= 2 nc
-  int stages;        // pipeline depth
-  int* status;
+// A group of passes in one launch (instances of a batch): CTA b belongs to
+// the pass k with start[k] <= b < start[k + 1].
+struct MmaTable {
+  const MmaPassArgs* passes;  // device, one per pass
+  const CUtensorMap* maps;    // device, four per pass: A of rhs 0 / 1, B of rhs 0 / 1
+  const int* start;           // device, npass + 1 prefix sums of the passes' CTA counts
+  int npass;
 };
 
 // One pipeline stage: three A splits (128 fibers x kStageK) and three B
@@ -86,23 +81,41 @@ static __host__ __device__ constexpr uint32_t mma_stage_bytes(int nc) {
   return 3u * (kMmaM * kStageK * 2u) + 3u * (static_cast<uint32_t>(nc) * kStageK * 2u);
 }
 
-// CTA (tile, half): 128 fibers x the n outputs of component c' = half.
-// TMEM columns [0, n): the (h, h) product; [n, 2n): the five correction
-// products.  Keeping the large term in its own accumulator keeps the
-// accumulator rounding of the many small MMAs relative to the small terms.
+// CTA (tile, half, sub): 128 fibers x output rows [sub nc, (sub + 1) nc) of
+// component c' = half.  TMEM columns [0, nc): the (h, h) product; [nc, 2nc):
+// the five correction products.  Keeping the large term in its own
+// accumulator keeps the accumulator rounding of the many small MMAs relative
+// to the small terms.  Rows i >= n (padding, or the other component's rows
+// when nsub nc > np) are computed and discarded.
+template <bool kTable>
 __global__ void __launch_bounds__(kMmaThreads, 1)
     mma_mode_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                     const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
-                    const MmaPassArgs a) {
+                    const MmaPassArgs args, const MmaTable table) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int n = a.n;
   const int rhs = blockIdx.y;
+  int64_t bx = blockIdx.x;
   const CUtensorMap* tmA = rhs ? &tmA1 : &tmA0;
   const CUtensorMap* tmB = rhs ? &tmB1 : &tmB0;
-  // K = 2n runs over (component c, position j); a stage holds kStageK values
-  // of j of one component (the copies fill j >= n with zeros)
-  const int nkc = (n + kStageK - 1) / kStageK;
+  int pass = 0;
+  if constexpr (kTable) {
+    int lo = 0, hi = table.npass - 1;  // last pass whose first CTA is <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (table.start[mid] <= bx) lo = mid;
+      else hi = mid - 1;
+    }
+    pass = lo;
+    bx -= table.start[pass];
+    tmA = &table.maps[4 * pass + rhs];
+    tmB = &table.maps[4 * pass + 2 + rhs];
+  }
+  const MmaPassArgs a = kTable ? table.passes[pass] : args;
+  const int n = a.n, np = a.np;
+  // K = 2 np runs over (component c, position j); a stage holds kStageK
+  // values of j of one component (the copies fill j >= n with zeros)
+  const int nkc = (np + kStageK - 1) / kStageK;
   const int nk = 2 * nkc;
   const int S = a.stages;
   const uint32_t a_bytes = kMmaM * kStageK * 2;
@@ -120,15 +133,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   // of the tile's A data is served from L2
   // CTA (tile, component, row block); the CTAs of one fiber tile are adjacent
   // blocks, so the repeated reads of the tile's A data are served from L2
-  const int64_t tile = blockIdx.x / (2 * a.nsub);
-  const int part = blockIdx.x % (2 * a.nsub);
+  const int64_t tile = bx / (2 * a.nsub);
+  const int part = (int)(bx % (2 * a.nsub));
   const int half = part / a.nsub;
   const int sub = part % a.nsub;
   int64_t q0 = 0, p0 = 0;
   if (a.a_mn) {
-    const int64_t per_q = a.P / kMmaM;
-    q0 = tile / per_q;
-    p0 = (tile - q0 * per_q) * kMmaM;
+    q0 = tile / a.per_q;
+    p0 = (tile - q0 * a.per_q) * kMmaM;  // a last tile of 64 fibers reads zeros for its second half
   } else {
     q0 = tile * kMmaM;
   }
@@ -157,7 +169,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     int slot = 0, c = 0, j0 = 0, loaded = 0;
     uint32_t phase = 0;
     bool ok = true;
-    const int rowB = half * n + sub * nc, pq = (int)(p0 / 64);
+    const int rowB = half * np + sub * nc, pq = (int)(p0 / 64);
     for (int kb = 0; kb < nk; ++kb) {
       // the slot's previous stage (kb - S) must have been consumed
       if (kb >= S && !mbar_wait(smem_u32(&empty[slot]), phase ^ 1u)) { ok = false; break; }
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       loaded = kb + 1;
       if (++slot == S) { slot = 0; phase ^= 1u; }
       j0 += kStageK;
-      if (j0 >= n) { j0 = 0; ++c; }
+      if (j0 >= np) { j0 = 0; ++c; }
     }
     counters[0] = loaded;
     if (!ok) *abort_flag = 1;
@@ -201,7 +213,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       consumed = kb + 1;
       tc_fence_after();
       const uint32_t so = slot * (stage_bytes / 16);
-      const int ksteps = min(kStageK, n - j0) / kMmaK;
+      const int ksteps = min(kStageK, np - j0) / kMmaK;
       for (int ks = 0; ks < ksteps; ++ks) {
 #pragma unroll
         for (int pr = 0; pr < 6; ++pr) {
@@ -216,7 +228,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       committed = kb + 1;
       if (++slot == S) { slot = 0; phase ^= 1u; }
       j0 += kStageK;
-      if (j0 >= n) j0 = 0;
+      if (j0 >= np) j0 = 0;
     }
     counters[1] = consumed;
     counters[2] = committed;
@@ -250,6 +262,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     // FP32 tile [128 fibers][nc] (pitch nc + 4 floats: conflict-free 16-byte
     // stores) and write each fiber's nc outputs as one contiguous run.
     const int64_t tile0 = p0 + a.P * (int64_t)n * q0;
+    const int64_t pvalid = a.P - p0;  // fibers of this tile inside the slab: 128 or 64
     const int pitch = nc + 4;
     for (int c0 = 0; c0 < nc; c0 += 16) {
       const int i0 = sub * nc + c0;  // first output row of this chunk
@@ -275,8 +288,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
         for (int k = 0; k < 4; ++k) {
           const int c = threadIdx.x + k * kMmaThreads;  // float4 chunk: row c / 32, column (c % 32) * 4
           const int row = c >> 5, col = (c & 31) * 4;
-          *reinterpret_cast<float4*>(o + a.P * (i0 + row) + col) =
-              *reinterpret_cast<const float4*>(so + row * kMmaM + col);
+          if (i0 + row < n && col < pvalid)
+            *reinterpret_cast<float4*>(o + a.P * (i0 + row) + col) =
+                *reinterpret_cast<const float4*>(so + row * kMmaM + col);
         }
         __syncthreads();
       } else {
@@ -295,8 +309,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
         for (int k = 0; k < 6; ++k) {
           const int c = threadIdx.x + k * kMmaThreads;  // 16-byte chunk of 8 fibers
           const int s = c >> 8, row = (c >> 4) & 15, col = (c & 15) * 8;
-          *reinterpret_cast<uint4*>(o + (int64_t)(s * 2 + half) * a.N + tile0 + a.P * (i0 + row) + col) =
-              *reinterpret_cast<const uint4*>(so + (s * 16 + row) * kMmaM + col);
+          if (i0 + row < n && col < pvalid)
+            *reinterpret_cast<uint4*>(o + (int64_t)(s * 2 + half) * a.N + tile0 + a.P * (i0 + row) + col) =
+                *reinterpret_cast<const uint4*>(so + (s * 16 + row) * kMmaM + col);
         }
         __syncthreads();
       }
@@ -309,10 +324,13 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       for (int e = threadIdx.x; e < kMmaM * cpf; e += kMmaThreads) {
         const int f = e / cpf, ch = e - f * cpf;
         const int64_t q = q0 + f;
-        if (q >= a.Q) continue;
+        // rows i >= n are not stored (a chunk that starts below n ends below
+        // np <= the fiber pitch, its rows past n being zero rows of the padded
+        // factor)
+        if (q >= a.Q || sub * nc + ch * 8 >= n) continue;
         const float4 x0 = *reinterpret_cast<const float4*>(so + f * pitch + ch * 8);
         const float4 x1 = *reinterpret_cast<const float4*>(so + f * pitch + ch * 8 + 4);
-        const int64_t off = (int64_t)n * q + sub * nc + ch * 8;
+        const int64_t off = a.pitch * q + sub * nc + ch * 8;
         if (a.out_fp32) {
           float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out[rhs]) + (int64_t)half * a.N + off);
           d4[0] = x0;
@@ -351,59 +369,74 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
 
 // ------------------------------------------------------------------ pointwise stages
 
-// Start of a sweep: prologue on complex64 inputs, BF16x3 planes of each rhs.
-__global__ void split_prologue_kernel(const float2* in0, const float2* in1, int nin, OpArgs op,
-                                      __nv_bfloat16* s0, __nv_bfloat16* s1, int nrhs, int64_t N) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+// Planes are laid out with the first direction padded to a pitch (a multiple
+// of 64): point i of the field (n_1 fastest) sits at
+//   plane_index(i) = i + (pitch - n_1) floor(i / n_1).
+__device__ __forceinline__ int64_t plane_index(int64_t i, int64_t n1, int64_t pitch) {
+  return pitch == n1 ? i : i + (pitch - n1) * (i / n1);
+}
+
+// Start of a sweep: prologue on complex64 inputs, BF16x3 planes of each rhs
+// (one field per segment; blockIdx.y selects the segment in table mode).
+template <bool kTable>
+__global__ void split_prologue_kernel(const SplitSeg one, const SplitSeg* __restrict__ segs, int nrhs) {
+  const SplitSeg& g = kTable ? segs[blockIdx.y] : one;
+  const int64_t P = g.Npad;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * blockDim.x) {
     float2 in[2], z[2];
-    in[0] = in0[i];
-    in[1] = nin > 1 ? in1[i] : in[0];
-    apply_prologue<float, float2>(op, in, z);
-    __nv_bfloat16* dst[2] = {s0, s1};
+    in[0] = g.in[0][i];
+    in[1] = g.nin > 1 ? g.in[1][i] : in[0];
+    apply_prologue<float, float2>(g.op, in, z);
+    const int64_t ip = plane_index(i, g.n1, g.pitch);
     for (int r = 0; r < nrhs; ++r) {
+      __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(g.dst[r]);
       __nv_bfloat16 h, m, l;
       split3(z[r].x, h, m, l);
-      dst[r][0 * N + i] = h;
-      dst[r][2 * N + i] = m;
-      dst[r][4 * N + i] = l;
+      d[0 * P + ip] = h;
+      d[2 * P + ip] = m;
+      d[4 * P + ip] = l;
       split3(z[r].y, h, m, l);
-      dst[r][1 * N + i] = h;
-      dst[r][3 * N + i] = m;
-      dst[r][5 * N + i] = l;
+      d[1 * P + ip] = h;
+      d[3 * P + ip] = m;
+      d[5 * P + ip] = l;
     }
   }
 }
 
 // End of a sweep: FP32 planes of each rhs + extras -> epilogue -> complex64.
-__global__ void plane_epilogue_kernel(const float* y0, const float* y1, int nrhs, const float2* e0,
-                                      const float2* e1, const float2* e2, int nextra, OpArgs op, float2* o0,
-                                      float2* o1, int nout, int64_t N, int* status) {
+template <bool kTable>
+__global__ void plane_epilogue_kernel(const EpiSeg one, const EpiSeg* __restrict__ segs, int nrhs, int* status) {
+  const EpiSeg& g = kTable ? segs[blockIdx.y] : one;
+  const int64_t P = g.Npad;
   bool bad = false;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    float2 y[2], ex[3], o[2];
-    y[0] = make_float2(y0[i], y0[N + i]);
-    y[1] = nrhs > 1 ? make_float2(y1[i], y1[N + i]) : y[0];
-    if (nextra > 0) ex[0] = e0[i];
-    if (nextra > 1) ex[1] = e1[i];
-    if (nextra > 2) ex[2] = e2[i];
-    const int no = apply_epilogue<float, float2>(op, y, ex, o);
-    if (no > 0 && nout > 0) { o0[i] = o[0]; bad |= !finite2(o[0]); }
-    if (no > 1 && nout > 1) { o1[i] = o[1]; bad |= !finite2(o[1]); }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ip = plane_index(i, g.n1, g.pitch);
+    float2 y[2], ex[kMaxExtra], o[2];
+    y[0] = make_float2(g.y[0][ip], g.y[0][P + ip]);
+    y[1] = nrhs > 1 ? make_float2(g.y[1][ip], g.y[1][P + ip]) : y[0];
+    for (int x = 0; x < g.nextra; ++x) ex[x] = g.ex[x][i];
+    const int no = apply_epilogue<float, float2>(g.op, y, ex, o);
+    if (no > 0 && g.nout > 0) { g.out[0][i] = o[0]; bad |= !finite2(o[0]); }
+    if (no > 1 && g.nout > 1) { g.out[1][i] = o[1]; bad |= !finite2(o[1]); }
   }
   if (bad && status) atomicOr(status, 1);
 }
 
 // Real form of an FP64 factor F (n x n, column-major), split in three BF16
-// matrices: out[s][row (c', i)][col (c, j)], K = col contiguous.
-__global__ void factor_split_kernel(const double2* F, int n, __nv_bfloat16* out) {
-  const int64_t total = 4ll * n * n;
+// matrices and zero-padded to np = n rounded up to 16:
+// out[s][row (c', i)][col (c, j)], rows and columns c * np + (i or j), K =
+// col contiguous; entries with i >= n or j >= n are zero.
+__global__ void factor_split_kernel(const double2* F, int n, int np, __nv_bfloat16* out) {
+  const int64_t total = 4ll * np * np;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int row = (int)(e / (2 * n)), col = (int)(e % (2 * n));
-    const int cp = row / n, i = row % n, c = col / n, j = col % n;
-    const double2 f = F[i + (int64_t)j * n];
-    double v;
-    if (cp == 0) v = (c == 0) ? f.x : -f.y;
-    else v = (c == 0) ? f.y : f.x;
+    const int row = (int)(e / (2 * np)), col = (int)(e % (2 * np));
+    const int cp = row / np, i = row % np, c = col / np, j = col % np;
+    double v = 0;
+    if (i < n && j < n) {
+      const double2 f = F[i + (int64_t)j * n];
+      if (cp == 0) v = (c == 0) ? f.x : -f.y;
+      else v = (c == 0) ? f.y : f.x;
+    }
     const __nv_bfloat16 h = __double2bfloat16(v);
     const double r1 = v - (double)__bfloat162float(h);
     const __nv_bfloat16 m = __double2bfloat16(r1);
@@ -437,23 +470,25 @@ static CUtensorMapSwizzle k_major_swizzle() {
 
 // A operand map of one rhs for mode geometry (n, P, Q) over a buffer of six
 // BF16 planes of N values each, plane 2 s + c = split s of component c.  One
-// box holds a whole pipeline stage of A, the three splits one after another
-// (4 KB apart), so a stage takes one copy instruction:
-//   P == 1 (mode 1, K-major): dims (j, q, c, s), box (K, 128, 1, 3), swizzle
-//     span = K values: [s][128 fibers][K j];
-//   P > 1 (MN-major): dims (p mod 64, j, p / 64, q + Q c, s), box
-//     (64, K, 2, 1, 3), 128-byte swizzle: [s][two 64-fiber halves][K j][64],
-// K = kStageK; positions j >= n of a ragged last stage read as zero.
-cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N) {
+// box holds a whole pipeline stage of A, the three splits one after another,
+// so a stage takes one copy instruction:
+//   P == 1 (mode 1, K-major): dims (j, q, c, s), fibers `pitch` apart, box
+//     (K, 128, 1, 3), swizzle span = K values: [s][128 fibers][K j];
+//   P > 1 (MN-major, P % 64 == 0): dims (p mod 64, j, p / 64, q + Q c, s),
+//     box (64, K, 2, 1, 3), 128-byte swizzle: [s][two 64-fiber halves][K j][64],
+// K = kStageK; positions j >= n and fiber groups p >= P read as zero.
+cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N,
+                            int64_t pitch) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
+  if ((P > 1 && P % 64 != 0) || (P == 1 && (pitch < n || pitch % 8 != 0))) return cudaErrorInvalidValue;
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_out);
   std::memset(m, 0, sizeof(CUtensorMap));
   CUresult r;
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   if (P == 1) {
     const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)Q, 2, 3};
-    const cuuint64_t strides[3] = {(cuuint64_t)n * 2, (cuuint64_t)N * 2, (cuuint64_t)N * 4};
+    const cuuint64_t strides[3] = {(cuuint64_t)pitch * 2, (cuuint64_t)N * 2, (cuuint64_t)N * 4};
     const cuuint32_t box[4] = {(cuuint32_t)kStageK, (cuuint32_t)kMmaM, 1, 3};
     r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(splits), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, k_major_swizzle(), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -469,19 +504,19 @@ cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// B operand map over three (2n x 2n) BF16 factor splits, the K index of a
-// row split as (j, c): dims (j, row, c, s) (the copy engine walks a box in
-// planes of its first two dimensions, so these are the large ones); one box =
-// nc output rows x kStageK positions j of one component, all three splits
-// ([s][nc rows][K]), zero for j >= n.
+// B operand map over three padded (2np x 2np) BF16 factor splits, the K index
+// of a row split as (j, c): dims (j, row, c, s) (the copy engine walks a box
+// in planes of its first two dimensions, so these are the large ones); one
+// box = nc output rows x kStageK positions j of one component, all three
+// splits ([s][nc rows][K]); rows past 2np read as zero.
 cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n) {
-  const int nc = n / mma_row_blocks(n);
+  const int np = mma_pad16(n), nc = mma_rows_per_cta(np);
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_out);
   std::memset(m, 0, sizeof(CUtensorMap));
-  const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)2 * n, 2, 3};
-  const cuuint64_t strides[3] = {(cuuint64_t)4 * n, (cuuint64_t)2 * n, (cuuint64_t)8 * n * n};
+  const cuuint64_t dims[4] = {(cuuint64_t)np, (cuuint64_t)2 * np, 2, 3};
+  const cuuint64_t strides[3] = {(cuuint64_t)4 * np, (cuuint64_t)2 * np, (cuuint64_t)8 * np * np};
   const cuuint32_t box[4] = {(cuuint32_t)kStageK, (cuuint32_t)nc, 1, 3};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(fsplit), dims, strides, box, estr,
@@ -490,84 +525,114 @@ cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+size_t mma_factor_bytes(int n) {
+  const size_t np = mma_pad16(n);
+  return 3 * 4 * np * np * 2;
+}
+
 // Pipeline depth: up to kMaxStages stages within kSmemPerCta (two CTAs per
 // SM, so that one's epilogue runs under the other's MMAs), at least two.
 static int mma_stages(int nc) {
   const int fit = (int)((kSmemPerCta - 1024 - 256) / mma_stage_bytes(nc));
   return fit < 2 ? 2 : (fit > kMaxStages ? kMaxStages : fit);
 }
-static size_t mma_smem_bytes(int nc) { return (size_t)mma_stages(nc) * mma_stage_bytes(nc) + 1024 + 256; }
+size_t mma_smem_bytes(int nc) { return (size_t)mma_stages(nc) * mma_stage_bytes(nc) + 1024 + 256; }
 
 constexpr size_t kMaxDynSmem = 227 * 1024;
 
-// Largest shared-memory need over the supported mode lengths (multiples of
-// 16 up to 256), within the per-CTA limit.
+// Largest shared-memory need over the supported mode lengths (up to 256),
+// within the per-CTA limit.
 static size_t mma_smem_limit() {
   size_t m = 0;
-  for (int n = 16; n <= 256; n += 16) {
-    const size_t b = mma_smem_bytes(n / mma_row_blocks(n));
+  for (int np = 16; np <= 256; np += 16) {
+    const size_t b = mma_smem_bytes(mma_rows_per_cta(np));
     if (b <= kMaxDynSmem && b > m) m = b;
   }
   return m;
 }
 
 cudaError_t prepare_mma_pass() {
-  return cudaFuncSetAttribute(mma_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mma_smem_limit());
+  const int lim = (int)mma_smem_limit();
+  cudaError_t e = cudaFuncSetAttribute(mma_mode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mma_mode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e;
 }
 
-cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
+int64_t mma_build_args(const MmaLaunch& L, MmaPassArgs* out) {
   MmaPassArgs a{};
   a.n = L.n;
+  a.np = mma_pad16(L.n);
   a.P = L.P;
   a.Q = L.Q;
+  a.pitch = L.pitch;
+  a.per_q = (L.P + kMmaM - 1) / kMmaM;
   a.a_mn = L.P > 1 ? 1 : 0;
   a.out_fp32 = L.out_fp32;
   a.out[0] = L.out[0];
   a.out[1] = L.out[1];
   a.N = L.N;
-  const int64_t mtiles = L.P > 1 ? (L.P / kMmaM) * L.Q : (L.Q + kMmaM - 1) / kMmaM;
+  const int64_t mtiles = a.a_mn ? a.per_q * L.Q : (L.Q + kMmaM - 1) / kMmaM;
+  a.nc = mma_rows_per_cta(a.np);
+  a.nsub = (a.np + a.nc - 1) / a.nc;
   int cols = 32;
-  a.nsub = mma_row_blocks(L.n);
-  a.nc = L.n / a.nsub;
   while (cols < 2 * a.nc) cols *= 2;
   a.tmem_cols = cols;
   a.stages = mma_stages(a.nc);
   a.status = L.status;
+  *out = a;
+  if (L.n < 1 || L.n > 256 || (a.a_mn && L.P % 64 != 0) || (!a.a_mn && L.pitch < a.np)) return -1;
+  if (mma_smem_bytes(a.nc) > mma_smem_limit()) return -1;
+  // mode 1 stages its FP32 tile [128][nc + 4] in the pipeline buffers
+  if (!a.a_mn && (size_t)kMmaM * (a.nc + 4) * 4 > (size_t)a.stages * mma_stage_bytes(a.nc)) return -1;
+  return 2 * a.nsub * mtiles;  // CTAs per rhs: (fiber tile, component, row block)
+}
+
+cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
+  MmaPassArgs a;
+  const int64_t ctas = mma_build_args(L, &a);
+  if (ctas < 0) return cudaErrorInvalidValue;
   const CUtensorMap* A0 = reinterpret_cast<const CUtensorMap*>(L.tmA[0]);
   const CUtensorMap* A1 = reinterpret_cast<const CUtensorMap*>(L.tmA[L.nrhs > 1 ? 1 : 0]);
   const CUtensorMap* B0 = reinterpret_cast<const CUtensorMap*>(L.tmB[0]);
   const CUtensorMap* B1 = reinterpret_cast<const CUtensorMap*>(L.tmB[L.nrhs > 1 ? 1 : 0]);
-  if (mma_smem_bytes(a.nc) > mma_smem_limit()) return cudaErrorInvalidValue;
-  // mode 1 stages its FP32 tile [128][nc + 4] in the pipeline buffers
-  if (!a.a_mn && (size_t)kMmaM * (a.nc + 4) * 4 > (size_t)a.stages * mma_stage_bytes(a.nc))
-    return cudaErrorInvalidValue;
-  dim3 grid((unsigned)(2 * a.nsub * mtiles), (unsigned)L.nrhs);  // (fiber tile, component, row block)
-  mma_mode_kernel<<<grid, kMmaThreads, mma_smem_bytes(a.nc), s>>>(*A0, *A1, *B0, *B1, a);
+  dim3 grid((unsigned)ctas, (unsigned)L.nrhs);
+  mma_mode_kernel<false><<<grid, kMmaThreads, mma_smem_bytes(a.nc), s>>>(*A0, *A1, *B0, *B1, a, MmaTable{});
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_prologue(const void* in0, const void* in1, int nin, const OpArgs& op, void* s0, void* s1,
-                                  int nrhs, int64_t N, cudaStream_t s) {
-  const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
-  split_prologue_kernel<<<blocks, 256, 0, s>>>((const float2*)in0, (const float2*)in1, nin, op,
-                                               (__nv_bfloat16*)s0, (__nv_bfloat16*)s1, nrhs, N);
+cudaError_t launch_mma_group(const void* passes, const void* maps, const int* start, int npass, int64_t ctas,
+                             int nrhs, size_t smem, cudaStream_t s) {
+  if (smem > mma_smem_limit() || npass < 1 || ctas < 1) return cudaErrorInvalidValue;
+  MmaTable t{static_cast<const MmaPassArgs*>(passes), static_cast<const CUtensorMap*>(maps), start, npass};
+  CUtensorMap dummy;
+  std::memset(&dummy, 0, sizeof(dummy));
+  dim3 grid((unsigned)ctas, (unsigned)nrhs);
+  mma_mode_kernel<true><<<grid, kMmaThreads, smem, s>>>(dummy, dummy, dummy, dummy, MmaPassArgs{}, t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_plane_epilogue(const void* y0, const void* y1, int nrhs, void* const* extra, int nextra,
-                                  const OpArgs& op, void* o0, void* o1, int nout, int64_t N, int* status,
+cudaError_t launch_split_prologue(const SplitSeg& one, const SplitSeg* segs, int nseg, int64_t max_n, int nrhs,
                                   cudaStream_t s) {
-  const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
-  plane_epilogue_kernel<<<blocks, 256, 0, s>>>((const float*)y0, (const float*)y1, nrhs, (const float2*)extra[0],
-                                               (const float2*)extra[1], (const float2*)extra[2], nextra, op,
-                                               (float2*)o0, (float2*)o1, nout, N, status);
+  const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((max_n + 255) / 256, segs ? 64 : 152 * 16));
+  if (segs) split_prologue_kernel<true><<<dim3(bx, (unsigned)nseg), 256, 0, s>>>(one, segs, nrhs);
+  else split_prologue_kernel<false><<<bx, 256, 0, s>>>(one, nullptr, nrhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_epilogue(const EpiSeg& one, const EpiSeg* segs, int nseg, int64_t max_n, int nrhs,
+                                  int* status, cudaStream_t s) {
+  const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((max_n + 255) / 256, segs ? 64 : 152 * 16));
+  if (segs) plane_epilogue_kernel<true><<<dim3(bx, (unsigned)nseg), 256, 0, s>>>(one, segs, nrhs, status);
+  else plane_epilogue_kernel<false><<<bx, 256, 0, s>>>(one, nullptr, nrhs, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_factor_split(const double2* F, int n, void* out, cudaStream_t s) {
-  const int64_t total = 4ll * n * n;
+  const int np = mma_pad16(n);
+  const int64_t total = 4ll * np * np;
   factor_split_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(
-      F, n, (__nv_bfloat16*)out);
+      F, n, np, (__nv_bfloat16*)out);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@ struct cgl_plan {
   void* splits[2] = {nullptr, nullptr};
   void* splits_alt[2] = {nullptr, nullptr};  // second set: mode passes alternate, none writes over its input
   void* planes[2] = {nullptr, nullptr};
+  int64_t pitch = 0, Npad = 0;  // planes: first direction padded to `pitch`, Npad values per plane
   void* fsplit[2][3] = {{nullptr}};
   alignas(64) unsigned char tmA[3][2][cgl::kTensorMapBytes];
   alignas(64) unsigned char tmB[2][3][cgl::kTensorMapBytes];
@@ -91,6 +92,8 @@ struct cgl_plan {
 namespace cgl {
 
 int64_t axis_P(const cgl_plan* p, int axis);
+int64_t mma_axis_P(const cgl_plan* p, int axis);
+int64_t mma_axis_Q(const cgl_plan* p, int axis);
 PassGeom geom(const cgl_plan* p, int axis);
 int dev_alloc(cgl_plan* p, void** ptr, size_t bytes);
 cudaError_t prepare_kernels(int dev);

@@ -61,7 +61,7 @@ def create(**kw):
     (dict(n=[8, 2048]), nat.CGL_EUNSUPPORTED),
     (dict(scheme=8), nat.CGL_EINVAL),
     (dict(bc=[2, 2], precision=nat.CGL_BF16X3), nat.CGL_EUNSUPPORTED),
-    (dict(n=[24, 128], precision=nat.CGL_BF16X3), nat.CGL_EUNSUPPORTED),
+    (dict(n=[24, 300], precision=nat.CGL_BF16X3), nat.CGL_EUNSUPPORTED),
 ])
 def test_invalid_arguments_are_rejected_before_any_cuda_call(lib, kw, status):
     st, h = create(**kw)

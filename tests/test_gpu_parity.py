@@ -114,13 +114,18 @@ def test_linear_flow(n, bc, prec):
 
 # ------------------------------------------------------------ tensor cores (BF16x3)
 
-# shapes the tcgen05 path takes: n_mu multiple of 16 and <= 256, n_1 a
-# multiple of 128 for d >= 2; several 128-fiber tiles and a ragged last tile
-# of mode-1 fibers (Q not a multiple of 128) included, and row blocks of
-# 16 (n = 208), 80 (n = 240) and 128 (n = 256) output rows
+# the tcgen05 path takes any n_mu <= 256: factors zero-padded to a multiple
+# of 16, planes' first direction to a multiple of 64.  Cases: several
+# 128-fiber tiles and ragged last tiles of mode-1 fibers (Q not a multiple of
+# 128) and of strided fibers (P an odd multiple of 64); row blocks of 64, 80,
+# 112, 128 rows and whole-np blocks; np > 128 not a multiple of 32 (two
+# blocks of 128 rows covering past np: n = 230, 240); n not a multiple of 16
+# in every mode position.
 MMA_SHAPES = [((16,), (0,)), ((48,), (1,)), ((256,), (0,)), ((128, 16), (0, 1)), ((128, 48), (1, 0)),
               ((256, 64), (0, 0)), ((128, 32, 16), (1, 0, 1)), ((128, 16, 80), (0, 1, 1)),
-              ((256, 256, 3 * 16), (1, 1, 0)), ((240,), (1,)), ((128, 208), (0, 1))]
+              ((256, 256, 3 * 16), (1, 1, 0)), ((240,), (1,)), ((128, 208), (0, 1)),
+              ((37,), (0,)), ((50, 77), (0, 1)), ((130, 100), (1, 0)), ((230, 9), (1, 0)),
+              ((40, 24, 33), (1, 0, 1)), ((20, 6, 230), (0, 1, 1)), ((200, 9, 5), (0, 1, 0)), ((64, 150), (1, 1))]
 
 
 @pytest.mark.parametrize("n,bc", MMA_SHAPES)
@@ -144,15 +149,16 @@ def test_tensor_core_path_is_deterministic():
     """Two runs of a multi-mode BF16x3 scheme give identical bytes and no
     value strays far from the oracle (relative inf norm): a pass that read
     input another work item had already overwritten would show in either."""
-    p, rng = rand_problem(8, (128, 64, 48), (1, 0, 1), cubic=True)
-    U0 = smooth_data(p, rng, amp=0.8)
-    runs = [run_gpu(p, U0, 0.004, 4, "lawson4", "bf16x3") for _ in range(2)]
-    assert runs[0].tobytes() == runs[1].tobytes()
-    ref = O.integrate(oprob(p), U0, 0.004, 4, "lawson4")
-    assert O.rel_inf(runs[0], ref) <= 10 * TOL["bf16x3"]
+    for n in ((128, 64, 48), (70, 40, 30)):
+        p, rng = rand_problem(8, n, (1, 0, 1), cubic=True)
+        U0 = smooth_data(p, rng, amp=0.8)
+        runs = [run_gpu(p, U0, 0.004, 4, "lawson4", "bf16x3") for _ in range(2)]
+        assert runs[0].tobytes() == runs[1].tobytes()
+        ref = O.integrate(oprob(p), U0, 0.004, 4, "lawson4")
+        assert O.rel_inf(runs[0], ref) <= 10 * TOL["bf16x3"]
 
 
-@pytest.mark.parametrize("n,bc", [((64, 64), (0, 0)), ((24,), (0,)), ((128, 300), (0, 0)), ((8, 8), (2, 2))])
+@pytest.mark.parametrize("n,bc", [((128, 300), (0, 0)), ((300,), (1,)), ((8, 8), (2, 2))])
 def test_tensor_core_path_rejects_unsupported_shapes(n, bc):
     p, _ = rand_problem(5, n, bc)
     with pytest.raises(nat.CglError) as ei:
@@ -186,7 +192,8 @@ def test_schemes_match_oracle(n, bc, schemes, cubic, prec):
         check(got, ref, prec, "%s cubic=%s" % (s, cubic))
 
 
-MMA_SCHEME_CASES = [((128, 32), (0, 1)), ((128, 16, 32), (1, 0, 1)), ((64,), (0,))]
+MMA_SCHEME_CASES = [((128, 32), (0, 1)), ((128, 16, 32), (1, 0, 1)), ((64,), (0,)), ((50, 33), (0, 1)),
+                    ((20, 12, 9), (1, 0, 1))]
 
 
 @pytest.mark.parametrize("n,bc", MMA_SCHEME_CASES)
