@@ -107,9 +107,10 @@ def measured_peaks():
 def run_batch512(args):
     """512 independent 2D cubic / cubic-quintic instances (grids 48..256 per
     direction, Dirichlet/Neumann mixes, random parameters and bumps),
-    Lawson4, tau = 0.01: batched persistent launches (FP32 and FP64) against
-    the plain method (one FP64 plan per instance, stepped one after another),
-    and the FP32 batch's error after 200 steps against the FP64 batch."""
+    Lawson4, tau = 0.01: batched launches (BF16x3 on the tensor cores, FP32
+    and FP64 SIMT) against the plain method (one FP64 plan per instance,
+    stepped one after another), and the complex64 batches' errors after 200
+    steps against the FP64 batch."""
     import torch
     from paper_2403_02816_gb300 import native as nat
 
@@ -126,6 +127,8 @@ def run_batch512(args):
     # algorithmic flops per Lawson4 step: 2 sweeps x 2 fields x 8 n_mu N per mode,
     # plus g (15), the first-sweep combination (46) and the last (19) per point
     flops_step = sum(4 * 8 * (p.n[0] + p.n[1]) * p.N + (15 + 46 + 19) * p.N for p in probs)
+    # tensor-core flops issued per step: 6 split products of each mode product
+    tensor_flops_step = sum(6 * 4 * 8 * (p.n[0] + p.n[1]) * p.N for p in probs)
 
     def timed(step_fn, K):
         for _ in range(max(args.warmup, 3)):
@@ -144,12 +147,12 @@ def run_batch512(args):
 
     res, finals = {}, {}
     with Clocks(0) as clk:
-        for prec in ("f32", "f64"):
+        for prec in ("bf16x3", "f32", "f64"):
             t0 = time.perf_counter()
             with nat.Batch(probs, tau, "lawson4", prec) as b:
                 create_s = time.perf_counter() - t0
                 u = b.pack(fields, dev)
-                ms = timed(lambda k: b.step(u, k), args.steps if prec == "f32" else max(1, args.steps // 2))
+                ms = timed(lambda k: b.step(u, k), args.steps if prec != "f64" else max(1, args.steps // 2))
                 res["batched_" + prec] = {"grid_pt_steps_per_s": total / (ms / 1e3), "ms_per_time_step": ms,
                                           "create_s": create_s, "launches_per_step": b.launches_per_step,
                                           "achieved_tflops": flops_step / (ms / 1e3) / 1e12}
@@ -170,25 +173,40 @@ def run_batch512(args):
                                    "achieved_tflops": flops_step / (ms / 1e3) / 1e12}
         for pl in plans:
             pl.close()
-    errs = [float(np.linalg.norm(a - r) / np.linalg.norm(r)) for a, r in zip(finals["f32"], finals["f64"])]
+    def errs_vs_f64(prec):
+        e = [float(np.linalg.norm(a - r) / np.linalg.norm(r)) for a, r in zip(finals[prec], finals["f64"])]
+        return {"max": max(e), "median": float(np.median(e))}
     fp32_peak = FP32_PEAK_TFLOPS
     f32 = res["batched_f32"]
+    bf = res["batched_bf16x3"]
+    bf["achieved_tensor_tflops"] = tensor_flops_step / (bf["ms_per_time_step"] / 1e3) / 1e12
+    peaks = measured_peaks()
+    tpeak = float(peaks.get("bf16_tflops", 1948.7))
     line = {
-        "metric": METRIC, "value": f32["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": f32["ms_per_time_step"] * chunk, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": bf["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": bf["ms_per_time_step"] * chunk, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
         "config": {"workload": "batched_512x2d_lawson4_c64", "instances": count, "total_points": total,
                    "tau": tau, "time_steps_per_bench_step": chunk, "T_steps_for_error": args.t1_steps,
                    "l2": "flushed (256 MiB write) between timed iterations"},
         "results": res,
-        "f32_vs_f64_rel_l2_per_instance": {"max": max(errs), "median": float(np.median(errs))},
+        "bf16x3_vs_f64_rel_l2_per_instance": errs_vs_f64("bf16x3"),
+        "f32_vs_f64_rel_l2_per_instance": errs_vs_f64("f32"),
+        "speedup_batched_bf16x3_vs_single_f64": bf["grid_pt_steps_per_s"] /
+        res["single_plans_f64"]["grid_pt_steps_per_s"],
         "speedup_batched_f32_vs_single_f64": f32["grid_pt_steps_per_s"] / res["single_plans_f64"]["grid_pt_steps_per_s"],
         "speedup_batched_f64_vs_single_f64": res["batched_f64"]["grid_pt_steps_per_s"] /
         res["single_plans_f64"]["grid_pt_steps_per_s"],
-        "roofline": {"bound": "alu", "kernel": "batched_mode_pass_kernel<float>", "achieved": f32["achieved_tflops"],
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": f32["achieved_tflops"] / fp32_peak,
-                     "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
-                     "note": "whole-step time, all passes"},
+        "roofline": {"bound": "tensor", "kernel": "mma_mode_kernel (grouped)", "achieved": bf["achieved_tensor_tflops"],
+                     "peak": tpeak, "unit": "TFLOP/s", "frac": bf["achieved_tensor_tflops"] / tpeak,
+                     "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
+                     "note": "issued tensor flops over the whole-step time (all launches, pointwise stages "
+                             "included): a lower bound for the grouped pass"},
+        "roofline_f32_simt": {"bound": "alu", "kernel": "batched_mode_pass_kernel<float>",
+                              "achieved": f32["achieved_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
+                              "frac": f32["achieved_tflops"] / fp32_peak,
+                              "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
+                              "note": "whole-step time, all passes"},
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

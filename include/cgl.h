@@ -242,14 +242,19 @@ typedef struct cgl_batch cgl_batch;
 /*
  * Create a batch of `count` finite-difference problems (Dirichlet/Neumann;
  * periodic -> EUNSUPPORTED) sharing one step size and scheme (strang,
- * split4, lawson4, lawson2, strang_3t, split4_3t) in CGL_F64 or CGL_F32.  Each instance gets its own
- * FP64 factors exp(c tau A_mu) (Sec. 3.1).  Every mu-mode pass of a time step
- * is ONE persistent launch over all instances: a fixed grid of CTAs pulls
- * (instance, fiber tile) work items, largest first, from a device queue; the
- * fibers per tile come from cgl_autotune_mode_tile.  The whole time step is
- * replayed as one CUDA graph.  Synchronous (set-up and autotuning).
- * Errors: EINVAL (per-instance validation as cgl_plan_create, message names
- * the instance), EUNSUPPORTED, ENOMEM, ECUDA.
+ * split4, lawson4, lawson2, strang_3t, split4_3t) in CGL_F64, CGL_F32 or
+ * CGL_BF16X3 (complex64 state; every n_mu <= 256).  Each instance gets its
+ * own FP64 factors exp(c tau A_mu) (Sec. 3.1).  Every mu-mode pass of a time
+ * step is ONE launch over all instances.  F64 / F32: a fixed grid of CTAs
+ * pulls (instance, fiber tile) work items, largest first, from a device
+ * queue; the fibers per tile come from cgl_autotune_mode_tile.  BF16X3: one
+ * grouped tensor-core launch per mode whose CTAs map to (instance, fiber
+ * tile, output block) through a device table of per-instance arguments,
+ * between one grouped split prologue and one grouped plane epilogue per
+ * sweep.  The whole time step is replayed as one CUDA graph.  Synchronous
+ * (set-up and autotuning).
+ * Errors: EINVAL (bad precision or scheme; per-instance validation as
+ * cgl_plan_create, message names the instance), EUNSUPPORTED, ENOMEM, ECUDA.
  */
 int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, double tau, int scheme,
                      int precision, void* stream);

@@ -15,6 +15,13 @@
 // not, precision, right-hand sides, SM count) it times the mode-pass kernel on
 // a synthetic 2048-fiber field for every admissible tile size and keeps the
 // fastest, in memory and in the text file named by $CGL_AUTOTUNE_CACHE.
+//
+// BF16x3 batches run every mode pass on the tensor cores: per sweep one
+// grouped split prologue (a segment per instance), one grouped tcgen05 pass
+// per mode (a device table of per-instance pass arguments and tensor maps;
+// CTA b finds its instance by the CTA prefix sums) and one grouped plane
+// epilogue, over the BF16 / FP32 planes, factor splits and maps that each
+// instance's plan owns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +58,24 @@ struct cgl_batch {
     BatchItem* items = nullptr;     // device
   };
   std::vector<Pass> passes;
+  // BF16x3: per sweep, grouped pointwise stages and one grouped tcgen05 pass
+  // per mode
+  struct MmaMode {
+    void* passes = nullptr;  // device MmaPassArgs[npass]
+    void* maps = nullptr;    // device CUtensorMap[4 npass]
+    int* start = nullptr;    // device CTA prefix sums [npass + 1]
+    int npass = 0;
+    int64_t ctas = 0;
+    size_t smem = 0;
+  };
+  struct MmaSweep {
+    int sweep = 0, nrhs = 1;
+    SplitSeg* pro = nullptr;  // device, one per instance
+    EpiSeg* epi = nullptr;    // device, one per instance
+    int64_t max_n = 0;
+    std::vector<MmaMode> modes;
+  };
+  std::vector<MmaSweep> msweeps;
   std::vector<void*> allocations;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -205,8 +230,59 @@ int batch_alloc(cgl_batch* b, void** ptr, size_t bytes) {
   return CGL_OK;
 }
 
+// Per-instance buffers of field buffer u: u, then the work fields.
+void instance_bufs(const cgl_batch* b, void* u, int i, void** bufs) {
+  const size_t off = (size_t)b->offsets[i] * b->elem;
+  bufs[0] = (char*)u + off;
+  for (int w = 0; w < 3; ++w) bufs[1 + w] = b->work[w] ? (char*)b->work[w] + off : nullptr;
+}
+
+// BF16x3: the pointwise segments of every sweep for field buffer u.
+int upload_mma_segments(cgl_batch* b, void* u) {
+  std::vector<SplitSeg> pro(b->count);
+  std::vector<EpiSeg> epi(b->count);
+  for (auto& ms : b->msweeps) {
+    for (int i = 0; i < b->count; ++i) {
+      cgl_plan* p = b->plans[i];
+      const Sweep& sw = p->sweeps[ms.sweep];
+      void* bufs[NBUF];
+      instance_bufs(b, u, i, bufs);
+      SplitSeg g{};
+      for (int r = 0; r < 2; ++r) {
+        g.in[r] = static_cast<const float2*>(bufs[sw.in[r]]);
+        g.dst[r] = p->splits[r < sw.nrhs ? r : 0];
+      }
+      g.nin = sw.nin;
+      g.op = sw.op;
+      g.N = p->N;
+      g.n1 = p->n[0];
+      g.pitch = p->pitch;
+      g.Npad = p->Npad;
+      pro[i] = g;
+      EpiSeg e{};
+      for (int r = 0; r < 2; ++r) {
+        e.y[r] = static_cast<const float*>(p->planes[r < sw.nrhs ? r : 0]);
+        e.out[r] = static_cast<float2*>(bufs[sw.out[r]]);
+      }
+      for (int x = 0; x < kMaxExtra; ++x) e.ex[x] = static_cast<const float2*>(bufs[sw.extra[x]]);
+      e.nextra = sw.nextra;
+      e.nout = sw.nout;
+      e.op = sw.op;
+      e.N = p->N;
+      e.n1 = p->n[0];
+      e.pitch = p->pitch;
+      e.Npad = p->Npad;
+      epi[i] = e;
+    }
+    CUDA_TRY(cudaMemcpy(ms.pro, pro.data(), pro.size() * sizeof(SplitSeg), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(ms.epi, epi.data(), epi.size() * sizeof(EpiSeg), cudaMemcpyHostToDevice));
+  }
+  return CGL_OK;
+}
+
 // Per-instance pass arguments for field buffer u (device tables).
 int upload_tables(cgl_batch* b, void* u) {
+  if (b->precision == CGL_BF16X3) return upload_mma_segments(b, u);
   std::vector<ModePassArgs> host(b->count);
   for (auto& ps : b->passes) {
     for (int i = 0; i < b->count; ++i) {
@@ -224,6 +300,18 @@ int upload_tables(cgl_batch* b, void* u) {
 }
 
 int enqueue_batch_step(cgl_batch* b, cudaStream_t s) {
+  for (const auto& ms : b->msweeps) {
+    SplitSeg none{};
+    cudaError_t e = launch_split_prologue(none, ms.pro, b->count, ms.max_n, ms.nrhs, s);
+    if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched split prologue: ") + cudaGetErrorString(e));
+    for (const auto& md : ms.modes) {
+      e = launch_mma_group(md.passes, md.maps, md.start, md.npass, md.ctas, ms.nrhs, md.smem, s);
+      if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched tensor-core pass: ") + cudaGetErrorString(e));
+    }
+    EpiSeg enone{};
+    e = launch_plane_epilogue(enone, ms.epi, b->count, ms.max_n, ms.nrhs, b->status, s);
+    if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched plane epilogue: ") + cudaGetErrorString(e));
+  }
   for (size_t k = 0; k < b->passes.size(); ++k) {
     const auto& ps = b->passes[k];
     CUDA_TRY(cudaMemsetAsync(b->counters + k, 0, sizeof(int), s));
@@ -263,6 +351,97 @@ int ensure_batch_graph(cgl_batch* b, void* u) {
   return CGL_OK;
 }
 
+// BF16x3: the grouped tensor-core passes of every sweep (pass arguments and
+// tensor maps do not depend on the field buffer) and room for the pointwise
+// segments.
+int build_mma_sweeps(cgl_batch* b) {
+  const int nsweeps = (int)b->plans[0]->sweeps.size();
+  for (int sw = 0; sw < nsweeps; ++sw) {
+    cgl_batch::MmaSweep ms;
+    ms.sweep = sw;
+    ms.nrhs = b->plans[0]->sweeps[sw].nrhs;
+    for (cgl_plan* p : b->plans) ms.max_n = std::max(ms.max_n, p->N);
+    int st = batch_alloc(b, (void**)&ms.pro, (size_t)b->count * sizeof(SplitSeg));
+    if (!st) st = batch_alloc(b, (void**)&ms.epi, (size_t)b->count * sizeof(EpiSeg));
+    if (st) return st;
+    for (int mu = 0; mu < 3; ++mu) {
+      std::vector<MmaPassArgs> args;
+      std::vector<unsigned char> maps;
+      std::vector<int64_t> ctas;
+      std::vector<double> cost;
+      for (int i = 0; i < b->count; ++i) {
+        cgl_plan* p = b->plans[i];
+        if (p->d <= mu) continue;
+        const Sweep& w = p->sweeps[sw];
+        MmaLaunch L{};
+        L.n = (int)p->n[mu];
+        L.P = mma_axis_P(p, mu);
+        L.Q = mma_axis_Q(p, mu);
+        L.N = p->Npad;
+        L.pitch = p->pitch;
+        L.nrhs = w.nrhs;
+        for (int r = 0; r < 2; ++r) {
+          const int rr = r < w.nrhs ? r : 0;
+          L.tmA[r] = p->tmA[mu][rr];
+          L.tmB[r] = p->tmB[w.fac[rr]][mu];
+          // as in a single plan: mode passes alternate between the two plane
+          // sets, the last one writes the FP32 planes
+          L.out[r] = (mu == p->d - 1) ? p->planes[rr] : ((mu & 1) ? p->splits[rr] : p->splits_alt[rr]);
+        }
+        L.out_fp32 = mu == p->d - 1;
+        L.status = b->status;
+        MmaPassArgs a;
+        const int64_t c = mma_build_args(L, &a);
+        if (c < 0) {
+          char msg[96];
+          std::snprintf(msg, sizeof(msg), "instance %d: mode %d not supported by the tensor-core pass", i, mu + 1);
+          return fail(CGL_EUNSUPPORTED, msg);
+        }
+        args.push_back(a);
+        for (const void* m : {L.tmA[0], L.tmA[1], L.tmB[0], L.tmB[1]}) {
+          const unsigned char* q = static_cast<const unsigned char*>(m);
+          maps.insert(maps.end(), q, q + kTensorMapBytes);
+        }
+        ctas.push_back(c);
+        cost.push_back((double)c * a.np);
+      }
+      if (args.empty()) continue;
+      // largest passes first: their CTAs start before the small ones'
+      std::vector<size_t> order(args.size());
+      std::iota(order.begin(), order.end(), 0);
+      std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+      std::vector<MmaPassArgs> sargs(args.size());
+      std::vector<unsigned char> smaps(maps.size());
+      std::vector<int> start(args.size() + 1, 0);
+      cgl_batch::MmaMode md;
+      int64_t total = 0;
+      for (size_t k = 0; k < order.size(); ++k) {
+        const size_t o = order[k];
+        sargs[k] = args[o];
+        std::copy(maps.begin() + o * 4 * kTensorMapBytes, maps.begin() + (o + 1) * 4 * kTensorMapBytes,
+                  smaps.begin() + k * 4 * kTensorMapBytes);
+        start[k] = (int)total;
+        total += ctas[o];
+        md.smem = std::max(md.smem, mma_smem_bytes(args[o].nc));
+      }
+      if (total >= (int64_t)1 << 31) return fail(CGL_EUNSUPPORTED, "batch too large for one grouped pass");
+      start[order.size()] = (int)total;
+      md.npass = (int)sargs.size();
+      md.ctas = total;
+      st = batch_alloc(b, &md.passes, sargs.size() * sizeof(MmaPassArgs));
+      if (!st) st = batch_alloc(b, &md.maps, smaps.size());
+      if (!st) st = batch_alloc(b, (void**)&md.start, start.size() * sizeof(int));
+      if (st) return st;
+      CUDA_TRY(cudaMemcpy(md.passes, sargs.data(), sargs.size() * sizeof(MmaPassArgs), cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(md.maps, smaps.data(), smaps.size(), cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(md.start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
+      ms.modes.push_back(md);
+    }
+    b->msweeps.push_back(ms);
+  }
+  return CGL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -280,8 +459,9 @@ int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, doubl
   if (!out) return fail(CGL_EINVAL, "out is NULL");
   *out = nullptr;
   if (count < 1 || !probs) return fail(CGL_EINVAL, "count must be >= 1 and probs non-NULL");
-  if (precision != CGL_F64 && precision != CGL_F32)
-    return fail(CGL_EUNSUPPORTED, "batches run in CGL_F64 or CGL_F32");
+  if (precision != CGL_F64 && precision != CGL_F32 && precision != CGL_BF16X3)
+    return fail(precision < CGL_F64 || precision > CGL_BF16X3 ? CGL_EINVAL : CGL_EUNSUPPORTED,
+                "batches run in CGL_F64, CGL_F32 or CGL_BF16X3");
   if (scheme != CGL_STRANG && scheme != CGL_SPLIT4 && scheme != CGL_LAWSON4 && scheme != CGL_LAWSON2 &&
       scheme != CGL_STRANG3T && scheme != CGL_SPLIT4_3T)
     return fail(scheme < CGL_STRANG || scheme > CGL_SPLIT4_3T ? CGL_EINVAL : CGL_EUNSUPPORTED,
@@ -296,7 +476,7 @@ int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, doubl
   b->scheme = scheme;
   b->precision = precision;
   b->tau = tau;
-  b->elem = precision == CGL_F64 ? sizeof(double2) : sizeof(float2);
+  b->elem = precision == CGL_F64 ? sizeof(double2) : sizeof(float2);  // BF16x3: complex64 state
   int st = CGL_OK;
   for (int i = 0; i < count && !st; ++i) {
     const cgl_problem& q = probs[i];
@@ -319,9 +499,10 @@ int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, doubl
   if (!st && cudaMemset(b->status, 0, sizeof(int)) != cudaSuccess) st = fail(CGL_ECUDA, "memset status");
   if (!st && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
     st = fail(CGL_ECUDA, "stream create");
-  // passes and their work lists
+  if (!st && precision == CGL_BF16X3) st = build_mma_sweeps(b);
+  // passes and their work lists (SIMT precisions)
   const int sms = st ? 0 : sm_count();
-  const int nsweeps = st ? 0 : (int)b->plans[0]->sweeps.size();
+  const int nsweeps = (st || precision == CGL_BF16X3) ? 0 : (int)b->plans[0]->sweeps.size();
   const int d_max = 3;
   for (int sw = 0; !st && sw < nsweeps; ++sw) {
     for (int mu = 0; !st && mu < d_max; ++mu) {
@@ -388,7 +569,11 @@ int cgl_batch_info(const cgl_batch* b, int64_t* total_points, int64_t* offsets, 
     for (void* w : b->work) nw += w != nullptr;
     *workspace_bytes = (size_t)nw * b->total * b->elem;
   }
-  if (launches_per_step) *launches_per_step = (int)b->passes.size();
+  if (launches_per_step) {
+    int l = (int)b->passes.size();
+    for (const auto& ms : b->msweeps) l += 2 + (int)ms.modes.size();
+    *launches_per_step = l;
+  }
   return CGL_OK;
 }
 

@@ -166,6 +166,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   // and phase advance incrementally (no divisions on the issuing threads).
   int* counters = abort_flag + 1;  // stages loaded / consumed / committed
   if (threadIdx.x == 32) {
+    if constexpr (kTable) {
+      tensormap_acquire(tmA);
+      tensormap_acquire(tmB);
+    }
     int slot = 0, c = 0, j0 = 0, loaded = 0;
     uint32_t phase = 0;
     bool ok = true;

@@ -95,7 +95,6 @@ def test_batch_validation_before_any_cuda_call(lib):
     assert lib.cgl_batch_create(ctypes.byref(h), 0, arr, 0.01, nat.CGL_LAWSON4, nat.CGL_F32, None) == nat.CGL_EINVAL
     assert lib.cgl_batch_create(ctypes.byref(h), 1, arr, 0.01, nat.CGL_RK4, nat.CGL_F32, None) \
         == nat.CGL_EUNSUPPORTED
-    assert lib.cgl_batch_create(ctypes.byref(h), 1, arr, 0.01, nat.CGL_LAWSON4, nat.CGL_BF16X3, None) \
-        == nat.CGL_EUNSUPPORTED
+    assert lib.cgl_batch_create(ctypes.byref(h), 1, arr, 0.01, nat.CGL_LAWSON4, 7, None) == nat.CGL_EINVAL
     assert lib.cgl_batch_destroy(None) == nat.CGL_OK
     assert lib.cgl_autotune_mode_tile(1, 1, 0, 1, None, None) == nat.CGL_EINVAL

@@ -12,7 +12,7 @@ from paper_2403_02816_gb300 import native as nat
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-11, "f32": 2e-5}
+TOL = {"f64": 1e-11, "f32": 2e-5, "bf16x3": 2e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,9 +41,11 @@ def mixed_instances(seed=11):
     return probs, fields
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16x3"])
 @pytest.mark.parametrize("scheme", ["lawson4", "strang", "split4", "lawson2", "split4_3t"])
 def test_batch_equals_single_plans_and_oracle(prec, scheme):
+    """BF16x3: the grouped launches run the single plan's kernels per instance
+    (same splits, MMA order and epilogue), so batch and single plans agree."""
     probs, fields = mixed_instances()
     tau, nsteps = 0.01, 4
     dt = torch.complex128 if prec == "f64" else torch.complex64
@@ -65,9 +67,10 @@ def test_batch_equals_single_plans_and_oracle(prec, scheme):
         assert O.rel_l2(G, ref) <= TOL[prec], (p.n, O.rel_l2(G, ref))
 
 
-def test_batch_graph_follows_new_field_pointer():
+@pytest.mark.parametrize("prec", ["f32", "bf16x3"])
+def test_batch_graph_follows_new_field_pointer(prec):
     probs, fields = mixed_instances(3)
-    with nat.Batch(probs[:3], 0.01, "lawson4", "f32") as b:
+    with nat.Batch(probs[:3], 0.01, "lawson4", prec) as b:
         a = b.pack(fields[:3])
         c = b.pack(fields[:3])
         b.step(a, 2)
@@ -76,13 +79,14 @@ def test_batch_graph_follows_new_field_pointer():
         assert torch.equal(a, c)
 
 
-def test_batched_workload_subset_against_oracle_full_run():
+@pytest.mark.parametrize("prec", ["f32", "bf16x3"])
+def test_batched_workload_subset_against_oracle_full_run(prec):
     """The 512-instance workload's first 4 instances (complex64, Lawson4,
     tau = 0.01, 200 steps) inside a 16-instance batch, against the oracle."""
     probs = I.batched_problems(16)
     fields = [I.u0_bumps(p, np.random.Generator(np.random.PCG64(I.SEED_BASE + 3 + 1000 * i)))
               for i, p in enumerate(probs)]
-    with nat.Batch(probs, 0.01, "lawson4", "f32") as b:
+    with nat.Batch(probs, 0.01, "lawson4", prec) as b:
         u = b.pack(fields)
         b.step(u, 200)
         torch.cuda.synchronize()
