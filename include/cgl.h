@@ -89,8 +89,10 @@ enum cgl_status {
  * the workspace.
  *   out        receives the plan (set to NULL on failure).
  *   d          1, 2 or 3.
- *   n[d]       grid sizes, n_mu >= 2.  Periodic: powers of two <= 2048.
- *              Finite differences: n_mu <= 1024.
+ *   n[d]       grid sizes, n_mu >= 2.  Periodic: n_mu <= 2048 with no prime
+ *              factor above 7 (powers of two: radix-4/2 passes; others:
+ *              mixed-radix 4, 2, 3, 5, 7 passes).  Finite differences:
+ *              n_mu <= 1024.
  *   bc[d]      cgl_bc per direction; all periodic or none (else EUNSUPPORTED).
  *   lo[d],hi[d] domain, hi > lo.
  *   a1 > 0 (Sec. 1 assumption); b1, a2, a3, b3, a4, b4 any finite values
@@ -130,6 +132,28 @@ int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc,
 int cgl_plan_create_ex(cgl_plan** out, int d, const int64_t* n, const double* const* A,
                        double a3, double b3, double a4, double b4, double tau, int scheme,
                        int precision, void* stream);
+
+/*
+ * Create a plan for the coupled two-field system (Sec. 4.5, eq. coupled):
+ *   u_t =  a0 d_x1 u + (a1+i b1) Lap u + a2 u + (a3+i b3)|u|^2 u
+ *          + (a4+i b4)|u|^4 u + a5 |v|^2 u,
+ *   v_t = -a0 d_x1 v + (a1+i b1) Lap v + a2 v + (a3+i b3)|v|^2 v
+ *          + (a4+i b4)|v|^4 v + a5 |u|^2 v,
+ * periodic in every direction (Fourier pseudospectral; sizes as for
+ * cgl_plan_create).  K is block diagonal: each field has its own separable
+ * symbol, the advection term i (+-a0) kappa_1 on direction 1 (0 at the
+ * Nyquist mode of an even n_1, which keeps the system's mirror symmetry
+ * x1 -> L - x1, u <-> v).  The nonlinear sub-flow is one RK4 step of the
+ * coupled pointwise system.  scheme: CGL_STRANG or CGL_SPLIT4 (others
+ * EUNSUPPORTED); precision: CGL_F64 or CGL_F32.
+ * The field passed to cgl_step / cgl_step_host holds u (N values) followed
+ * by v (N values), each in the single-field layout; cgl_linear_flow applies
+ * exp(c tau K) to both.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA.
+ */
+int cgl_plan_create_coupled(cgl_plan** out, int d, const int64_t* n, const double* lo, const double* hi,
+                            double a0, double a1, double b1, double a2, double a3, double b3,
+                            double a4, double b4, double a5, double tau, int scheme, int precision,
+                            void* stream);
 
 /*
  * The paper's fourth-order finite-difference d^2/dx^2 matrix on (lo, hi),

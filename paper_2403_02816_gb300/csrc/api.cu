@@ -42,6 +42,15 @@ int64_t axis_P(const cgl_plan* p, int axis) {
   return P;
 }
 
+// Periodic sizes the FFT passes take: 2 <= n <= 2048 with no prime factor
+// above 7 (powers of two: radix-4/2 passes; else mixed radix 4, 2, 3, 5, 7).
+bool fft_size_ok(int64_t n) {
+  if (n < 2 || n > 2048) return false;
+  for (int r : {2, 3, 5, 7})
+    while (n % r == 0) n /= r;
+  return n == 1;
+}
+
 // Tensor-core planes: the faster product with the first direction padded to
 // the plane pitch, and the slower product.
 int64_t mma_axis_P(const cgl_plan* p, int axis) {
@@ -80,6 +89,7 @@ double pro_flops(const cgl_plan* p, const OpArgs& o) {
     case PRO_LAW2: return 23;
     case PRO_CQ: return 40;
     case PRO_CQ2: return 80;
+    case PRO_CFLOW: return 160;  // one coupled RK4 step: 4 x (g_u, g_v) + combinations
     default: return 0;
   }
 }
@@ -95,6 +105,8 @@ double epi_flops(const cgl_plan* p, const OpArgs& o) {
     case EPI_QC: return 40;
     case EPI_QC2: return 100;
     case EPI_SPLIT4_3T: return 44;
+    case EPI_CFLOW: return 160;
+    case EPI_CSPLIT4: return 168;
     default: return 0;
   }
 }
@@ -126,6 +138,13 @@ struct Timer {
   }
 };
 
+// Pointer of a sweep slot: buffer `id`, field `f` (coupled system: v is N
+// values after u).
+static void* slot_ptr(const cgl_plan* p, void* const* bufs, int id, int f) {
+  void* b = bufs[id];
+  return (b && f) ? static_cast<char*>(b) + (size_t)f * p->N * p->elem : b;
+}
+
 ModePassArgs make_mode_args(const cgl_plan* p, const Sweep& sw, int mu, void* const* bufs) {
   ModePassArgs a{};
   a.g = geom(p, mu);
@@ -134,11 +153,11 @@ ModePassArgs make_mode_args(const cgl_plan* p, const Sweep& sw, int mu, void* co
   a.f.nextra = sw.nextra;
   a.f.nout = sw.nout;
   for (int r = 0; r < 2; ++r) {
-    a.f.in[r] = bufs[sw.in[r]];
-    a.f.work[r] = bufs[sw.work[r]];
-    a.f.out[r] = bufs[sw.out[r]];
+    a.f.in[r] = slot_ptr(p, bufs, sw.in[r], sw.in_f[r]);
+    a.f.work[r] = slot_ptr(p, bufs, sw.work[r], sw.work_f[r]);
+    a.f.out[r] = slot_ptr(p, bufs, sw.out[r], sw.out_f[r]);
   }
-  for (int x = 0; x < 3; ++x) a.f.extra[x] = bufs[sw.extra[x]];
+  for (int x = 0; x < 3; ++x) a.f.extra[x] = slot_ptr(p, bufs, sw.extra[x], sw.extra_f[x]);
   a.op = sw.op;
   a.flags = (mu == 0 ? PASS_PRO : 0) | (mu == p->d - 1 ? PASS_EPI : 0);
   for (int r = 0; r < 2; ++r) a.factor[r] = p->fac[sw.fac[r < sw.nrhs ? r : 0]][mu];
@@ -154,11 +173,11 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
   f.nextra = sw.nextra;
   f.nout = sw.nout;
   for (int r = 0; r < 2; ++r) {
-    f.in[r] = bufs[sw.in[r]];
-    f.work[r] = bufs[sw.work[r]];
-    f.out[r] = bufs[sw.out[r]];
+    f.in[r] = slot_ptr(p, bufs, sw.in[r], sw.in_f[r]);
+    f.work[r] = slot_ptr(p, bufs, sw.work[r], sw.work_f[r]);
+    f.out[r] = slot_ptr(p, bufs, sw.out[r], sw.out_f[r]);
   }
-  for (int x = 0; x < 3; ++x) f.extra[x] = bufs[sw.extra[x]];
+  for (int x = 0; x < 3; ++x) f.extra[x] = slot_ptr(p, bufs, sw.extra[x], sw.extra_f[x]);
   const double Nd = (double)p->N;
   const double es = (double)p->elem;
   const bool f64 = p->precision == CGL_F64;
@@ -304,6 +323,7 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
     }
     a.twiddle = p->twiddle[mu];
     a.twform = p->twform[mu];
+    a.twplain = p->twplain[mu];
     a.status = p->status;
     const double nn = (double)p->n[mu];
     const double fft = 5.0 * std::log2(nn) * Nd * sw.nrhs;  // 5 n log2 n per pencil
@@ -455,19 +475,23 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
     for (int c = 0; c < p->nfac; ++c) {
       if ((st = dev_alloc(p, (void**)&p->fac64[c][mu], n * sizeof(double2)))) return st;
       CUDA_TRY(periodic_symbol_device(p->fac64[c][mu], n, L, p->cval[c] * p->tau, p->a1, p->b1, p->a2 / p->d,
-                                      1.0 / n, 0, s));
+                                      mu == 0 ? p->adv[c] : 0.0, 1.0 / n, 0, s));
       if ((st = make_working(p, p->fac64[c][mu], n, &p->fac[c][mu], s))) return st;
     }
     if (p->scheme == CGL_RK4 || p->scheme == CGL_RK2) {
       double2* k64 = nullptr;
       if ((st = dev_alloc(p, (void**)&k64, n * sizeof(double2)))) return st;
-      CUDA_TRY(periodic_symbol_device(k64, n, L, 0.0, p->a1, p->b1, p->a2 / p->d, 1.0 / (double)p->N, 1, s));
+      CUDA_TRY(periodic_symbol_device(k64, n, L, 0.0, p->a1, p->b1, p->a2 / p->d, 0.0, 1.0 / (double)p->N, 1, s));
       if ((st = make_working(p, k64, n, &p->ksym[mu], s))) return st;
     }
     const size_t treal = p->precision == CGL_F64 ? sizeof(double) : sizeof(float);
     if ((st = dev_alloc(p, &p->twiddle[mu], 2 * 3 * (size_t)n * treal))) return st;
     if ((st = dev_alloc(p, (void**)&p->twform[mu], 2 * (size_t)n * sizeof(int)))) return st;
     CUDA_TRY(fma_twiddles_device(p->twiddle[mu], p->twform[mu], n, p->precision == CGL_F64, s));
+    if ((n & (n - 1)) != 0) {  // mixed-radix passes take plain twiddles
+      if ((st = dev_alloc(p, &p->twplain[mu], 2 * (size_t)n * p->elem))) return st;
+      CUDA_TRY(plain_twiddles_device(p->twplain[mu], n, p->precision == CGL_F64, s));
+    }
   }
   return CGL_OK;
 }
@@ -475,12 +499,50 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
 void build_program(cgl_plan* p) {
   const double tau = p->tau;
   NlParams nl{p->a3, p->b3, p->a4, p->b4, p->cubic, tau};
+  nl.a5 = p->a5;
   auto base = [&]() {
     Sweep s;
     s.op.nl = nl;
     return s;
   };
   p->sweeps.clear();
+  if (p->coupled) {
+    // coupled system (eq. coupled): every sweep carries both fields, u as
+    // rhs 0 and v as rhs 1 (the second field of each buffer), with factors
+    // 2 k (u) and 2 k + 1 (v); phi is the coupled RK4 flow
+    auto pair = [&](Sweep& s, int in, int work, int out, int k) {
+      s.nin = 2; s.in[0] = s.in[1] = in; s.in_f[0] = 0; s.in_f[1] = 1;
+      s.nrhs = 2; s.fac[0] = 2 * k; s.fac[1] = 2 * k + 1;
+      s.work[0] = s.work[1] = work; s.work_f[0] = 0; s.work_f[1] = 1;
+      s.nout = 2; s.out[0] = s.out[1] = out; s.out_f[0] = 0; s.out_f[1] = 1;
+    };
+    if (p->scheme == CGL_STRANG) {  // eq. Strang
+      Sweep s = base();
+      pair(s, BUF_U, BUF_U, BUF_U, 0);
+      s.op.pro = PRO_CFLOW; s.op.t0 = tau / 2;
+      s.op.epi = EPI_CFLOW; s.op.te = tau / 2;
+      p->sweeps.push_back(s);
+    } else {  // eq. Richardson: c = 1 (k = 0), c = 1/2 (k = 1)
+      Sweep s1 = base();  // u_{n2} = phi_{tau/2}(E_1 phi_{tau/2}(W)) -> W0
+      pair(s1, BUF_U, BUF_W0, BUF_W0, 0);
+      s1.op.pro = PRO_CFLOW; s1.op.t0 = tau / 2;
+      s1.op.epi = EPI_CFLOW; s1.op.te = tau / 2;
+      Sweep s2 = base();  // v = phi_{tau/2}(E_{1/2} phi_{tau/4}(W)) -> W1
+      pair(s2, BUF_U, BUF_W1, BUF_W1, 1);
+      s2.op.pro = PRO_CFLOW; s2.op.t0 = tau / 4;
+      s2.op.epi = EPI_CFLOW; s2.op.te = tau / 2;
+      Sweep s3 = base();  // W = 4/3 phi_{tau/4}(E_{1/2} v) - 1/3 u_{n2}
+      pair(s3, BUF_W1, BUF_U, BUF_U, 1);
+      s3.op.pro = PRO_NONE;
+      s3.op.epi = EPI_CSPLIT4; s3.op.te = tau / 4;
+      s3.nextra = 2; s3.extra[0] = s3.extra[1] = BUF_W0; s3.extra_f[0] = 0; s3.extra_f[1] = 1;
+      p->sweeps.push_back(s1);
+      p->sweeps.push_back(s2);
+      p->sweeps.push_back(s3);
+    }
+    for (Sweep& s : p->sweeps) single_copies(s.op);
+    return;
+  }
   switch (p->scheme) {
     case CGL_STRANG: {  // eq. Strang
       Sweep s = base();
@@ -675,7 +737,8 @@ namespace cgl {
 
 int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
                      double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
-                     int scheme, int precision, void* stream, bool minimal, const double* const* A) {
+                     int scheme, int precision, void* stream, bool minimal, const double* const* A,
+                     const double* coupled) {
   g_last_error.clear();
   if (!out) return fail(CGL_EINVAL, "out is NULL");
   *out = nullptr;
@@ -697,10 +760,17 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   }
   if (nper != 0 && nper != d)
     return fail(CGL_EUNSUPPORTED, "mixing periodic and finite-difference directions is not supported");
+  if (coupled) {
+    if (!finite_all({coupled[0], coupled[1]})) return fail(CGL_EINVAL, "parameters must be finite");
+    if (nper != d) return fail(CGL_EUNSUPPORTED, "the coupled system is periodic (Fourier) only");
+    if (scheme != CGL_STRANG && scheme != CGL_SPLIT4)
+      return fail(CGL_EUNSUPPORTED, "the coupled system supports strang and split4");
+    if (precision == CGL_BF16X3) return fail(CGL_EUNSUPPORTED, "the coupled system runs in CGL_F64 or CGL_F32");
+  }
   const bool periodic = nper == d;
   for (int m = 0; m < d; ++m) {
-    if (periodic && ((n[m] & (n[m] - 1)) != 0 || n[m] > 2048))
-      return fail(CGL_EUNSUPPORTED, "periodic sizes must be powers of two <= 2048");
+    if (periodic && !fft_size_ok(n[m]))
+      return fail(CGL_EUNSUPPORTED, "periodic sizes must be 2^a 3^b 5^c 7^d <= 2048");
     if (!periodic && n[m] > 1024) return fail(CGL_EUNSUPPORTED, "finite-difference sizes must be <= 1024");
   }
   if (A) {
@@ -760,6 +830,22 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
     case CGL_RK2: p->nwork = 3; break;
     default: p->nwork = 2;
   }
+  if (coupled) {
+    // one factor per (c, field): slot 2 k + f has c = cval[k] of the single
+    // field scheme and advection +a0 (u, f = 0) or -a0 (v, f = 1)
+    p->coupled = true;
+    p->nfield = 2;
+    p->a0 = coupled[0];
+    p->a5 = coupled[1];
+    const int nc = p->nfac;
+    const double cv[2] = {p->cval[0], p->cval[1]};
+    for (int k = 0; k < nc; ++k)
+      for (int f = 0; f < 2; ++f) {
+        p->cval[2 * k + f] = cv[k];
+        p->adv[2 * k + f] = f == 0 ? p->a0 : -p->a0;
+      }
+    p->nfac = 2 * nc;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   int st = CGL_OK;
   cudaError_t e = prepare_kernels(p->dev);
@@ -773,7 +859,7 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   }
   if (!st) st = dev_alloc(p, (void**)&p->status, sizeof(int));
   if (!st && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) st = fail(CGL_ECUDA, "memset status");
-  for (int w = 0; !st && !minimal && w < p->nwork; ++w) st = dev_alloc(p, &p->work[w], p->N * p->elem);
+  for (int w = 0; !st && !minimal && w < p->nwork; ++w) st = dev_alloc(p, &p->work[w], p->nfield * p->N * p->elem);
   if (!st && precision == CGL_BF16X3) {
     // planes with the first direction padded to a multiple of 64, zeroed once:
     // the padding is never written afterwards (mode passes store rows i < n)
@@ -832,6 +918,19 @@ int cgl_plan_create_ex(cgl_plan** out, int d, const int64_t* n, const double* co
                           A);
 }
 
+int cgl_plan_create_coupled(cgl_plan** out, int d, const int64_t* n, const double* lo, const double* hi,
+                            double a0, double a1, double b1, double a2, double a3, double b3, double a4, double b4,
+                            double a5, double tau, int scheme, int precision, void* stream) {
+  if (d < 1 || d > 3) {
+    if (out) *out = nullptr;
+    return fail(CGL_EINVAL, "d must be 1, 2 or 3");
+  }
+  const int bc[3] = {CGL_BC_PERIODIC, CGL_BC_PERIODIC, CGL_BC_PERIODIC};
+  const double cpl[2] = {a0, a5};
+  return plan_create_impl(out, d, n, bc, lo, hi, a1, b1, a2, a3, b3, a4, b4, tau, scheme, precision, stream, false,
+                          nullptr, cpl);
+}
+
 int cgl_fd4_matrix(int n, double lo, double hi, int right_bc, double* out) {
   if (!out) return fail(CGL_EINVAL, "out is NULL");
   if (n < 6) return fail(CGL_EINVAL, "n must be >= 6");
@@ -887,11 +986,11 @@ int cgl_step_host(cgl_plan* p, void* u_host, int64_t nsteps, void* stream) {
   if (nsteps < 0) return fail(CGL_EINVAL, "nsteps must be >= 0");
   CUDA_TRY(cudaSetDevice(p->dev));
   if (!p->host_stage) {
-    int st = dev_alloc(p, &p->host_stage, p->N * p->elem);
+    int st = dev_alloc(p, &p->host_stage, p->nfield * p->N * p->elem);
     if (st) return st;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = p->N * p->elem;
+  const size_t bytes = p->nfield * p->N * p->elem;
   CUDA_TRY(cudaMemcpyAsync(p->host_stage, u_host, bytes, cudaMemcpyHostToDevice, s));
   int st = cgl_step(p, p->host_stage, nsteps, stream);
   if (st) return st;
@@ -903,14 +1002,19 @@ int cgl_step_host(cgl_plan* p, void* u_host, int64_t nsteps, void* stream) {
 int cgl_linear_flow(cgl_plan* p, double c, void* u, void* stream) {
   if (!p || !u) return fail(CGL_EINVAL, "plan and u must be non-NULL");
   int idx = -1;
-  for (int k = 0; k < p->nfac; ++k)
-    if (p->cval[k] == c) idx = k;
+  for (int k = p->nfac - 1; k >= 0; --k)
+    if (p->cval[k] == c) idx = k;  // the first factor with this c (coupled: u's, v's follows)
   if (idx < 0) return fail(CGL_EINVAL, "c is not one of the plan's factor values");
   CUDA_TRY(cudaSetDevice(p->dev));
   Sweep s;
   s.op.nl = NlParams{p->a3, p->b3, p->a4, p->b4, p->cubic, p->tau};
   single_copies(s.op);
   s.fac[0] = idx;
+  if (p->coupled) {  // both fields, each with its own symbol
+    s.nin = s.nrhs = s.nout = 2;
+    s.fac[1] = idx + 1;
+    s.in_f[1] = s.work_f[1] = s.out_f[1] = 1;
+  }
   return enqueue_sweep(p, s, u, (cudaStream_t)stream);
 }
 
@@ -918,7 +1022,7 @@ int cgl_plan_factor(cgl_plan* p, double c, int mu, double* host_out) {
   if (!p || !host_out) return fail(CGL_EINVAL, "plan and host_out must be non-NULL");
   if (mu < 0 || mu >= p->d) return fail(CGL_EINVAL, "mu out of range");
   int idx = -1;
-  for (int k = 0; k < p->nfac; ++k)
+  for (int k = p->nfac - 1; k >= 0; --k)
     if (p->cval[k] == c) idx = k;
   if (idx < 0) return fail(CGL_EINVAL, "c is not one of the plan's factor values");
   CUDA_TRY(cudaSetDevice(p->dev));
@@ -929,8 +1033,8 @@ int cgl_plan_factor(cgl_plan* p, double c, int mu, double* host_out) {
 
 int cgl_plan_info(const cgl_plan* p, size_t* field_bytes, size_t* workspace_bytes, int* launches) {
   if (!p) return fail(CGL_EINVAL, "plan is NULL");
-  if (field_bytes) *field_bytes = p->N * p->elem;
-  if (workspace_bytes) *workspace_bytes = (size_t)p->nwork * p->N * p->elem;
+  if (field_bytes) *field_bytes = p->nfield * p->N * p->elem;
+  if (workspace_bytes) *workspace_bytes = (size_t)p->nwork * p->nfield * p->N * p->elem;
   if (launches) *launches = launches_per_step(p);
   return CGL_OK;
 }

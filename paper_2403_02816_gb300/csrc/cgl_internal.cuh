@@ -55,7 +55,8 @@ enum ProOp : int {
   PRO_LAW4 = 3,    // z0 = in0, z1 = g(in0)                            (Lawson4, first sweep)
   PRO_LAW2 = 4,    // z0 = in0 + tau g(in0), z1 = in0 + tau/2 g(in0)   (Lawson2)
   PRO_CQ = 5,      // z0 = phi^c_{t0}(phi^q_{t0}(in0))                 (strang_3t)
-  PRO_CQ2 = 6      // z0 = phi^c_{t0}(phi^q_{t0}(in0)), z1 likewise t1 (split4_3t, first sweep)
+  PRO_CQ2 = 6,     // z0 = phi^c_{t0}(phi^q_{t0}(in0)), z1 likewise t1 (split4_3t, first sweep)
+  PRO_CFLOW = 7    // (z0, z1) = phi_{t0}(in0, in1): coupled system, u and v (eq. coupled)
 };
 enum EpiOp : int {
   EPI_NONE = 0,    // out_r = y_r
@@ -69,7 +70,9 @@ enum EpiOp : int {
   EPI_QC = 8,      // out0 = phi^q_t(phi^c_t(y0))                      (strang_3t)
   EPI_QC2 = 9,     // out0 = phi^q_t(phi^c_t(y0)),                     (split4_3t, first sweep)
                    // out1 = phi^c_{t/2}(phi^q_t(phi^c_{t/2}(y1)))
-  EPI_SPLIT4_3T = 10  // out0 = 4/3 phi^q_t(phi^c_t(y0)) - 1/3 e0      (split4_3t, second sweep)
+  EPI_SPLIT4_3T = 10, // out0 = 4/3 phi^q_t(phi^c_t(y0)) - 1/3 e0      (split4_3t, second sweep)
+  EPI_CFLOW = 11,     // (out0, out1) = phi_t(y0, y1)                  (coupled system)
+  EPI_CSPLIT4 = 12    // (out0, out1) = 4/3 phi_t(y0, y1) - 1/3 (e0, e1) (coupled split4)
 };
 
 // Nonlinear model parameters (eq. 1) and the per-pass operator constants.
@@ -80,6 +83,9 @@ struct NlParams {
   // FP32 copies (set by single_copies): FP32 kernels read these, so no
   // FP64-to-FP32 conversion runs per grid point
   float a3f, b3f, a4f, b4f, tauf;
+  // coupled system (eq. coupled): cross-coupling a5 |other|^2
+  double a5;
+  float a5f;
 };
 
 struct OpArgs {
@@ -102,6 +108,7 @@ inline void single_copies(OpArgs& o) {
   o.nl.a4f = (float)o.nl.a4;
   o.nl.b4f = (float)o.nl.b4;
   o.nl.tauf = (float)o.nl.tau;
+  o.nl.a5f = (float)o.nl.a5;
 }
 
 // The parameter in the working precision: the FP64 value or its FP32 copy.
@@ -153,6 +160,34 @@ template <class T, class T2> __device__ __forceinline__ T2 nl_flow(const NlParam
   return caxpy(u, t * (T(1) / T(6)), s);
 }
 
+// Coupled system (Sec. 4.5, eq. coupled): the nonlinear parts of the u and v
+// equations, g_u = ((a3 + i b3)|u|^2 + (a4 + i b4)|u|^4 + a5 |v|^2) u and g_v
+// with u and v exchanged.
+template <class T, class T2> __device__ __forceinline__ void nl_g2(const NlParams& p, T2 u, T2 v, T2& gu, T2& gv) {
+  const T a3 = pv<T>(p.a3, p.a3f), b3 = pv<T>(p.b3, p.b3f), a4 = pv<T>(p.a4, p.a4f), b4 = pv<T>(p.b4, p.b4f);
+  const T a5 = pv<T>(p.a5, p.a5f);
+  const T ru = fma(u.x, u.x, u.y * u.y), rv = fma(v.x, v.x, v.y * v.y);
+  const T cur = fma(ru, fma(a4, ru, a3), a5 * rv), cui = ru * fma(b4, ru, b3);
+  const T cvr = fma(rv, fma(a4, rv, a3), a5 * ru), cvi = rv * fma(b4, rv, b3);
+  gu = mk<T2>(fma(cur, u.x, -cui * u.y), fma(cur, u.y, cui * u.x));
+  gv = mk<T2>(fma(cvr, v.x, -cvi * v.y), fma(cvr, v.y, cvi * v.x));
+}
+
+// Nonlinear sub-flow of the coupled system: one RK4 step of (u, v)' = g(u, v)
+// over time t (the coupled flow has no closed form; Sec. 4.3 uses one RK4
+// step for the cubic-quintic model).
+template <class T, class T2> __device__ __forceinline__ void nl_flow2(const NlParams& p, T2& u, T2& v, T t) {
+  const T h = t * T(0.5);
+  T2 k1u, k1v, k2u, k2v, k3u, k3v, k4u, k4v;
+  nl_g2<T, T2>(p, u, v, k1u, k1v);
+  nl_g2<T, T2>(p, caxpy(u, h, k1u), caxpy(v, h, k1v), k2u, k2v);
+  nl_g2<T, T2>(p, caxpy(u, h, k2u), caxpy(v, h, k2v), k3u, k3v);
+  nl_g2<T, T2>(p, caxpy(u, t, k3u), caxpy(v, t, k3v), k4u, k4v);
+  const T s = t * (T(1) / T(6));
+  u = caxpy(u, s, caxpy(cadd(k1u, k4u), T(2), cadd(k2u, k3u)));
+  v = caxpy(v, s, caxpy(cadd(k1v, k4v), T(2), cadd(k2v, k3v)));
+}
+
 // Three-term splitting (Sec. 4.3): the cubic and quintic parts of g with
 // their exact flows, phi^c (eq. exsolcub) and phi^q, composed as
 // P_t = phi^c_t o phi^q_t before the linear flow and P*_t = phi^q_t o phi^c_t
@@ -184,6 +219,11 @@ __device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2
     case PRO_CQ2:
       z[0] = flow_c<T, T2>(o.nl, flow_q<T, T2>(o.nl, in[0], pv<T>(o.t0, o.t0f)), pv<T>(o.t0, o.t0f));
       z[1] = flow_c<T, T2>(o.nl, flow_q<T, T2>(o.nl, in[0], pv<T>(o.t1, o.t1f)), pv<T>(o.t1, o.t1f));
+      break;
+    case PRO_CFLOW:
+      z[0] = in[0];
+      z[1] = in[1];
+      nl_flow2<T, T2>(o.nl, z[0], z[1], pv<T>(o.t0, o.t0f));
       break;
     case PRO_LAW2: {
       const T2 gn = nl_g<T, T2>(o.nl, in[0]);
@@ -277,6 +317,20 @@ __device__ __forceinline__ int apply_epilogue(const OpArgs& o, const T2* y, cons
       return 1;
     case EPI_RK:
       return rk_stage<T, T2>(o, y[0], e, out);
+    case EPI_CFLOW:
+      out[0] = y[0];
+      out[1] = y[1];
+      nl_flow2<T, T2>(o.nl, out[0], out[1], pv<T>(o.te, o.tef));
+      return 2;
+    case EPI_CSPLIT4: {
+      T2 f0 = y[0], f1 = y[1];
+      nl_flow2<T, T2>(o.nl, f0, f1, pv<T>(o.te, o.tef));
+      out[0] = mk<T2>(fma(T(4) / T(3), f0.x, -(T(1) / T(3)) * e[0].x),
+                      fma(T(4) / T(3), f0.y, -(T(1) / T(3)) * e[0].y));
+      out[1] = mk<T2>(fma(T(4) / T(3), f1.x, -(T(1) / T(3)) * e[1].x),
+                      fma(T(4) / T(3), f1.y, -(T(1) / T(3)) * e[1].y));
+      return 2;
+    }
     default:
       out[0] = y[0];
       out[1] = y[1];
@@ -331,6 +385,7 @@ struct FftPassArgs {
   Symbol sym[kMaxRhs];
   const void* twiddle;  // T[2][n_ax][3]: FMA-butterfly form of exp(-+2 pi i m / n_ax), see fft.cu
   const int* twform;    // int[2][n_ax]
+  const void* twplain;  // T2[2][n_ax]: exp(-+2 pi i m / n_ax) (mixed-radix n_ax)
   int* status;          // device status word (bit 0: non-finite output)
 };
 
@@ -393,11 +448,15 @@ cudaError_t launch_conv_mma(const float* x, const __nv_bfloat16* w, const float*
 // dA: n x n column-major double2 (device); dOut: same layout.  work: 3*n*n double2.
 cudaError_t expm_device(const double2* dA, double scale, int n, double2* dOut, double2* work,
                         double norm1, cudaStream_t s);
-// Periodic symbols: vec[k] = exp(c*tau*(alpha*(-kappa_k^2) + beta)) * post  (sum_form = 0)
-//                   vec[k] = (alpha*(-kappa_k^2) + beta) * post              (sum_form = 1)
+// Periodic symbols: vec[k] = exp(c*tau*(alpha*(-kappa_k^2) + beta + i adv kappa'_k)) * post  (sum_form = 0)
+//                   vec[k] = (alpha*(-kappa_k^2) + beta + i adv kappa'_k) * post              (sum_form = 1)
+// kappa' = kappa but 0 at the Nyquist mode of an even n.
 cudaError_t periodic_symbol_device(double2* dOut, int n, double L, double ctau, double ar,
-                                   double ai, double beta, double post, int sum_form,
+                                   double ai, double beta, double adv, double post, int sum_form,
                                    cudaStream_t s);
+// Plain twiddles exp(-+2 pi i m/n), T2[2][n] (forward, inverse), for the
+// mixed-radix FFT passes.
+cudaError_t plain_twiddles_device(void* tab, int n, int f64, cudaStream_t s);
 // FFT twiddles for the FMA butterflies: for w = exp(-+2 pi i m/n) = c + i s,
 // form 0 (|c| >= |s|): tau = s/c, m_re = m_im = c; form 1: tau = -c/s,
 // m_re = -s, m_im = s.  Tables in T (double when f64, else float).

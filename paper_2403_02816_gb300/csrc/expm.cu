@@ -103,18 +103,22 @@ cudaError_t expm_device(const double2* dA, double scale, int n, double2* dOut, d
 }
 
 // Fourier symbol of one periodic direction (Sec. 3.2), FFT order
-// m = 0..n/2-1, -n/2..-1, kappa = 2 pi m / L:
-//   sum_form = 0: exp(ctau * ((ar + i ai)(-kappa^2) + beta)) * post
-//   sum_form = 1: ((ar + i ai)(-kappa^2) + beta) * post
+// m = 0..ceil(n/2)-1, then the negative frequencies, kappa = 2 pi m / L:
+//   sum_form = 0: exp(ctau * ((ar + i ai)(-kappa^2) + beta + i adv kappa')) * post
+//   sum_form = 1: ((ar + i ai)(-kappa^2) + beta + i adv kappa') * post
+// kappa' = kappa except at the Nyquist mode of an even n, where the first
+// derivative's symbol is 0 (adv: the advection speed of eq. (coupled) on its
+// direction, 0 elsewhere).
 __global__ void periodic_symbol_kernel(double2* out, int n, double L, double ctau, double ar, double ai,
-                                       double beta, double post, int sum_form) {
+                                       double beta, double adv, double post, int sum_form) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const int m = (k < n / 2) ? k : k - n;
+  const int m = (k <= (n - 1) / 2) ? k : k - n;
   const double kap = 2.0 * M_PI * (double)m / L;
   const double k2 = kap * kap;
+  const double k1 = (2 * k == n) ? 0.0 : kap;
   const double re = -ar * k2 + beta;
-  const double im = -ai * k2;
+  const double im = -ai * k2 + adv * k1;
   if (sum_form) {
     out[k] = make_double2(re * post, im * post);
   } else {
@@ -126,8 +130,27 @@ __global__ void periodic_symbol_kernel(double2* out, int n, double L, double cta
 }
 
 cudaError_t periodic_symbol_device(double2* dOut, int n, double L, double ctau, double ar, double ai,
-                                   double beta, double post, int sum_form, cudaStream_t s) {
-  periodic_symbol_kernel<<<(n + 127) / 128, 128, 0, s>>>(dOut, n, L, ctau, ar, ai, beta, post, sum_form);
+                                   double beta, double adv, double post, int sum_form, cudaStream_t s) {
+  periodic_symbol_kernel<<<(n + 127) / 128, 128, 0, s>>>(dOut, n, L, ctau, ar, ai, beta, adv, post, sum_form);
+  return cudaGetLastError();
+}
+
+// Plain twiddles exp(-+2 pi i m / n) (forward table, then inverse), for the
+// mixed-radix passes: T2 tab[2][n].
+template <class T2> __global__ void plain_twiddle_kernel(T2* tab, int n) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double sn, cs;
+  sincospi(2.0 * (double)m / (double)n, &sn, &cs);
+  tab[m].x = cs;
+  tab[m].y = -sn;
+  tab[n + m].x = cs;
+  tab[n + m].y = sn;
+}
+
+cudaError_t plain_twiddles_device(void* tab, int n, int f64, cudaStream_t s) {
+  if (f64) plain_twiddle_kernel<double2><<<(n + 127) / 128, 128, 0, s>>>((double2*)tab, n);
+  else plain_twiddle_kernel<float2><<<(n + 127) / 128, 128, 0, s>>>((float2*)tab, n);
   return cudaGetLastError();
 }
 

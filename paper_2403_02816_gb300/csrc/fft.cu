@@ -152,6 +152,75 @@ __device__ void fft_tile(T2* s0, int tile_stride, int pitch, int n, int logn, in
   if (logn & 1) fft_stage<T, T2, 2, NR>(s0, tile_stride, pitch, n, logn - 1, tb, p, tt, tf, inv);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-radix passes (n = 2^a 3^b 5^c 7^d, not a power of two): the same
+// Stockham recursion with radices 4, 2, 3, 5, 7 in that order, out of place
+// between two tiles, plain complex twiddles w_(pR)^(r k) and R-point DFTs
+// whose roots of unity come from the same n-point table (w_R^j = w_n^(j n/R)).
+// ---------------------------------------------------------------------------
+
+template <class T2, int R>
+__device__ __forceinline__ void mr_stage(const T2* src, T2* dst, int nrhs_tiles, int tile_stride, int pitch, int n,
+                                         int tb, int p, const T2* tw, bool inv) {
+  const int nb = n / R;
+  const int total = tb * nb;
+  const int twstep = n / (p * R);
+  const int rstep = n / R;
+  for (int q = threadIdx.x; q < total; q += kFftThreads) {
+    const int t = q / nb, i = q - t * nb;
+    const int k = i % p;
+    const int so = t * pitch + i;
+    const int dso = t * pitch + (i - k) * R + k;
+    for (int rr = 0; rr < nrhs_tiles; ++rr) {
+      T2 x[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = src[rr * tile_stride + so + r * nb];
+      if (k > 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw[r * k * twstep]);
+      }
+      if constexpr (R == 2) {
+        dft2(x);
+      } else if constexpr (R == 4) {
+        dft4(x, inv);
+      } else {
+        T2 y[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          T2 acc = x[0];
+#pragma unroll
+          for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(x[r], tw[((r * m) % R) * rstep]));
+          y[m] = acc;
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = y[m];
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[rr * tile_stride + dso + r * p] = x[r];
+    }
+  }
+  __syncthreads();
+}
+
+// Transform the NR tiles starting in `a`; returns the tile holding the result
+// (a or b).  tw: this direction's plain table (forward or inverse).
+template <class T2, int NR>
+__device__ T2* mr_tile(T2* a, T2* b, int tile_stride, int pitch, int n, int tb, const T2* tw, bool inv) {
+  int m = n, p = 1;
+  T2 *src = a, *dst = b;
+  while (m > 1) {
+    if (m % 4 == 0) { mr_stage<T2, 4>(src, dst, NR, tile_stride, pitch, n, tb, p, tw, inv); p *= 4; m /= 4; }
+    else if (m % 2 == 0) { mr_stage<T2, 2>(src, dst, NR, tile_stride, pitch, n, tb, p, tw, inv); p *= 2; m /= 2; }
+    else if (m % 3 == 0) { mr_stage<T2, 3>(src, dst, NR, tile_stride, pitch, n, tb, p, tw, inv); p *= 3; m /= 3; }
+    else if (m % 5 == 0) { mr_stage<T2, 5>(src, dst, NR, tile_stride, pitch, n, tb, p, tw, inv); p *= 5; m /= 5; }
+    else { mr_stage<T2, 7>(src, dst, NR, tile_stride, pitch, n, tb, p, tw, inv); p *= 7; m /= 7; }
+    T2* x = src;
+    src = dst;
+    dst = x;
+  }
+  return src;
+}
+
 template <class T2> __device__ __forceinline__ T2 ldf(const void* base, int64_t off) {
   return reinterpret_cast<const T2*>(base)[off];
 }
@@ -159,11 +228,11 @@ template <class T2> __device__ __forceinline__ void stf(void* base, int64_t off,
   reinterpret_cast<T2*>(base)[off] = v;
 }
 
-template <class T, int NR>
+template <class T, int NR, bool MR>
 __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned char* smem_raw) {
   using T2 = typename C2<T>::type;
   const int n = (int)a.g.n_ax;
-  const int logn = __ffs(n) - 1;
+  const int logn = __ffs(n) - 1;  // power-of-two passes only
   const int tbmax = max(1, kFftTile / n);
   const int pitch = n + 1;
   const int tile_stride = tbmax * pitch;
@@ -172,14 +241,33 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned cha
   const int64_t P = a.g.P;
 
   T2* tile0 = reinterpret_cast<T2*>(smem_raw);
-  T2* pfac = tile0 + NR * tile_stride;  // [kMaxRhs][tbmax]
+  T2* tile1 = tile0 + NR * tile_stride;               // mixed radix: second (ping-pong) tile
+  T2* pfac = tile0 + (MR ? 2 : 1) * NR * tile_stride;  // [kMaxRhs][tbmax]
   int64_t* pbase = reinterpret_cast<int64_t*>(pfac + kMaxRhs * tbmax);
   T* tt = reinterpret_cast<T*>(pbase + tbmax);  // [2][n][3] twiddles (forward, inverse)
   int* tf = reinterpret_cast<int*>(tt + 6 * n);  // [2][n] twiddle forms
+  // mixed radix: [2][n] plain twiddles, 16-byte aligned (tbmax may be odd)
+  T2* twp = reinterpret_cast<T2*>((reinterpret_cast<uintptr_t>(pbase + tbmax) + 15) & ~uintptr_t(15));
 
-  const T* ttg = reinterpret_cast<const T*>(a.twiddle);
-  for (int m = threadIdx.x; m < 6 * n; m += kFftThreads) tt[m] = ttg[m];
-  for (int m = threadIdx.x; m < 2 * n; m += kFftThreads) tf[m] = a.twform[m];
+  if constexpr (MR) {
+    const T2* twg = reinterpret_cast<const T2*>(a.twplain);
+    for (int m = threadIdx.x; m < 2 * n; m += kFftThreads) twp[m] = twg[m];
+  } else {
+    const T* ttg = reinterpret_cast<const T*>(a.twiddle);
+    for (int m = threadIdx.x; m < 6 * n; m += kFftThreads) tt[m] = ttg[m];
+    for (int m = threadIdx.x; m < 2 * n; m += kFftThreads) tf[m] = a.twform[m];
+  }
+  // (pencil t, position j) of element e: pencil-major for contiguous
+  // pencils, position-major otherwise
+  auto split = [&](int e, int& t, int& j) {
+    if (P == 1) {
+      if (MR) { t = e / n; j = e - t * n; }
+      else { t = e >> logn; j = e & (n - 1); }
+    } else {
+      j = e / tb;
+      t = e - j * tb;
+    }
+  };
   for (int t = threadIdx.x; t < tb; t += kFftThreads) {
     const int64_t b = b0 + t;
     const int64_t p = b % P, q = b / P;
@@ -210,8 +298,7 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned cha
   const int cnt = tb * n;
   for (int e = threadIdx.x; e < cnt; e += kFftThreads) {
     int t, j;
-    if (P == 1) { t = e >> logn; j = e & (n - 1); }
-    else { j = e / tb; t = e - j * tb; }
+    split(e, t, j);
     const int64_t off = pbase[t] + P * j;
     T2 z[2];
     if (a.flags & PASS_PRO) {
@@ -229,34 +316,42 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned cha
   __syncthreads();
 
   // ---- transforms (all right-hand sides together)
-  if (a.flags & PASS_FWD) fft_tile<T, T2, NR>(tile0, tile_stride, pitch, n, logn, tb, tt, tf, false);
+  T2* cur = tile0;  // tile holding the data (mixed radix ping-pongs)
+  if (a.flags & PASS_FWD) {
+    if constexpr (MR) cur = mr_tile<T2, NR>(cur, cur == tile0 ? tile1 : tile0, tile_stride, pitch, n, tb, twp, false);
+    else fft_tile<T, T2, NR>(tile0, tile_stride, pitch, n, logn, tb, tt, tf, false);
+  }
   if (a.flags & PASS_MUL) {
     for (int e = threadIdx.x; e < cnt; e += kFftThreads) {
-      const int t = e >> logn, j = e & (n - 1);
+      int t, j;
+      if (MR) { t = e / n; j = e - t * n; }
+      else { t = e >> logn; j = e & (n - 1); }
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const Symbol& S = a.sym[r];
         const T2 va = reinterpret_cast<const T2*>(S.vec[a.g.axis])[j];
         const T2 c = pfac[r * tbmax + t];
         const T2 f = S.sum_form ? cadd(c, va) : cmul(c, va);
-        T2* sp = tile0 + r * tile_stride + t * pitch + j;
+        T2* sp = cur + r * tile_stride + t * pitch + j;
         *sp = cmul(*sp, f);
       }
     }
     __syncthreads();
   }
-  if (a.flags & PASS_INV) fft_tile<T, T2, NR>(tile0, tile_stride, pitch, n, logn, tb, tt + 3 * n, tf + n, true);
+  if (a.flags & PASS_INV) {
+    if constexpr (MR) cur = mr_tile<T2, NR>(cur, cur == tile0 ? tile1 : tile0, tile_stride, pitch, n, tb, twp + n, true);
+    else fft_tile<T, T2, NR>(tile0, tile_stride, pitch, n, logn, tb, tt + 3 * n, tf + n, true);
+  }
 
   // ---- store (+ epilogue)
   bool bad = false;
   for (int e = threadIdx.x; e < cnt; e += kFftThreads) {
     int t, j;
-    if (P == 1) { t = e >> logn; j = e & (n - 1); }
-    else { j = e / tb; t = e - j * tb; }
+    split(e, t, j);
     const int64_t off = pbase[t] + P * j;
     T2 y[2];
-    y[0] = tile0[t * pitch + j];
-    y[1] = NR > 1 ? tile0[tile_stride + t * pitch + j] : y[0];
+    y[0] = cur[t * pitch + j];
+    y[1] = NR > 1 ? cur[tile_stride + t * pitch + j] : y[0];
     if (a.flags & PASS_EPI) {
       T2 ex[kMaxExtra], o[2];
 #pragma unroll
@@ -278,10 +373,10 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned cha
   if (bad && a.status) atomicOr(a.status, 1);
 }
 
-template <class T, int NR>
+template <class T, int NR, bool MR = false>
 __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftPassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fft_pass_body<T, NR>(a, smem_raw);
+  fft_pass_body<T, NR, MR>(a, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -468,12 +563,13 @@ __global__ void __launch_bounds__(kFftThreads) fft4_pass_kernel(const FftPassArg
     for (int r = 0; r < B; ++r) v[rr][r] = mk<T2>(0, 0);
   if (live) {
     if ((a.flags & PASS_PRO) && a.op.pro != PRO_NONE) {
-      // an operator prologue (one input field): all loads first, parked in
+      // an operator prologue: the first input field's loads first, parked in
       // this thread's own slots of the exchange buffer (free until the first
       // transpose, whose opening barrier orders these reads before its
       // writes); then the operator as a rolled loop over chunks of four
       // elements, each chunk appended at the top of v while v shifts down
-      // by four, for the reason given at the store
+      // by four, for the reason given at the store.  A second input field
+      // (the coupled system's v) is read inside the loop.
       constexpr int CH = B < 4 ? B : 4;
       T2* park = ex + pp * PS;
       {
@@ -490,6 +586,7 @@ __global__ void __launch_bounds__(kFftThreads) fft4_pass_kernel(const FftPassArg
         for (int c = 0; c < CH; ++c) {
           const T2 x = park[t + A * (r0 + c)];
           T2 in[2] = {x, x}, z[2];
+          if (a.f.nin > 1) in[1] = ldf<T2>(a.f.in[1], base + P * (t + A * (r0 + c)));
           apply_prologue<T, T2>(a.op, in, z);
           z0[c] = z[0];
           z1[c] = z[1];
@@ -629,21 +726,34 @@ static cudaError_t fft4_dispatch(int logn, bool prepare, const FftPassArgs* a, c
   }
 }
 
-static size_t fft_smem_bytes(int n, int nrhs, size_t elem) {
+static size_t fft_smem_bytes(int n, int nrhs, size_t elem, bool mr = false) {
   const int tbmax = std::max(1, kFftTile / n);
   const int pitch = n + 1;
-  // tiles | pencil factors | pencil bases | twiddles [2][n][3] of T | forms [2][n]
-  return (size_t)tbmax * pitch * elem * nrhs + (size_t)kMaxRhs * tbmax * elem + (size_t)tbmax * sizeof(int64_t) +
-         (size_t)6 * n * (elem / 2) + (size_t)2 * n * sizeof(int);
+  // tiles (two when mixed radix) | pencil factors | pencil bases | twiddles:
+  // [2][n][3] of T + forms [2][n], or plain [2][n] of T2 (mixed radix)
+  const size_t tw = mr ? (size_t)2 * n * elem + 16 : (size_t)6 * n * (elem / 2) + (size_t)2 * n * sizeof(int);
+  return (size_t)tbmax * pitch * elem * nrhs * (mr ? 2 : 1) + (size_t)kMaxRhs * tbmax * elem +
+         (size_t)tbmax * sizeof(int64_t) + tw;
 }
+
+bool fft_is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 template <class T> cudaError_t launch_fft_pass(const FftPassArgs& a, cudaStream_t s) {
   using T2 = typename C2<T>::type;
   const int n = (int)a.g.n_ax;
-  const int logn = __builtin_ctz((unsigned)n);
-  if (logn >= kFft4MinLogn && logn <= fft4_max_logn<T>()) return fft4_dispatch<T>(logn, false, &a, s);
   const int tbmax = std::max(1, kFftTile / n);
   const int64_t grid = (a.g.npencils + tbmax - 1) / tbmax;
+  if (!fft_is_pow2(n)) {
+    const size_t smem = fft_smem_bytes(n, a.f.nrhs, sizeof(T2), true);
+    if (smem > kFftMaxSmem || !a.twplain) return cudaErrorInvalidValue;
+    if (a.f.nrhs > 1)
+      fft_pass_kernel<T, 2, true><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
+    else
+      fft_pass_kernel<T, 1, true><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  const int logn = __builtin_ctz((unsigned)n);
+  if (logn >= kFft4MinLogn && logn <= fft4_max_logn<T>()) return fft4_dispatch<T>(logn, false, &a, s);
   const size_t smem = fft_smem_bytes(n, a.f.nrhs, sizeof(T2));
   if (a.f.nrhs > 1)
     fft_pass_kernel<T, 2><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
@@ -658,6 +768,10 @@ template <class T> cudaError_t prepare_fft_pass() {
   cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fft_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fft_pass_kernel<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fft_pass_kernel<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem);
   if (e != cudaSuccess) return e;
   for (int logn = kFft4MinLogn; logn <= fft4_max_logn<T>(); ++logn)
     if ((e = fft4_dispatch<T>(logn, true, nullptr, nullptr)) != cudaSuccess) return e;

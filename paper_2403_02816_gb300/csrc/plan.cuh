@@ -24,6 +24,9 @@ struct Sweep {
   int nout = 1, out[2] = {BUF_U, BUF_U};
   OpArgs op{};
   bool stencil = false;  // FD Runge-Kutta stage: K x as a stencil + epilogue, one launch
+  // field of each slot within its buffer (coupled system: 0 = u, 1 = v, N
+  // values further)
+  int in_f[2] = {0, 0}, work_f[2] = {0, 0}, extra_f[3] = {0, 0, 0}, out_f[2] = {0, 0};
 };
 
 struct KernelStat {
@@ -49,18 +52,25 @@ struct cgl_plan {
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   double a1 = 0, b1 = 0, a2 = 0, a3 = 0, b3 = 0, a4 = 0, b4 = 0, tau = 0;
   int scheme = 0, precision = 0, periodic = 0, cubic = 0;
+  // coupled two-field system (eq. coupled): advection a0, cross-coupling a5;
+  // the state is u followed by v (nfield = 2 fields of N values)
+  bool coupled = false;
+  int nfield = 1;
+  double a0 = 0, a5 = 0;
   bool user_mats = false;            // direction matrices supplied by the caller
   std::vector<double2> userA[3];     // their host copies (n_mu x n_mu, column-major)
   int64_t N = 0;
   size_t elem = 0;
 
   int nfac = 0;
-  double cval[2] = {0, 0};
-  void* fac[2][3] = {{nullptr}};        // working-precision factors / symbol vectors
-  double2* fac64[2][3] = {{nullptr}};   // FP64 masters
+  double cval[4] = {0, 0, 0, 0};
+  double adv[4] = {0, 0, 0, 0};         // advection speed of each factor's field (periodic direction 1)
+  void* fac[4][3] = {{nullptr}};        // working-precision factors / symbol vectors
+  double2* fac64[4][3] = {{nullptr}};   // FP64 masters
   void* ksym[3] = {nullptr};            // K symbol vectors (periodic Runge-Kutta)
   void* twiddle[3] = {nullptr};         // FFT twiddle tables per axis: [fwd, inv][n][tau, m_re, m_im]
   int* twform[3] = {nullptr};           // [fwd, inv][n] twiddle form (0: m = cos, 1: m = sin)
+  void* twplain[3] = {nullptr};         // mixed-radix axes: [fwd, inv][n] plain twiddles (T2)
   std::vector<void*> allocations;
 
   int nwork = 0;
@@ -104,8 +114,10 @@ ModePassArgs make_mode_args(const cgl_plan* p, const Sweep& sw, int mu, void* co
 // the tensor-core buffers (factors only, for batches).
 // A (optional): caller-supplied direction matrices A_mu, complex n_mu x n_mu
 // column-major as (re, im) doubles, replacing (a1 + i b1) D2_mu + a2/d.
+// coupled (optional): {a0, a5} of the coupled two-field system (eq. coupled).
 int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
                      double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,
-                     int scheme, int precision, void* stream, bool minimal, const double* const* A = nullptr);
+                     int scheme, int precision, void* stream, bool minimal, const double* const* A = nullptr,
+                     const double* coupled = nullptr);
 
 }  // namespace cgl

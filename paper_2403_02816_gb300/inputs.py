@@ -233,3 +233,67 @@ def plane_wave_data(prob: Problem, m_vec, amp: float) -> np.ndarray:
     phase = sum(2 * np.pi * m_vec[mu] / (prob.hi[mu] - prob.lo[mu]) * X[mu]
                 for mu in range(prob.d))
     return amp * np.exp(1j * phase)
+
+
+# --------------------------------------------------------------------------
+# Coupled two-field system (Sec. 4.5, eq. coupled)
+# --------------------------------------------------------------------------
+
+@dataclass
+class CoupledProblem:
+    """Parameters of eq. (coupled), periodic in every direction."""
+
+    n: Tuple[int, ...]
+    lo: Tuple[float, ...]
+    hi: Tuple[float, ...]
+    a0: float
+    a1: float
+    b1: float
+    a2: float
+    a3: float
+    b3: float
+    a4: float
+    b4: float
+    a5: float
+
+    @property
+    def d(self) -> int:
+        return len(self.n)
+
+    @property
+    def N(self) -> int:
+        return int(np.prod(self.n))
+
+    @property
+    def bc(self):
+        return (PERIODIC,) * self.d
+
+    @property
+    def periodic(self) -> bool:
+        return True
+
+
+def coupled_problem(n1: int = 700, n2: int = 350) -> CoupledProblem:
+    """The paper's coupled workload (Sec. 4.5): (0, 70) x (0, 35), a0 = -0.4,
+    a5 = 0.5, a1 = 0.125, b1 = 0.5, a2 = -0.9, a3 = 1, b3 = 0.8, a4 = -0.1,
+    b4 = -0.6, n = 700 x 350 (other sizes keep the domain)."""
+    return CoupledProblem((n1, n2), (0.0, 0.0), (70.0, 35.0), -0.4, 0.125, 0.5, -0.9, 1.0, 0.8, -0.1, -0.6, 0.5)
+
+
+def coupled_u0(prob: CoupledProblem, seed: int = SEED_BASE + 5) -> np.ndarray:
+    """Two quasi-1D solitons approaching each other: u0(x1, x2) = w0(x1) and
+    v0(x1, x2) = w0(L1 - x1), w0 = delta exp(-(x1 - chi)^2 / (2 sigma^2)) with
+    the paper's delta = 2.25, chi = 17.5, sigma = 2.5 (the seed of its 1D
+    relaxation run, standing in for the relaxed soliton), times (1 + 1e-3 xi)
+    with xi complex N(0,1) noise so the x2 direction is not exactly uniform.
+    Returns W of shape (2, n1, n2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x1 = nodes(prob.n[0], prob.lo[0], prob.hi[0], PERIODIC)
+    L1 = prob.hi[0] - prob.lo[0]
+    w = lambda x: 2.25 * np.exp(-((x - 17.5) ** 2) / (2 * 2.5 ** 2))
+    shape = tuple(prob.n)
+    u = w(x1)[:, None] * np.ones(shape[1:])[None, :]
+    v = w(L1 - x1)[:, None] * np.ones(shape[1:])[None, :]
+    u = u * (1 + 1e-3 * complex_noise(rng, shape))
+    v = v * (1 + 1e-3 * complex_noise(rng, shape))
+    return np.stack([u, v]).astype(complex)

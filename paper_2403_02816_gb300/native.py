@@ -82,6 +82,8 @@ def load() -> ctypes.CDLL:
                                 ctypes.POINTER(D), D, D, D, D, D, D, D, D, I, I, VP]),
         "cgl_plan_create_ex": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I64), ctypes.POINTER(VP), D, D, D, D, D, I,
                                    I, VP]),
+        "cgl_plan_create_coupled": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I64), ctypes.POINTER(D),
+                                        ctypes.POINTER(D), D, D, D, D, D, D, D, D, D, D, I, I, VP]),
         "cgl_fd4_matrix": (I, [I, D, D, I, ctypes.POINTER(D)]),
         "cgl_step": (I, [P, VP, I64, VP]),
         "cgl_step_host": (I, [P, VP, I64, VP]),
@@ -218,6 +220,8 @@ def cgl_measure_fma_peak(precision, iters, stream=None):
 class Plan:
     """A libcgl plan for one problem, step size, scheme and precision."""
 
+    nfield = 1  # fields in the state (the coupled system has two)
+
     def __init__(self, prob, tau: float, scheme: str, precision: str = "f64", stream=None):
         self.prob = prob
         self.scheme = scheme
@@ -246,7 +250,8 @@ class Plan:
     # torch helpers -------------------------------------------------------
     @property
     def shape(self):
-        return tuple(reversed(self.prob.n))
+        n = tuple(reversed(self.prob.n))
+        return n if self.nfield == 1 else (self.nfield,) + n
 
     @property
     def dtype(self):
@@ -254,9 +259,9 @@ class Plan:
         return torch.complex128 if self.prec == CGL_F64 else torch.complex64
 
     def _field(self, u):
-        if not u.is_cuda or not u.is_contiguous() or u.dtype != self.dtype or u.numel() != self.prob.N:
-            raise ValueError("field must be a contiguous %s CUDA tensor with %d elements"
-                             % (self.dtype, self.prob.N))
+        count = self.nfield * self.prob.N
+        if not u.is_cuda or not u.is_contiguous() or u.dtype != self.dtype or u.numel() != count:
+            raise ValueError("field must be a contiguous %s CUDA tensor with %d elements" % (self.dtype, count))
         return ctypes.c_void_p(u.data_ptr())
 
     def step(self, u, nsteps: int, stream=None):
@@ -326,6 +331,41 @@ def to_device(U, dtype, device="cuda"):
     import torch
     t = torch.from_numpy(np.ascontiguousarray(U.T))
     return t.to(dtype).to(device).contiguous()
+
+
+def to_device_pair(W, dtype, device="cuda"):
+    """numpy (2, n_1..n_d) (u, v) -> contiguous torch tensor (2, n_d..n_1)."""
+    import torch
+    return torch.stack([to_device(W[0], dtype, device), to_device(W[1], dtype, device)]).contiguous()
+
+
+def from_device_pair(t):
+    """torch tensor (2, n_d..n_1) -> complex128 numpy array (2, n_1..n_d)."""
+    import numpy as np
+    return np.stack([from_device(t[0]), from_device(t[1])])
+
+
+class CoupledPlan(Plan):
+    """Plan of the coupled two-field system (cgl_plan_create_coupled).  `prob`
+    carries n, lo, hi and a0, a1, b1, a2, a3, b3, a4, b4, a5; the state is a
+    tensor of shape (2, n_d, ..., n_1): u, then v."""
+
+    nfield = 2
+
+    def __init__(self, prob, tau: float, scheme: str, precision: str = "f64", stream=None):
+        self.prob = prob
+        self.scheme = scheme
+        self.precision = precision
+        self.prec = PRECISIONS[precision]
+        lib = load()
+        h = ctypes.c_void_p()
+        d = len(prob.n)
+        st = lib.cgl_plan_create_coupled(ctypes.byref(h), d, (ctypes.c_int64 * d)(*prob.n),
+                                         (ctypes.c_double * d)(*prob.lo), (ctypes.c_double * d)(*prob.hi),
+                                         prob.a0, prob.a1, prob.b1, prob.a2, prob.a3, prob.b3, prob.a4, prob.b4,
+                                         prob.a5, float(tau), SCHEMES[scheme], self.prec, _stream_handle(stream))
+        self.handle = h
+        check(st, "cgl_plan_create_coupled")
 
 
 def from_device(t):

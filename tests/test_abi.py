@@ -56,7 +56,7 @@ def create(**kw):
     (dict(scheme=99), nat.CGL_EINVAL),
     (dict(precision=7), nat.CGL_EINVAL),
     (dict(bc=[2, 0]), nat.CGL_EUNSUPPORTED),
-    (dict(bc=[2, 2], n=[8, 12]), nat.CGL_EUNSUPPORTED),
+    (dict(bc=[2, 2], n=[8, 22]), nat.CGL_EUNSUPPORTED),
     (dict(bc=[2, 2], n=[8, 4096]), nat.CGL_EUNSUPPORTED),
     (dict(n=[8, 2048]), nat.CGL_EUNSUPPORTED),
     (dict(scheme=8), nat.CGL_EINVAL),
@@ -98,3 +98,33 @@ def test_batch_validation_before_any_cuda_call(lib):
     assert lib.cgl_batch_create(ctypes.byref(h), 1, arr, 0.01, nat.CGL_LAWSON4, 7, None) == nat.CGL_EINVAL
     assert lib.cgl_batch_destroy(None) == nat.CGL_OK
     assert lib.cgl_autotune_mode_tile(1, 1, 0, 1, None, None) == nat.CGL_EINVAL
+
+
+def coupled_create(**kw):
+    base = dict(d=2, n=[70, 35], lo=[0.0, 0.0], hi=[70.0, 35.0], a0=-0.4, a1=0.125, b1=0.5, a2=-0.9, a3=1.0,
+                b3=0.8, a4=-0.1, b4=-0.6, a5=0.5, tau=0.01, scheme=nat.CGL_SPLIT4, precision=nat.CGL_F64)
+    base.update(kw)
+    lib = nat.load()
+    h = ctypes.c_void_p()
+    d = base["d"]
+    st = lib.cgl_plan_create_coupled(ctypes.byref(h), d, (ctypes.c_int64 * max(d, 1))(*base["n"]),
+                                     (ctypes.c_double * max(d, 1))(*base["lo"]),
+                                     (ctypes.c_double * max(d, 1))(*base["hi"]), base["a0"], base["a1"], base["b1"],
+                                     base["a2"], base["a3"], base["b3"], base["a4"], base["b4"], base["a5"],
+                                     base["tau"], base["scheme"], base["precision"], None)
+    return st, h
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(a0=float("nan")), nat.CGL_EINVAL),
+    (dict(a5=float("inf")), nat.CGL_EINVAL),
+    (dict(d=4, n=[8] * 4, lo=[0.0] * 4, hi=[1.0] * 4), nat.CGL_EINVAL),
+    (dict(scheme=nat.CGL_LAWSON4), nat.CGL_EUNSUPPORTED),
+    (dict(precision=nat.CGL_BF16X3), nat.CGL_EUNSUPPORTED),
+    (dict(n=[70, 22]), nat.CGL_EUNSUPPORTED),
+    (dict(a1=0.0), nat.CGL_EINVAL),
+])
+def test_coupled_plan_validation_before_any_cuda_call(lib, kw, status):
+    st, h = coupled_create(**kw)
+    assert st == status
+    assert not h.value
