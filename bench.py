@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="periodic128",
-                    choices=["periodic128", "periodic256_f32", "neumann256", "stencil256", "batch512", "corrector"],
+                    choices=["periodic128", "periodic256_f32", "neumann256", "stencil256", "batch512", "corrector",
+                             "coupled700x350"],
                     help="periodic128: the headline 3D periodic workload; periodic256_f32: the same "
                          "problem at 256^3 in complex64 (HBM roofline, cuFFT yardstick); neumann256: the 3D "
                          "Neumann precision study (FP64 / FP32 / BF16x3 tensor cores)")
@@ -376,6 +377,113 @@ def run_neumann256(args):
     print(json.dumps(line))
 
 
+# the paper's coupled run (Sec. 4.5): split4 with 500 steps to T = 3 on
+# N = 700 x 350 took 85.5 s (MATLAB FP64 on a 6-core laptop CPU)
+PAPER_COUPLED_SPLIT4 = 700 * 350 * 500 / 85.5
+
+
+def run_coupled(args):
+    """Coupled two-field cubic-quintic system on the paper's 700 x 350
+    periodic grid (Sec. 4.5, its parameters and a soliton-pair initial
+    state), tau = 3/500 (its coarsest split4 step): split4 and Strang in FP64
+    and FP32 (grid points N = 700 x 350 per time step, as the paper counts
+    degrees of freedom), per-kernel timing of the mixed-radix FFT passes,
+    the FP64 split4 result against the oracle after two steps, end to end
+    through host buffers, and the oracle on one host core (one step, also
+    the parity check of one GPU step)."""
+    import torch
+    from oracle import coupled_oracle as C
+    from paper_2403_02816_gb300 import native as nat
+
+    dev = torch.device("cuda", 0)
+    nat.load()
+    p = I.coupled_problem()
+    W0 = I.coupled_u0(p)
+    N = p.N
+    tau, chunk = 3.0 / 500, args.chunk
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res, prof = {}, None
+    launches = 0
+    with Clocks(0) as clk:
+        for prec in ("f64", "f32"):
+            dt = torch.complex128 if prec == "f64" else torch.complex64
+            for scheme in ("split4", "strang"):
+                with nat.CoupledPlan(p, tau, scheme, prec) as plan:
+                    w = nat.to_device_pair(W0, dt, dev)
+                    for _ in range(max(args.warmup, 3)):
+                        plan.step(w, chunk)
+                    torch.cuda.synchronize()
+                    ms = 0.0
+                    for _ in range(args.steps):
+                        flush.fill_(1.0)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        plan.step(w, chunk)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        ms += e0.elapsed_time(e1)
+                    ms /= args.steps * chunk
+                    res["%s_%s" % (scheme, prec)] = {"grid_pt_steps_per_s": N / (ms / 1e3), "ms_per_time_step": ms,
+                                                     "launches_per_step": plan.info()["launches_per_step"],
+                                                     "device_status": plan.device_status()}
+                    if prec == "f64" and scheme == "split4":
+                        launches = plan.info()["launches_per_step"] * chunk * args.steps
+                        prof = plan.profile(w, 1)
+    head = res["split4_f64"]
+    dom = max(prof, key=lambda r: r["total_ms"])
+    achieved = dom["flops"] / (dom["total_ms"] / 1e3) / 1e12
+    peak = fp64_peak_tflops()
+    # cpu_baseline leg: one FP64 split4 step of the oracle on one host core,
+    # its result also compared with one GPU step
+    with nat.CoupledPlan(p, tau, "split4", "f64") as plan:
+        w = nat.to_device_pair(W0, torch.complex128, dev)
+        plan.step(w, 1)
+        got = nat.from_device_pair(w)
+    t0 = time.perf_counter()
+    ref = C.integrate(C.CoupledProblem(p.n, p.lo, p.hi, p.a0, p.a1, p.b1, p.a2, p.a3, p.b3, p.a4, p.b4, p.a5),
+                      W0, tau, 1, "split4")
+    cpu_s = time.perf_counter() - t0
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    # end to end through the C ABI with pinned host buffers (u and v)
+    with nat.CoupledPlan(p, tau, "split4", "f64") as plan:
+        host = torch.from_numpy(np.ascontiguousarray(np.stack([W0[0].T, W0[1].T]))).pin_memory()
+        plan.step_host(host, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.step_host(host, chunk)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+    line = {
+        "metric": METRIC, "value": head["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_time_step"] * chunk, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "coupled_cubicquintic_periodic_700x350_c128", "scheme": "split4", "tau": tau,
+                   "grid": list(p.n), "fields": 2, "time_steps_per_bench_step": chunk,
+                   "l2": "flushed (256 MiB write) between timed iterations",
+                   "data": "the paper's parameters; soliton pair from the Gaussian seed of its 1D relaxation run"},
+        "results": res,
+        "rel_l2_vs_oracle_1step": err,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": dom["name"] + " (mixed radix 700 = 4.5.5.7, 350 = 2.5.5.7)",
+                     "launches_profiled": dom["launches"], "avg_launch_ms": dom["total_ms"] / dom["launches"],
+                     "flops_counted": "5 n log2 n per transform, 6 per symbol multiply, nonlinear operators",
+                     "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                     "share": dom["total_ms"] / sum(r["total_ms"] for r in prof)},
+        "cpu_baseline": {"value": N / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "1 split4 time step of the 700x350 coupled system (numpy FP64, single thread)"},
+        "e2e": {"value": N * chunk * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * N * 16,
+                "d2h_bytes_per_step": 2 * N * 16},
+        "gpu_launches": launches,
+        "paper_context": {"note": "the paper's split4 run on this grid (500 steps, 85.5 s; MATLAB FP64 on a 6-core "
+                                  "laptop CPU)", "grid_pt_steps_per_s": PAPER_COUPLED_SPLIT4,
+                          "ratio": head["grid_pt_steps_per_s"] / PAPER_COUPLED_SPLIT4},
+        "kernels": prof, "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def run_periodic_f32(args):
     """3D cubic-quintic periodic 256^3 (the 128^3 workload's parameters and
     initial data on a finer grid), split4, tau = 0.005, in complex64 and in
@@ -664,6 +772,9 @@ def main():
         return
     if args.workload == "neumann256":
         run_neumann256(args)
+        return
+    if args.workload == "coupled700x350":
+        run_coupled(args)
         return
     if args.workload == "periodic256_f32":
         run_periodic_f32(args)

@@ -18,6 +18,7 @@ namespace cgl {
 
 constexpr int kFftThreads = 256;
 constexpr int kFftTile = 2048;  // complex elements of one field per CTA (8 per thread)
+constexpr int kFftTileMR = 1024;  // mixed radix: smaller tiles, more CTAs on small grids
 constexpr int kFftMaxSmem = 200 * 1024;
 
 template <class T2> __device__ __forceinline__ void dft2(T2* x) {
@@ -184,16 +185,33 @@ __device__ __forceinline__ void mr_stage(const T2* src, T2* dst, int nrhs_tiles,
       } else if constexpr (R == 4) {
         dft4(x, inv);
       } else {
-        T2 y[R];
+        // odd R: with a_r = x_r + x_(R-r), b_r = x_r - x_(R-r) and
+        // w^(r m) = c + i s (the table's sign for this direction),
+        // y_m = x_0 + sum_r (c a_r + i s b_r) and y_(R-m) = x_0 + sum_r (c a_r - i s b_r)
+        constexpr int H = (R - 1) / 2;
+        T2 a[H], b[H];
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-          T2 acc = x[0];
-#pragma unroll
-          for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(x[r], tw[((r * m) % R) * rstep]));
-          y[m] = acc;
+        for (int r = 1; r <= H; ++r) {
+          a[r - 1] = cadd(x[r], x[R - r]);
+          b[r - 1] = csub(x[r], x[R - r]);
         }
+        T2 y0 = x[0];
 #pragma unroll
-        for (int m = 0; m < R; ++m) x[m] = y[m];
+        for (int r = 0; r < H; ++r) y0 = cadd(y0, a[r]);
+#pragma unroll
+        for (int m = 1; m <= H; ++m) {
+          T2 A = x[0], B = mk<T2>(0, 0);
+#pragma unroll
+          for (int r = 1; r <= H; ++r) {
+            const T2 w = tw[((r * m) % R) * rstep];
+            A = mk<T2>(fma(w.x, a[r - 1].x, A.x), fma(w.x, a[r - 1].y, A.y));
+            B = mk<T2>(fma(w.y, b[r - 1].x, B.x), fma(w.y, b[r - 1].y, B.y));
+          }
+          // i B = (-B.y, B.x)
+          x[m] = mk<T2>(A.x - B.y, A.y + B.x);
+          x[R - m] = mk<T2>(A.x + B.y, A.y - B.x);
+        }
+        x[0] = y0;
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) dst[rr * tile_stride + dso + r * p] = x[r];
@@ -233,7 +251,7 @@ __device__ __forceinline__ void fft_pass_body(const FftPassArgs& a, unsigned cha
   using T2 = typename C2<T>::type;
   const int n = (int)a.g.n_ax;
   const int logn = __ffs(n) - 1;  // power-of-two passes only
-  const int tbmax = max(1, kFftTile / n);
+  const int tbmax = max(1, (MR ? kFftTileMR : kFftTile) / n);
   const int pitch = n + 1;
   const int tile_stride = tbmax * pitch;
   const int64_t b0 = (int64_t)blockIdx.x * tbmax;
@@ -727,7 +745,7 @@ static cudaError_t fft4_dispatch(int logn, bool prepare, const FftPassArgs* a, c
 }
 
 static size_t fft_smem_bytes(int n, int nrhs, size_t elem, bool mr = false) {
-  const int tbmax = std::max(1, kFftTile / n);
+  const int tbmax = std::max(1, (mr ? kFftTileMR : kFftTile) / n);
   const int pitch = n + 1;
   // tiles (two when mixed radix) | pencil factors | pencil bases | twiddles:
   // [2][n][3] of T + forms [2][n], or plain [2][n] of T2 (mixed radix)
@@ -741,9 +759,10 @@ bool fft_is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 template <class T> cudaError_t launch_fft_pass(const FftPassArgs& a, cudaStream_t s) {
   using T2 = typename C2<T>::type;
   const int n = (int)a.g.n_ax;
-  const int tbmax = std::max(1, kFftTile / n);
+  const bool mr = !fft_is_pow2(n);
+  const int tbmax = std::max(1, (mr ? kFftTileMR : kFftTile) / n);
   const int64_t grid = (a.g.npencils + tbmax - 1) / tbmax;
-  if (!fft_is_pow2(n)) {
+  if (mr) {
     const size_t smem = fft_smem_bytes(n, a.f.nrhs, sizeof(T2), true);
     if (smem > kFftMaxSmem || !a.twplain) return cudaErrorInvalidValue;
     if (a.f.nrhs > 1)
