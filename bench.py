@@ -385,8 +385,9 @@ PAPER_COUPLED_SPLIT4 = 700 * 350 * 500 / 85.5
 def run_coupled(args):
     """Coupled two-field cubic-quintic system on the paper's 700 x 350
     periodic grid (Sec. 4.5, its parameters and a soliton-pair initial
-    state), tau = 3/500 (its coarsest split4 step): split4 and Strang in FP64
-    and FP32 (grid points N = 700 x 350 per time step, as the paper counts
+    state), tau = 3/500 (its coarsest split4 step): split4, Lawson4 (if4),
+    Strang and Lawson2 (if2) in FP64 and FP32 (grid points N = 700 x 350 per
+    time step, as the paper counts
     degrees of freedom), per-kernel timing of the mixed-radix FFT passes,
     the FP64 split4 result against the oracle after two steps, end to end
     through host buffers, and the oracle on one host core (one step, also
@@ -408,7 +409,7 @@ def run_coupled(args):
     with Clocks(0) as clk:
         for prec in ("f64", "f32"):
             dt = torch.complex128 if prec == "f64" else torch.complex64
-            for scheme in ("split4", "strang"):
+            for scheme in ("split4", "lawson4", "strang", "lawson2"):
                 with nat.CoupledPlan(p, tau, scheme, prec) as plan:
                     w = nat.to_device_pair(W0, dt, dev)
                     for _ in range(max(args.warmup, 3)):

@@ -90,6 +90,8 @@ double pro_flops(const cgl_plan* p, const OpArgs& o) {
     case PRO_CQ: return 40;
     case PRO_CQ2: return 80;
     case PRO_CFLOW: return 160;  // one coupled RK4 step: 4 x (g_u, g_v) + combinations
+    case PRO_CG: return 34;
+    case PRO_CLAW2: return 42;
     default: return 0;
   }
 }
@@ -107,6 +109,10 @@ double epi_flops(const cgl_plan* p, const OpArgs& o) {
     case EPI_SPLIT4_3T: return 44;
     case EPI_CFLOW: return 160;
     case EPI_CSPLIT4: return 168;
+    case EPI_CLAW4P: return 84;
+    case EPI_CLAW4W: return 96;
+    case EPI_CLAW4B:
+    case EPI_CLAW2: return 42;
     default: return 0;
   }
 }
@@ -522,6 +528,40 @@ void build_program(cgl_plan* p) {
       s.op.pro = PRO_CFLOW; s.op.t0 = tau / 2;
       s.op.epi = EPI_CFLOW; s.op.te = tau / 2;
       p->sweeps.push_back(s);
+    } else if (p->scheme == CGL_LAWSON4) {
+      // eq. lawson4 with E = exp(tau K / 2) (factor pair k = 0), each sweep
+      // carrying u and v: a = E W; p and w from b = E g(W) and a; q = E p;
+      // W_{n+1} = E w + tau/6 g(q)
+      Sweep s1 = base();
+      pair(s1, BUF_U, BUF_W0, BUF_W0, 0);  // a -> W0
+      Sweep s2 = base();
+      pair(s2, BUF_U, BUF_W1, BUF_W1, 0);  // p -> W1
+      s2.op.pro = PRO_CG;
+      s2.op.epi = EPI_CLAW4P;
+      s2.nextra = 2; s2.extra[0] = s2.extra[1] = BUF_W0; s2.extra_f[0] = 0; s2.extra_f[1] = 1;
+      Sweep s3 = s2;  // w -> W2
+      pair(s3, BUF_U, BUF_W2, BUF_W2, 0);
+      s3.op.epi = EPI_CLAW4W;
+      Sweep s4 = base();
+      pair(s4, BUF_W1, BUF_W0, BUF_W0, 0);  // q = E p -> W0 (a is no longer read)
+      Sweep s5 = base();
+      pair(s5, BUF_W2, BUF_U, BUF_U, 0);  // E w + tau/6 g(q) -> W
+      s5.op.epi = EPI_CLAW4B;
+      s5.nextra = 2; s5.extra[0] = s5.extra[1] = BUF_W0; s5.extra_f[0] = 0; s5.extra_f[1] = 1;
+      for (Sweep* sw : {&s1, &s2, &s3, &s4, &s5}) p->sweeps.push_back(*sw);
+    } else if (p->scheme == CGL_LAWSON2) {
+      // eq. lawson2b with E = exp(tau K): v = E(W + tau g(W)) -> W0;
+      // W_{n+1} = E(W + tau/2 g(W)) + tau/2 g(v)
+      Sweep s1 = base();
+      pair(s1, BUF_U, BUF_W0, BUF_W0, 0);
+      s1.op.pro = PRO_CLAW2; s1.op.t0 = tau;
+      Sweep s2 = base();
+      pair(s2, BUF_U, BUF_U, BUF_U, 0);
+      s2.op.pro = PRO_CLAW2; s2.op.t0 = tau / 2;
+      s2.op.epi = EPI_CLAW2;
+      s2.nextra = 2; s2.extra[0] = s2.extra[1] = BUF_W0; s2.extra_f[0] = 0; s2.extra_f[1] = 1;
+      p->sweeps.push_back(s1);
+      p->sweeps.push_back(s2);
     } else {  // eq. Richardson: c = 1 (k = 0), c = 1/2 (k = 1)
       Sweep s1 = base();  // u_{n2} = phi_{tau/2}(E_1 phi_{tau/2}(W)) -> W0
       pair(s1, BUF_U, BUF_W0, BUF_W0, 0);
@@ -763,8 +803,8 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   if (coupled) {
     if (!finite_all({coupled[0], coupled[1]})) return fail(CGL_EINVAL, "parameters must be finite");
     if (nper != d) return fail(CGL_EUNSUPPORTED, "the coupled system is periodic (Fourier) only");
-    if (scheme != CGL_STRANG && scheme != CGL_SPLIT4)
-      return fail(CGL_EUNSUPPORTED, "the coupled system supports strang and split4");
+    if (scheme != CGL_STRANG && scheme != CGL_SPLIT4 && scheme != CGL_LAWSON4 && scheme != CGL_LAWSON2)
+      return fail(CGL_EUNSUPPORTED, "the coupled system supports strang, split4, lawson4 and lawson2");
     if (precision == CGL_BF16X3) return fail(CGL_EUNSUPPORTED, "the coupled system runs in CGL_F64 or CGL_F32");
   }
   const bool periodic = nper == d;
@@ -845,6 +885,7 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
         p->adv[2 * k + f] = f == 0 ? p->a0 : -p->a0;
       }
     p->nfac = 2 * nc;
+    if (scheme == CGL_LAWSON4) p->nwork = 3;  // a (then q), p, w
   }
   cudaStream_t s = (cudaStream_t)stream;
   int st = CGL_OK;

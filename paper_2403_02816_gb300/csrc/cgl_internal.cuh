@@ -56,7 +56,9 @@ enum ProOp : int {
   PRO_LAW2 = 4,    // z0 = in0 + tau g(in0), z1 = in0 + tau/2 g(in0)   (Lawson2)
   PRO_CQ = 5,      // z0 = phi^c_{t0}(phi^q_{t0}(in0))                 (strang_3t)
   PRO_CQ2 = 6,     // z0 = phi^c_{t0}(phi^q_{t0}(in0)), z1 likewise t1 (split4_3t, first sweep)
-  PRO_CFLOW = 7    // (z0, z1) = phi_{t0}(in0, in1): coupled system, u and v (eq. coupled)
+  PRO_CFLOW = 7,   // (z0, z1) = phi_{t0}(in0, in1): coupled system, u and v (eq. coupled)
+  PRO_CG = 8,      // (z0, z1) = g(in0, in1)                           (coupled Lawson4)
+  PRO_CLAW2 = 9    // (z0, z1) = (in0, in1) + t0 g(in0, in1)           (coupled Lawson2)
 };
 enum EpiOp : int {
   EPI_NONE = 0,    // out_r = y_r
@@ -72,7 +74,11 @@ enum EpiOp : int {
                    // out1 = phi^c_{t/2}(phi^q_t(phi^c_{t/2}(y1)))
   EPI_SPLIT4_3T = 10, // out0 = 4/3 phi^q_t(phi^c_t(y0)) - 1/3 e0      (split4_3t, second sweep)
   EPI_CFLOW = 11,     // (out0, out1) = phi_t(y0, y1)                  (coupled system)
-  EPI_CSPLIT4 = 12    // (out0, out1) = 4/3 phi_t(y0, y1) - 1/3 (e0, e1) (coupled split4)
+  EPI_CSPLIT4 = 12,   // (out0, out1) = 4/3 phi_t(y0, y1) - 1/3 (e0, e1) (coupled split4)
+  EPI_CLAW4P = 13,    // b = y, a = e -> p = a + tau g(u3)            (coupled Lawson4)
+  EPI_CLAW4W = 14,    // b = y, a = e -> w = a + tau/6 b + tau/3 (g(u2) + g(u3))
+  EPI_CLAW4B = 15,    // r = y, q = e -> r + tau/6 g(q)
+  EPI_CLAW2 = 16      // w = y, v = e -> w + tau/2 g(v)               (coupled Lawson2)
 };
 
 // Nonlinear model parameters (eq. 1) and the per-pass operator constants.
@@ -225,6 +231,17 @@ __device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2
       z[1] = in[1];
       nl_flow2<T, T2>(o.nl, z[0], z[1], pv<T>(o.t0, o.t0f));
       break;
+    case PRO_CG:
+      nl_g2<T, T2>(o.nl, in[0], in[1], z[0], z[1]);
+      break;
+    case PRO_CLAW2: {
+      T2 g0, g1;
+      nl_g2<T, T2>(o.nl, in[0], in[1], g0, g1);
+      const T t0 = pv<T>(o.t0, o.t0f);
+      z[0] = caxpy(in[0], t0, g0);
+      z[1] = caxpy(in[1], t0, g1);
+      break;
+    }
     case PRO_LAW2: {
       const T2 gn = nl_g<T, T2>(o.nl, in[0]);
       const T tau = pv<T>(o.nl.tau, o.nl.tauf);
@@ -329,6 +346,28 @@ __device__ __forceinline__ int apply_epilogue(const OpArgs& o, const T2* y, cons
                       fma(T(4) / T(3), f0.y, -(T(1) / T(3)) * e[0].y));
       out[1] = mk<T2>(fma(T(4) / T(3), f1.x, -(T(1) / T(3)) * e[1].x),
                       fma(T(4) / T(3), f1.y, -(T(1) / T(3)) * e[1].y));
+      return 2;
+    }
+    case EPI_CLAW4P:
+    case EPI_CLAW4W: {
+      // Lawson4 on the pair with E = exp(tau K / 2): a = E W (extras), b =
+      // E g(W) (this sweep); u2 = a + tau/2 b, u3 = a + tau/2 g(u2)
+      T2 g2[2], g3[2];
+      nl_g2<T, T2>(o.nl, caxpy(e[0], tau * T(0.5), y[0]), caxpy(e[1], tau * T(0.5), y[1]), g2[0], g2[1]);
+      nl_g2<T, T2>(o.nl, caxpy(e[0], tau * T(0.5), g2[0]), caxpy(e[1], tau * T(0.5), g2[1]), g3[0], g3[1]);
+      for (int f = 0; f < 2; ++f)
+        out[f] = o.epi == EPI_CLAW4P
+                     ? caxpy(e[f], tau, g3[f])
+                     : caxpy(caxpy(e[f], tau * (T(1) / T(6)), y[f]), tau * (T(1) / T(3)), cadd(g2[f], g3[f]));
+      return 2;
+    }
+    case EPI_CLAW4B:
+    case EPI_CLAW2: {
+      T2 g0, g1;
+      nl_g2<T, T2>(o.nl, e[0], e[1], g0, g1);
+      const T c = o.epi == EPI_CLAW4B ? tau * (T(1) / T(6)) : tau * T(0.5);
+      out[0] = caxpy(y[0], c, g0);
+      out[1] = caxpy(y[1], c, g1);
       return 2;
     }
     default:

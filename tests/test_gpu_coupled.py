@@ -114,7 +114,7 @@ def test_coupled_linear_flow(n, prec):
 
 
 @pytest.mark.parametrize("n", COUPLED_SHAPES)
-@pytest.mark.parametrize("scheme", ["strang", "split4"])
+@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_coupled_schemes_match_oracle(n, scheme, prec):
     rng = np.random.default_rng(6)
@@ -145,7 +145,7 @@ def test_coupled_mirror_symmetry_on_gpu():
     assert np.max(np.abs(got[1] - mirror(got[0]))) < 1e-12 * np.max(np.abs(got))
 
 
-@pytest.mark.parametrize("scheme", ["strang", "split4"])
+@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2"])
 def test_coupled_paper_grid_700x350(scheme):
     """The paper's 700 x 350 grid, parameters and soliton-pair data, 3 steps
     of tau = 3/500 (its coarsest split4 step), FP64 against the oracle."""
