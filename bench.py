@@ -431,6 +431,21 @@ def run_coupled(args):
                     if prec == "f64" and scheme == "split4":
                         launches = plan.info()["launches_per_step"] * chunk * args.steps
                         prof = plan.profile(w, 1)
+    # explicit RK4 at the paper's finest RK4 step (3/2562, inside its stability limit)
+    with nat.CoupledPlan(p, 3.0 / 2562, "rk4", "f64") as plan:
+        w = nat.to_device_pair(W0, torch.complex128, dev)
+        for _ in range(max(args.warmup, 3)):
+            plan.step(w, chunk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.step(w, chunk * args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (chunk * args.steps)
+        res["rk4_f64_tau_3/2562"] = {"grid_pt_steps_per_s": N / (ms / 1e3), "ms_per_time_step": ms,
+                                     "launches_per_step": plan.info()["launches_per_step"],
+                                     "device_status": plan.device_status()}
     head = res["split4_f64"]
     dom = max(prof, key=lambda r: r["total_ms"])
     achieved = dom["flops"] / (dom["total_ms"] / 1e3) / 1e12

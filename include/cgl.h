@@ -144,9 +144,11 @@ int cgl_plan_create_ex(cgl_plan** out, int d, const int64_t* n, const double* co
  * symbol, the advection term i (+-a0) kappa_1 on direction 1 (0 at the
  * Nyquist mode of an even n_1, which keeps the system's mirror symmetry
  * x1 -> L - x1, u <-> v).  The nonlinear sub-flow is one RK4 step of the
- * coupled pointwise system.  scheme: CGL_STRANG, CGL_SPLIT4, CGL_LAWSON4 or
- * CGL_LAWSON2, each as a chain of sweeps that carry u and v together
- * (others EUNSUPPORTED); precision: CGL_F64 or CGL_F32.
+ * coupled pointwise system.  scheme: CGL_STRANG, CGL_SPLIT4, CGL_LAWSON4,
+ * CGL_LAWSON2 (chains of sweeps that carry u and v together), CGL_RK4 or
+ * CGL_RK2 (one sweep per field and stage; explicit, so tau must respect their
+ * stability limit); the three-term splittings give EUNSUPPORTED.  precision:
+ * CGL_F64 or CGL_F32.
  * The field passed to cgl_step / cgl_step_host holds u (N values) followed
  * by v (N values), each in the single-field layout; cgl_linear_flow applies
  * exp(c tau K) to both.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA.

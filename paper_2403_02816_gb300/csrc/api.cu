@@ -163,7 +163,7 @@ ModePassArgs make_mode_args(const cgl_plan* p, const Sweep& sw, int mu, void* co
     a.f.work[r] = slot_ptr(p, bufs, sw.work[r], sw.work_f[r]);
     a.f.out[r] = slot_ptr(p, bufs, sw.out[r], sw.out_f[r]);
   }
-  for (int x = 0; x < 3; ++x) a.f.extra[x] = slot_ptr(p, bufs, sw.extra[x], sw.extra_f[x]);
+  for (int x = 0; x < kMaxExtra; ++x) a.f.extra[x] = slot_ptr(p, bufs, sw.extra[x], sw.extra_f[x]);
   a.op = sw.op;
   a.flags = (mu == 0 ? PASS_PRO : 0) | (mu == p->d - 1 ? PASS_EPI : 0);
   for (int r = 0; r < 2; ++r) a.factor[r] = p->fac[sw.fac[r < sw.nrhs ? r : 0]][mu];
@@ -183,7 +183,7 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
     f.work[r] = slot_ptr(p, bufs, sw.work[r], sw.work_f[r]);
     f.out[r] = slot_ptr(p, bufs, sw.out[r], sw.out_f[r]);
   }
-  for (int x = 0; x < 3; ++x) f.extra[x] = slot_ptr(p, bufs, sw.extra[x], sw.extra_f[x]);
+  for (int x = 0; x < kMaxExtra; ++x) f.extra[x] = slot_ptr(p, bufs, sw.extra[x], sw.extra_f[x]);
   const double Nd = (double)p->N;
   const double es = (double)p->elem;
   const bool f64 = p->precision == CGL_F64;
@@ -324,8 +324,9 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
     a.flags = passes[k].flags;
     for (int r = 0; r < sw.nrhs; ++r) {
       const int fi = sw.fac[r];
-      for (int m = 0; m < d; ++m) a.sym[r].vec[m] = (fi == FAC_K) ? p->ksym[m] : p->fac[fi][m];
-      a.sym[r].sum_form = (fi == FAC_K) ? 1 : 0;
+      for (int m = 0; m < d; ++m)
+        a.sym[r].vec[m] = (fi == FAC_K) ? p->ksym[m] : (fi == FAC_K2) ? p->ksym2[m] : p->fac[fi][m];
+      a.sym[r].sum_form = (fi == FAC_K || fi == FAC_K2) ? 1 : 0;
     }
     a.twiddle = p->twiddle[mu];
     a.twform = p->twform[mu];
@@ -485,10 +486,15 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
       if ((st = make_working(p, p->fac64[c][mu], n, &p->fac[c][mu], s))) return st;
     }
     if (p->scheme == CGL_RK4 || p->scheme == CGL_RK2) {
-      double2* k64 = nullptr;
-      if ((st = dev_alloc(p, (void**)&k64, n * sizeof(double2)))) return st;
-      CUDA_TRY(periodic_symbol_device(k64, n, L, 0.0, p->a1, p->b1, p->a2 / p->d, 0.0, 1.0 / (double)p->N, 1, s));
-      if ((st = make_working(p, k64, n, &p->ksym[mu], s))) return st;
+      // K symbols (sum form); the coupled system's u and v differ in the
+      // advection term on direction 1
+      for (int f = 0; f < p->nfield; ++f) {
+        const double adv = (mu == 0) ? (f == 0 ? p->a0 : -p->a0) : 0.0;
+        double2* k64 = nullptr;
+        if ((st = dev_alloc(p, (void**)&k64, n * sizeof(double2)))) return st;
+        CUDA_TRY(periodic_symbol_device(k64, n, L, 0.0, p->a1, p->b1, p->a2 / p->d, adv, 1.0 / (double)p->N, 1, s));
+        if ((st = make_working(p, k64, n, f == 0 ? &p->ksym[mu] : &p->ksym2[mu], s))) return st;
+      }
     }
     const size_t treal = p->precision == CGL_F64 ? sizeof(double) : sizeof(float);
     if ((st = dev_alloc(p, &p->twiddle[mu], 2 * 3 * (size_t)n * treal))) return st;
@@ -549,6 +555,37 @@ void build_program(cgl_plan* p) {
       s5.op.epi = EPI_CLAW4B;
       s5.nextra = 2; s5.extra[0] = s5.extra[1] = BUF_W0; s5.extra_f[0] = 0; s5.extra_f[1] = 1;
       for (Sweep* sw : {&s1, &s2, &s3, &s4, &s5}) p->sweeps.push_back(*sw);
+    } else if (p->scheme == CGL_RK4 || p->scheme == CGL_RK2) {
+      // eq. RK4 / RK2 on W' = K W + g(W): each stage is a sweep per field
+      // (K x_f with that field's symbol, FAC_K / FAC_K2) whose epilogue forms
+      // k_f = K x_f + g_f(x_f; x_other) and the stage update (extras: x_f,
+      // u_n, acc, x_other).  Stage arguments alternate between W0 and W1
+      // (x_1 = W), so the v sweep still reads the old x_u; acc lives in W2;
+      // each field's passes work in the next stage-argument slot.
+      const int stages = p->scheme == CGL_RK4 ? 4 : 2;
+      int xcur = BUF_U;
+      for (int st = 1; st <= stages; ++st) {
+        const int xnext = (xcur == BUF_W0) ? BUF_W1 : BUF_W0;
+        for (int f = 0; f < 2; ++f) {
+          Sweep s = base();
+          s.in[0] = xcur; s.in_f[0] = f;
+          s.fac[0] = f == 0 ? FAC_K : FAC_K2;
+          s.work[0] = xnext; s.work_f[0] = f;
+          s.op.epi = EPI_RK; s.op.rk_scheme = stages; s.op.rk_stage = st; s.op.rk_coupled = 1;
+          s.nextra = 4;
+          s.extra[0] = xcur; s.extra_f[0] = f;
+          s.extra[1] = BUF_U; s.extra_f[1] = f;
+          s.extra[2] = BUF_W2; s.extra_f[2] = f;
+          s.extra[3] = xcur; s.extra_f[3] = 1 - f;
+          if (st < stages) {
+            s.nout = 2; s.out[0] = xnext; s.out_f[0] = f; s.out[1] = BUF_W2; s.out_f[1] = f;
+          } else {
+            s.nout = 1; s.out[0] = BUF_U; s.out_f[0] = f;
+          }
+          p->sweeps.push_back(s);
+        }
+        xcur = xnext;
+      }
     } else if (p->scheme == CGL_LAWSON2) {
       // eq. lawson2b with E = exp(tau K): v = E(W + tau g(W)) -> W0;
       // W_{n+1} = E(W + tau/2 g(W)) + tau/2 g(v)
@@ -803,8 +840,8 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   if (coupled) {
     if (!finite_all({coupled[0], coupled[1]})) return fail(CGL_EINVAL, "parameters must be finite");
     if (nper != d) return fail(CGL_EUNSUPPORTED, "the coupled system is periodic (Fourier) only");
-    if (scheme != CGL_STRANG && scheme != CGL_SPLIT4 && scheme != CGL_LAWSON4 && scheme != CGL_LAWSON2)
-      return fail(CGL_EUNSUPPORTED, "the coupled system supports strang, split4, lawson4 and lawson2");
+    if (scheme == CGL_STRANG3T || scheme == CGL_SPLIT4_3T)
+      return fail(CGL_EUNSUPPORTED, "the coupled system has no three-term splittings");
     if (precision == CGL_BF16X3) return fail(CGL_EUNSUPPORTED, "the coupled system runs in CGL_F64 or CGL_F32");
   }
   const bool periodic = nper == d;

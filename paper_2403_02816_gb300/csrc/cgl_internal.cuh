@@ -17,7 +17,7 @@
 namespace cgl {
 
 constexpr int kMaxRhs = 2;
-constexpr int kMaxExtra = 3;
+constexpr int kMaxExtra = 4;
 
 // ---------------------------------------------------------------- complex
 
@@ -100,6 +100,7 @@ struct OpArgs {
   double te;       // epilogue flow time
   int rk_scheme;   // 4 or 2 (EPI_RK)
   int rk_stage;    // 1-based stage (EPI_RK)
+  int rk_coupled;  // EPI_RK of one field of the coupled system: e3 = the other field's stage argument
   NlParams nl;
   float t0f, t1f, tef;  // FP32 copies of t0, t1, te
 };
@@ -255,15 +256,25 @@ __device__ __forceinline__ void apply_prologue(const OpArgs& o, const T2* in, T2
   }
 }
 
+// g of one field of the coupled system given the other field: g_u(u; v) =
+// ((a3 + i b3)|u|^2 + (a4 + i b4)|u|^4 + a5 |v|^2) u (eq. coupled).
+template <class T, class T2> __device__ __forceinline__ T2 nl_g_cross(const NlParams& p, T2 u, T2 v) {
+  const T rho = fma(u.x, u.x, u.y * u.y), rv = fma(v.x, v.x, v.y * v.y);
+  const T cr = fma(rho, fma(pv<T>(p.a4, p.a4f), rho, pv<T>(p.a3, p.a3f)), pv<T>(p.a5, p.a5f) * rv);
+  const T ci = rho * fma(pv<T>(p.b4, p.b4f), rho, pv<T>(p.b3, p.b3f));
+  return mk<T2>(fma(cr, u.x, -ci * u.y), fma(cr, u.y, ci * u.x));
+}
+
 // Runge-Kutta stage epilogue on y = K x (eq. RK4 / eq. RK2):
-// extras e0 = x (stage argument), e1 = u_n, e2 = acc; outputs o0, o1.
+// extras e0 = x (stage argument), e1 = u_n, e2 = acc (coupled system: e3 =
+// the other field's stage argument, for g); outputs o0, o1.
 //   RK4 s=1..3: k = y + g(x); acc (+)= w_s k; x_next = u_n + c_{s+1} k  -> (x_next, acc)
 //   RK4 s=4   : u_{n+1} = u_n + tau/6 (acc + k)                        -> (u_{n+1})
 //   RK2 s=1   : acc = k; x_next = u_n + tau k ; s=2: u_n + tau/2 (acc + k)
 template <class T, class T2>
 __device__ __forceinline__ int rk_stage(const OpArgs& o, T2 y, const T2* e, T2* out) {
   const T tau = pv<T>(o.nl.tau, o.nl.tauf);
-  const T2 k = cadd(y, nl_g<T, T2>(o.nl, e[0]));
+  const T2 k = cadd(y, o.rk_coupled ? nl_g_cross<T, T2>(o.nl, e[0], e[3]) : nl_g<T, T2>(o.nl, e[0]));
   if (o.rk_scheme == 4) {
     switch (o.rk_stage) {
       case 1: out[1] = k; out[0] = caxpy(e[1], tau * T(0.5), k); return 2;

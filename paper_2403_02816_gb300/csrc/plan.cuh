@@ -15,18 +15,19 @@ namespace cgl {
 int fail(int status, const std::string& msg);
 
 enum { BUF_U = 0, BUF_W0 = 1, BUF_W1 = 2, BUF_W2 = 3, NBUF = 4 };
-constexpr int FAC_K = -1;  // the Runge-Kutta sweeps apply K, not an exponential
+constexpr int FAC_K = -1;   // the Runge-Kutta sweeps apply K, not an exponential
+constexpr int FAC_K2 = -2;  // ... the coupled system's v field (advection -a0)
 
 struct Sweep {
   int nin = 1, in[2] = {BUF_U, BUF_U};
   int nrhs = 1, fac[2] = {0, 0}, work[2] = {BUF_U, BUF_U};
-  int nextra = 0, extra[3] = {BUF_U, BUF_U, BUF_U};
+  int nextra = 0, extra[kMaxExtra] = {BUF_U, BUF_U, BUF_U, BUF_U};
   int nout = 1, out[2] = {BUF_U, BUF_U};
   OpArgs op{};
   bool stencil = false;  // FD Runge-Kutta stage: K x as a stencil + epilogue, one launch
   // field of each slot within its buffer (coupled system: 0 = u, 1 = v, N
   // values further)
-  int in_f[2] = {0, 0}, work_f[2] = {0, 0}, extra_f[3] = {0, 0, 0}, out_f[2] = {0, 0};
+  int in_f[2] = {0, 0}, work_f[2] = {0, 0}, extra_f[kMaxExtra] = {0, 0, 0, 0}, out_f[2] = {0, 0};
 };
 
 struct KernelStat {
@@ -68,6 +69,7 @@ struct cgl_plan {
   void* fac[4][3] = {{nullptr}};        // working-precision factors / symbol vectors
   double2* fac64[4][3] = {{nullptr}};   // FP64 masters
   void* ksym[3] = {nullptr};            // K symbol vectors (periodic Runge-Kutta)
+  void* ksym2[3] = {nullptr};           // the coupled system's v field
   void* twiddle[3] = {nullptr};         // FFT twiddle tables per axis: [fwd, inv][n][tau, m_re, m_im]
   int* twform[3] = {nullptr};           // [fwd, inv][n] twiddle form (0: m = cos, 1: m = sin)
   void* twplain[3] = {nullptr};         // mixed-radix axes: [fwd, inv][n] plain twiddles (T2)

@@ -119,8 +119,8 @@ def coupled_create(**kw):
     (dict(a0=float("nan")), nat.CGL_EINVAL),
     (dict(a5=float("inf")), nat.CGL_EINVAL),
     (dict(d=4, n=[8] * 4, lo=[0.0] * 4, hi=[1.0] * 4), nat.CGL_EINVAL),
-    (dict(scheme=nat.CGL_RK4), nat.CGL_EUNSUPPORTED),
     (dict(scheme=nat.CGL_SPLIT4_3T), nat.CGL_EUNSUPPORTED),
+    (dict(scheme=nat.CGL_STRANG3T), nat.CGL_EUNSUPPORTED),
     (dict(precision=nat.CGL_BF16X3), nat.CGL_EUNSUPPORTED),
     (dict(n=[70, 22]), nat.CGL_EUNSUPPORTED),
     (dict(a1=0.0), nat.CGL_EINVAL),

@@ -114,13 +114,14 @@ def test_coupled_linear_flow(n, prec):
 
 
 @pytest.mark.parametrize("n", COUPLED_SHAPES)
-@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2"])
+@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2", "rk4", "rk2"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_coupled_schemes_match_oracle(n, scheme, prec):
     rng = np.random.default_rng(6)
     p = small_coupled(n)
     W0 = coupled_data(p, rng)
-    tau, nsteps = 0.01, 5
+    # explicit Runge-Kutta: a step inside its stability limit on these grids
+    tau, nsteps = (0.001, 5) if scheme.startswith("rk") else (0.01, 5)
     ref = C.integrate(cprob(p), W0, tau, nsteps, scheme)
     with nat.CoupledPlan(p, tau, scheme, prec) as plan:
         w = nat.to_device_pair(W0, DT[prec])
@@ -145,13 +146,14 @@ def test_coupled_mirror_symmetry_on_gpu():
     assert np.max(np.abs(got[1] - mirror(got[0]))) < 1e-12 * np.max(np.abs(got))
 
 
-@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2"])
+@pytest.mark.parametrize("scheme", ["strang", "split4", "lawson4", "lawson2", "rk4", "rk2"])
 def test_coupled_paper_grid_700x350(scheme):
     """The paper's 700 x 350 grid, parameters and soliton-pair data, 3 steps
-    of tau = 3/500 (its coarsest split4 step), FP64 against the oracle."""
+    of tau = 3/500 (its coarsest split4 step; 3/2562, its finest RK step, for
+    the explicit schemes), FP64 against the oracle."""
     p = I.coupled_problem()
     W0 = I.coupled_u0(p)
-    tau, nsteps = 3.0 / 500, 3
+    tau, nsteps = (3.0 / 2562 if scheme.startswith("rk") else 3.0 / 500), 3
     ref = C.integrate(cprob(p), W0, tau, nsteps, scheme)
     with nat.CoupledPlan(p, tau, scheme, "f64") as plan:
         w = nat.to_device_pair(W0, torch.complex128)
