@@ -161,3 +161,52 @@ def test_coupled_paper_grid_700x350(scheme):
         torch.cuda.synchronize()
         assert plan.device_status() == nat.CGL_OK
         check(nat.from_device_pair(w), ref, "f64", scheme)
+
+
+# ------------------------------------------------------------ edge sizes
+
+@pytest.mark.parametrize("n", [(2025,), (1715, 2), (1536, 3), (1000,)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mixed_radix_largest_sizes(n, prec):
+    """Mixed-radix passes at the size limit: 2025 = 3^4 5^2 (odd), 1715 = 5 7^3,
+    1536 = 2^9 3, 1000 = 2^3 5^3 (one pencil per CTA, the largest twiddle
+    tables)."""
+    rng = np.random.default_rng(9)
+    d = len(n)
+    p = I.Problem(tuple(n), (I.PERIODIC,) * d, (0.0,) * d, tuple(30.0 + 5 * m for m in range(d)),
+                  0.3, 0.7, -0.2, 1.0, 0.5, -0.1, 0.2)
+    U = rng.standard_normal(p.n) + 1j * rng.standard_normal(p.n)
+    L = O.LinearOperator(oprob(p), 0.013)
+    with nat.Plan(p, 0.013, "split4", prec) as plan:
+        u = nat.to_device(U, DT[prec])
+        plan.linear_flow(u, 0.5)
+        check(nat.from_device(u), L.expK(U, 0.5), prec, "n=%s" % (n,))
+        U0 = 0.5 * U
+        ref = O.integrate(oprob(p), U0, 0.013, 2, "split4")  # the plan's step
+        u = nat.to_device(U0, DT[prec])
+        plan.step(u, 2)
+        torch.cuda.synchronize()
+        assert plan.device_status() == nat.CGL_OK
+        check(nat.from_device(u), ref, prec, "split4 n=%s" % (n,))
+
+
+@pytest.mark.parametrize("n", [(140,), (20, 15, 14)])
+@pytest.mark.parametrize("scheme", ["lawson4", "rk4", "split4"])
+def test_coupled_1d_and_3d(n, scheme):
+    """The coupled system in one and three dimensions (the advection acts on
+    direction 1 only)."""
+    rng = np.random.default_rng(10)
+    d = len(n)
+    base = I.coupled_problem()
+    p = I.CoupledProblem(tuple(n), (0.0,) * d, tuple([14.0, 3.0, 2.8][:d]), base.a0, base.a1, base.b1, base.a2,
+                         base.a3, base.b3, base.a4, base.b4, base.a5)
+    shape = tuple(n)
+    W0 = 0.6 * (1 + 0.1 * (rng.standard_normal((2,) + shape) + 1j * rng.standard_normal((2,) + shape)))
+    tau = 0.001 if scheme == "rk4" else 0.01
+    ref = C.integrate(cprob(p), W0, tau, 4, scheme)
+    with nat.CoupledPlan(p, tau, scheme, "f64") as plan:
+        w = nat.to_device_pair(W0, torch.complex128)
+        plan.step(w, 4)
+        torch.cuda.synchronize()
+        assert plan.device_status() == nat.CGL_OK
+        check(nat.from_device_pair(w), ref, "f64", scheme)
