@@ -125,7 +125,8 @@ MMA_SHAPES = [((16,), (0,)), ((48,), (1,)), ((256,), (0,)), ((128, 16), (0, 1)),
               ((256, 64), (0, 0)), ((128, 32, 16), (1, 0, 1)), ((128, 16, 80), (0, 1, 1)),
               ((256, 256, 3 * 16), (1, 1, 0)), ((240,), (1,)), ((128, 208), (0, 1)),
               ((37,), (0,)), ((50, 77), (0, 1)), ((130, 100), (1, 0)), ((230, 9), (1, 0)),
-              ((40, 24, 33), (1, 0, 1)), ((20, 6, 230), (0, 1, 1)), ((200, 9, 5), (0, 1, 0)), ((64, 150), (1, 1))]
+              ((40, 24, 33), (1, 0, 1)), ((20, 6, 230), (0, 1, 1)), ((200, 9, 5), (0, 1, 0)), ((64, 150), (1, 1)),
+              ((2,), (0,)), ((2, 3), (1, 0)), ((3, 256), (1, 1)), ((256, 2, 7), (0, 1, 0))]
 
 
 @pytest.mark.parametrize("n,bc", MMA_SHAPES)
