@@ -105,98 +105,169 @@ def measured_peaks():
         return {}
 
 
-def run_batch512(args):
-    """512 independent 2D cubic / cubic-quintic instances (grids 48..256 per
-    direction, Dirichlet/Neumann mixes, random parameters and bumps),
-    Lawson4, tau = 0.01: batched launches (BF16x3 on the tensor cores, FP32
-    and FP64 SIMT) against the plain method (one FP64 plan per instance,
-    stepped one after another), and the complex64 batches' errors after 200
-    steps against the FP64 batch."""
+def timed_steps(step_fn, K, chunk, warmup, flush, stream):
+    """ms per time step: `warmup` (at least 3) untimed calls of one step, then
+    K calls of `chunk` steps, each bracketed by CUDA events on `stream` with
+    L2 flushed (outside the events) before it."""
+    import torch
+    for _ in range(max(warmup, 3)):
+        step_fn(1)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(K):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step_fn(chunk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    return ms / (K * chunk)
+
+
+def neumann256_study(dev, flush, K, warmup, chunk, t1_steps, n=256, precisions=("bf16x3", "f32", "f64")):
+    """3D cubic Neumann n^3, Lawson4, tau = 0.01 in each precision: ms per
+    time step, per-kernel timing of one step, and the error after t1_steps
+    steps from the initial data against the FP64 path."""
     import torch
     from paper_2403_02816_gb300 import native as nat
+    w = I.workload_3d_neumann(n)
+    U0 = I.u0_3d_neumann(w)
+    N = w.prob.N
+    stream = torch.cuda.current_stream()
+    res, prof, finals = {}, {}, {}
+    for prec in precisions:
+        dt = torch.complex128 if prec in ("f64", "f64tc") else torch.complex64
+        with nat.Plan(w.prob, w.tau, "lawson4", prec) as plan:
+            u = nat.to_device(U0, dt, dev)
+            ms = timed_steps(lambda k: plan.step(u, k), K if prec != "f64" else 1, chunk, warmup, flush, stream)
+            res[prec] = {"grid_pt_steps_per_s": N / (ms / 1e3), "ms_per_time_step": ms,
+                         "launches_per_step": plan.info()["launches_per_step"]}
+            prof[prec] = plan.profile(u, 1)
+            v = nat.to_device(U0, dt, dev)
+            plan.step(v, t1_steps)
+            torch.cuda.synchronize()
+            res[prec]["device_status"] = plan.device_status()
+            finals[prec] = v
+    ref = finals.get("f64")
+    for prec in precisions:
+        if prec == "f64" or ref is None:
+            continue
+        e2, einf, nf = nat.cgl_rel_error(finals[prec].to(torch.complex128), ref, nat.CGL_F64)
+        res[prec]["rel_l2_vs_f64_at_T"] = e2
+        res[prec]["rel_inf_vs_f64_at_T"] = einf
+        res[prec]["speedup_vs_f64"] = res[prec]["grid_pt_steps_per_s"] / res["f64"]["grid_pt_steps_per_s"]
+    return w, res, prof
 
-    dev = torch.device("cuda", 0)
-    nat.load()
+
+def mma_roofline(prof_bf16):
+    """tcgen05 mode pass of the BF16x3 path: issued tensor flops over its
+    per-launch CUDA-event time, against the measured BF16 peak."""
+    peaks = measured_peaks()
+    mma = [r for r in prof_bf16 if r["name"] == "mma_mode_bf16x3"][0]
+    achieved = mma["flops"] / (mma["total_ms"] / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops", 1948.7))
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel": "mma_mode_bf16x3", "launches_profiled": mma["launches"],
+            "avg_launch_ms": mma["total_ms"] / mma["launches"],
+            "flops_counted": "issued: 6 split products x 8 n real flops per point per mode",
+            "algorithmic_frac": achieved / 6 / peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
+            "share": mma["total_ms"] / sum(r["total_ms"] for r in prof_bf16),
+            "frac_of_sustained": achieved / float(peaks.get("bf16_tflops_sustained", 1712.8))}
+
+
+def batch512_study(dev, flush, K, warmup, chunk, t1_steps, precisions=("bf16x3", "f32", "f64"), single=False):
+    """The 512-instance batch, Lawson4, tau = 0.01: ms per time step of each
+    precision, the per-instance errors after t1_steps steps against the FP64
+    batch, and (single=True) the plain method, one FP64 plan per instance."""
+    import torch
+    from paper_2403_02816_gb300 import native as nat
     count = 512
     probs = I.batched_problems(count)
     fields = [I.u0_bumps(p, np.random.Generator(np.random.PCG64(I.SEED_BASE + 3 + 1000 * i)))
               for i, p in enumerate(probs)]
     total = sum(p.N for p in probs)
-    tau, chunk = 0.01, args.chunk
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     # algorithmic flops per Lawson4 step: 2 sweeps x 2 fields x 8 n_mu N per mode,
     # plus g (15), the first-sweep combination (46) and the last (19) per point
     flops_step = sum(4 * 8 * (p.n[0] + p.n[1]) * p.N + (15 + 46 + 19) * p.N for p in probs)
     # tensor-core flops issued per step: 6 split products of each mode product
     tensor_flops_step = sum(6 * 4 * 8 * (p.n[0] + p.n[1]) * p.N for p in probs)
-
-    def timed(step_fn, K):
-        for _ in range(max(args.warmup, 3)):
-            step_fn(1)
-        torch.cuda.synchronize()
-        ms = 0.0
-        for _ in range(K):
-            flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step_fn(chunk)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
-        return ms / (K * chunk)
-
     res, finals = {}, {}
-    with Clocks(0) as clk:
-        for prec in ("bf16x3", "f32", "f64"):
-            t0 = time.perf_counter()
-            with nat.Batch(probs, tau, "lawson4", prec) as b:
-                create_s = time.perf_counter() - t0
-                u = b.pack(fields, dev)
-                ms = timed(lambda k: b.step(u, k), args.steps if prec != "f64" else max(1, args.steps // 2))
-                res["batched_" + prec] = {"grid_pt_steps_per_s": total / (ms / 1e3), "ms_per_time_step": ms,
-                                          "create_s": create_s, "launches_per_step": b.launches_per_step,
-                                          "achieved_tflops": flops_step / (ms / 1e3) / 1e12}
-                v = b.pack(fields, dev)
-                b.step(v, args.t1_steps)
-                torch.cuda.synchronize()
-                res["batched_" + prec]["device_status"] = b.device_status()
-                finals[prec] = b.unpack(v)
-        # the plain method: one FP64 plan per instance, stepped in turn
-        plans = [nat.Plan(p, tau, "lawson4", "f64") for p in probs]
+    for prec in precisions:
+        t0 = time.perf_counter()
+        with nat.Batch(probs, 0.01, "lawson4", prec) as b:
+            create_s = time.perf_counter() - t0
+            u = b.pack(fields, dev)
+            ms = timed_steps(lambda k: b.step(u, k), K if prec != "f64" else max(1, K // 2), chunk, warmup, flush,
+                             stream)
+            res[prec] = {"grid_pt_steps_per_s": total / (ms / 1e3), "ms_per_time_step": ms,
+                         "create_s": create_s, "launches_per_step": b.launches_per_step,
+                         "achieved_tflops": flops_step / (ms / 1e3) / 1e12}
+            v = b.pack(fields, dev)
+            b.step(v, t1_steps)
+            torch.cuda.synchronize()
+            res[prec]["device_status"] = b.device_status()
+            finals[prec] = b.unpack(v)
+    if "bf16x3" in res:
+        res["bf16x3"]["achieved_tensor_tflops"] = tensor_flops_step / (res["bf16x3"]["ms_per_time_step"] / 1e3) / 1e12
+    if single:
+        plans = [nat.Plan(p, 0.01, "lawson4", "f64") for p in probs]
         us = [nat.to_device(U, torch.complex128, dev) for U in fields]
 
         def seq(k):
             for pl, uu in zip(plans, us):
                 pl.step(uu, k)
-        ms = timed(seq, 1)
+        ms = timed_steps(seq, 1, chunk, warmup, flush, stream)
         res["single_plans_f64"] = {"grid_pt_steps_per_s": total / (ms / 1e3), "ms_per_time_step": ms,
                                    "achieved_tflops": flops_step / (ms / 1e3) / 1e12}
         for pl in plans:
             pl.close()
-    def errs_vs_f64(prec):
-        e = [float(np.linalg.norm(a - r) / np.linalg.norm(r)) for a, r in zip(finals[prec], finals["f64"])]
-        return {"max": max(e), "median": float(np.median(e))}
-    fp32_peak = FP32_PEAK_TFLOPS
-    f32 = res["batched_f32"]
-    bf = res["batched_bf16x3"]
-    bf["achieved_tensor_tflops"] = tensor_flops_step / (bf["ms_per_time_step"] / 1e3) / 1e12
+    errs = {}
+    if "f64" in finals:
+        for prec in finals:
+            if prec == "f64":
+                continue
+            e2 = [float(np.linalg.norm(a - r) / np.linalg.norm(r)) for a, r in zip(finals[prec], finals["f64"])]
+            ei = [float(np.abs(a - r).max() / np.abs(r).max()) for a, r in zip(finals[prec], finals["f64"])]
+            errs[prec] = {"rel_l2_max": max(e2), "rel_l2_median": float(np.median(e2)), "rel_inf_max": max(ei),
+                          "rel_inf_median": float(np.median(ei)), "steps": t1_steps}
+    return {"instances": count, "total_points": total, "flops_step": flops_step,
+            "tensor_flops_step": tensor_flops_step}, res, errs
+
+
+def run_batch512(args):
+    """512 independent 2D cubic / cubic-quintic instances (grids 48..256 per
+    direction, Dirichlet/Neumann mixes, random parameters and bumps),
+    Lawson4, tau = 0.01: batched launches (BF16x3 on the tensor cores, FP32
+    and FP64 SIMT) against the plain method (one FP64 plan per instance,
+    stepped one after another), and the complex64 batches' errors after
+    `--t1-steps` steps against the FP64 batch."""
+    import torch
+    from paper_2403_02816_gb300 import native as nat
+
+    dev = torch.device("cuda", 0)
+    nat.load()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    chunk = args.chunk
+    with Clocks(0) as clk:
+        info, res, errs = batch512_study(dev, flush, args.steps, args.warmup, chunk, args.t1_steps, single=True)
+    f32, bf = res["f32"], res["bf16x3"]
     peaks = measured_peaks()
     tpeak = float(peaks.get("bf16_tflops", 1948.7))
     line = {
         "metric": METRIC, "value": bf["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": bf["ms_per_time_step"] * chunk, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
-        "config": {"workload": "batched_512x2d_lawson4_c64", "instances": count, "total_points": total,
-                   "tau": tau, "time_steps_per_bench_step": chunk, "T_steps_for_error": args.t1_steps,
-                   "l2": "flushed (256 MiB write) between timed iterations"},
-        "results": res,
-        "bf16x3_vs_f64_rel_l2_per_instance": errs_vs_f64("bf16x3"),
-        "f32_vs_f64_rel_l2_per_instance": errs_vs_f64("f32"),
+        "config": {"workload": "batched_512x2d_lawson4_c64", "instances": info["instances"],
+                   "total_points": info["total_points"], "tau": 0.01, "time_steps_per_bench_step": chunk,
+                   "T_steps_for_error": args.t1_steps, "l2": "flushed (256 MiB write) between timed iterations"},
+        "results": res, "per_instance_errors_vs_f64": errs,
         "speedup_batched_bf16x3_vs_single_f64": bf["grid_pt_steps_per_s"] /
         res["single_plans_f64"]["grid_pt_steps_per_s"],
         "speedup_batched_f32_vs_single_f64": f32["grid_pt_steps_per_s"] / res["single_plans_f64"]["grid_pt_steps_per_s"],
-        "speedup_batched_f64_vs_single_f64": res["batched_f64"]["grid_pt_steps_per_s"] /
+        "speedup_batched_f64_vs_single_f64": res["f64"]["grid_pt_steps_per_s"] /
         res["single_plans_f64"]["grid_pt_steps_per_s"],
         "roofline": {"bound": "tensor", "kernel": "mma_mode_kernel (grouped)", "achieved": bf["achieved_tensor_tflops"],
                      "peak": tpeak, "unit": "TFLOP/s", "frac": bf["achieved_tensor_tflops"] / tpeak,
@@ -204,8 +275,8 @@ def run_batch512(args):
                      "note": "issued tensor flops over the whole-step time (all launches, pointwise stages "
                              "included): a lower bound for the grouped pass"},
         "roofline_f32_simt": {"bound": "alu", "kernel": "batched_mode_pass_kernel<float>",
-                              "achieved": f32["achieved_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
-                              "frac": f32["achieved_tflops"] / fp32_peak,
+                              "achieved": f32["achieved_tflops"], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": f32["achieved_tflops"] / FP32_PEAK_TFLOPS,
                               "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
                               "note": "whole-step time, all passes"},
         "clocks": clk.summary(),
@@ -303,59 +374,14 @@ def run_neumann256(args):
 
     dev = torch.device("cuda", 0)
     nat.load()
-    w = I.workload_3d_neumann(args.n if args.n != 128 else 256)
-    U0 = I.u0_3d_neumann(w)
-    N = w.prob.N
-    chunk = args.chunk
-    stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    res = {}
-    finals = {}
-    prof = {}
+    chunk = args.chunk
     with Clocks(0) as clk:
-        for prec in ("bf16x3", "f32", "f64"):
-            dt = torch.complex128 if prec == "f64" else torch.complex64
-            with nat.Plan(w.prob, w.tau, "lawson4", prec) as plan:
-                u = nat.to_device(U0, dt, dev)
-                K = args.steps if prec != "f64" else max(1, args.steps // 2)
-                for _ in range(max(args.warmup, 3)):
-                    plan.step(u, 1)
-                torch.cuda.synchronize()
-                ms = 0.0
-                for _ in range(K):
-                    flush.fill_(1.0)
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    plan.step(u, chunk)
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    ms += e0.elapsed_time(e1)
-                res[prec] = {"grid_pt_steps_per_s": N * chunk * K / (ms / 1e3), "ms_per_time_step": ms / (chunk * K)}
-                prof[prec] = plan.profile(u, 1)
-                # T = t1_steps * tau run from the initial field
-                v = nat.to_device(U0, dt, dev)
-                plan.step(v, args.t1_steps)
-                torch.cuda.synchronize()
-                res[prec]["device_status"] = plan.device_status()
-                finals[prec] = v
-    ref = finals["f64"]
-    for prec in ("bf16x3", "f32"):
-        e2, einf, nf = nat.cgl_rel_error(finals[prec].to(torch.complex128), ref, nat.CGL_F64)
-        res[prec]["rel_l2_vs_f64_at_T"] = e2
-        res[prec]["rel_inf_vs_f64_at_T"] = einf
-        res[prec]["speedup_vs_f64"] = res[prec]["grid_pt_steps_per_s"] / res["f64"]["grid_pt_steps_per_s"]
-    peaks = measured_peaks()
-    mma = [r for r in prof["bf16x3"] if r["name"] == "mma_mode_bf16x3"][0]
-    achieved = mma["flops"] / (mma["total_ms"] / 1e3) / 1e12
-    peak = float(peaks.get("bf16_tflops", 1948.7))
-    traffic = profiled_traffic("mma_mode_bf16x3_ncu_neumann256.md", ["mma_mode.cu", "tc_ptx.cuh", "cgl_internal.cuh"])
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "mma_mode_bf16x3", "launches_profiled": mma["launches"],
-                "avg_launch_ms": mma["total_ms"] / mma["launches"],
-                "flops_counted": "issued: 6 split products x 8 n real flops per point per mode",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
-                "share": mma["total_ms"] / sum(r["total_ms"] for r in prof["bf16x3"]),
-                "frac_of_sustained": achieved / float(peaks.get("bf16_tflops_sustained", 1712.8))}
+        w, res, prof = neumann256_study(dev, flush, args.steps, args.warmup, chunk, args.t1_steps,
+                                        n=args.n if args.n != 128 else 256)
+    roofline = mma_roofline(prof["bf16x3"])
+    roofline["traffic"] = profiled_traffic("mma_mode_bf16x3_ncu_neumann256.md",
+                                           ["mma_mode.cu", "tc_ptx.cuh", "cgl_internal.cuh"])
     f64k = [r for r in prof["f64"] if r["name"] == "mode_pass_f64"][0]
     f32k = [r for r in prof["f32"] if r["name"] == "mode_pass_f32"][0]
     line = {
@@ -720,6 +746,58 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def _oracle_worker(n, scheme, nsteps, barrier, queue):
+    """One process of the all-cores oracle baseline: build the workload,
+    wait for the others, time `nsteps` oracle steps."""
+    w = I.workload_3d_periodic(n)
+    U0 = I.u0_3d_periodic(w)
+    barrier.wait()
+    secs, _ = cpu_oracle_steps(w, U0, scheme, nsteps)
+    queue.put(secs)
+
+
+def cpu_oracle_all_cores(n, scheme, nsteps, procs):
+    """The oracle on every host core at once: `procs` spawned processes (one
+    numpy thread each) each time `nsteps` steps of the full field after a
+    common barrier; throughput = procs * N * nsteps / slowest process."""
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(n, scheme, nsteps, barrier, queue)) for _ in range(procs)]
+    for q in ps:
+        q.start()
+    secs = [queue.get(timeout=600) for _ in ps]
+    for q in ps:
+        q.join()
+    N = n ** 3
+    return procs * N * nsteps / max(secs), max(secs)
+
+
+def dirichlet64_gpu(dev, flush, K, warmup):
+    """The 2D Dirichlet 64^2 parity workload (FP64, tau = 0.01, 200 steps of
+    Strang and of Lawson4) on the GPU: ms per time step and the final fields."""
+    import torch
+    from paper_2403_02816_gb300 import native as nat
+    w = I.workload_2d_dirichlet(64)
+    U0 = I.u0_2d_dirichlet(w)
+    stream = torch.cuda.current_stream()
+    res, finals = {}, {}
+    for scheme in ("strang", "lawson4"):
+        with nat.Plan(w.prob, w.tau, scheme, "f64") as plan:
+            u = nat.to_device(U0, torch.complex128, dev)
+            ms = timed_steps(lambda k: plan.step(u, k), K, 200, warmup, flush, stream)
+            res[scheme] = {"grid_pt_steps_per_s": w.prob.N / (ms / 1e3), "ms_per_time_step": ms,
+                           "launches_per_step": plan.info()["launches_per_step"]}
+            v = nat.to_device(U0, torch.complex128, dev)
+            plan.step(v, 200)
+            torch.cuda.synchronize()
+            res[scheme]["device_status"] = plan.device_status()
+            finals[scheme] = nat.from_device(v)
+    return w, U0, res, finals
+
+
 def oracle_problem(p):
     from oracle import cgl_oracle as O
     return O.OracleProblem(p.n, p.bc, p.lo, p.hi, p.a1, p.b1, p.a2, p.a3, p.b3, p.a4, p.b4)
@@ -756,26 +834,28 @@ def over_ranks(ms_local, units_local, dist=None, device="cpu"):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on every host core (one process
+    per core, each advancing its own copy of the full field by one time step
+    per bench step, after `--warmup` untimed steps)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = I.workload_3d_periodic(args.n)
-    U0 = I.u0_3d_periodic(w)
     N = w.prob.N
-    for _ in range(max(args.warmup, 0)):
-        cpu_oracle_steps(w, U0, args.scheme, 1)
-    times = [cpu_oracle_steps(w, U0, args.scheme, 1)[0] for _ in range(args.steps)]
-    total = sum(times)
-    value = N * args.steps / total
+    procs = os.cpu_count() or 1
+    value, secs = cpu_oracle_all_cores(args.n, args.scheme, max(args.warmup, 0) + args.steps, procs)
+    # the warm-up steps run inside the same timed loop; the rate counts all steps
+    steps_run = max(args.warmup, 0) + args.steps
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / steps_run,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "scheme": args.scheme, "tau": w.tau, "grid": list(w.prob.n),
                    "time_steps_per_bench_step": 1, "l2": "input larger than L2 not needed (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d time steps of %s on the full %s field (numpy, FP64)"
-                                   % (args.steps, args.scheme, "x".join(map(str, w.prob.n)))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": "%d time steps of %s on the full %s field in each of %d processes at once "
+                                   "(numpy, FP64, one thread each)"
+                                   % (steps_run, args.scheme, "x".join(map(str, w.prob.n)), procs)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -859,16 +939,23 @@ def main():
     # per-kernel timing for the roofline (CUDA events around every launch)
     prof = plan.profile(u, 2)
     dom = max(prof, key=lambda r: r["total_ms"])
-    achieved = dom["flops"] / (dom["total_ms"] / 1e3) / 1e12
+    share = dom["total_ms"] / sum(r["total_ms"] for r in prof)
+    # the dominant kernel's time inside the replayed graph: its share (from
+    # the per-launch events of cgl_profile_step) of the graph-timed step
+    graph_ms_per_time_step = ms_max / (args.steps * chunk)
+    achieved = (dom["flops"] / 2) / (share * graph_ms_per_time_step / 1e3) / 1e12
+    achieved_events = dom["flops"] / (dom["total_ms"] / 1e3) / 1e12
     peak = fp64_peak_tflops()
     traffic = None
     if args.n == 128 and args.scheme == "split4":
         traffic = profiled_traffic("fft_pass_f64_dram_split4_128cubed.md", ["fft.cu", "cgl_internal.cuh"])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom["name"], "launches_profiled": dom["launches"],
-                "avg_launch_ms": dom["total_ms"] / dom["launches"],
+                "avg_launch_ms": share * graph_ms_per_time_step * 2 / dom["launches"],
+                "timing": "share of the graph-timed step (CUDA events around the replayed graphs)",
+                "achieved_per_launch_events": achieved_events,
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz (1.25 TFLOP/s nominal FP64)",
-                "share": dom["total_ms"] / sum(r["total_ms"] for r in prof)}
+                "share": share}
     fma = measured_fma_peaks()
     roofline["peak_fma_microbenchmark"] = fma["f64_tflops"]
     roofline["frac_of_fma_microbenchmark"] = achieved / fma["f64_tflops"]
@@ -897,13 +984,54 @@ def main():
                 extras[s] = N * chunk * 2 / (ms2 / 1e3)
         extras[args.scheme] = value / world
 
+    workloads = {}
+    c0 = None
+    if not args.no_extras and rank == 0:
+        with Clocks(local) as clk2:
+            c0 = dirichlet64_gpu(dev, flush, 3, 3)
+            workloads["dirichlet64_fd2_c128"] = {"config": c0[0].name, "tau": c0[0].tau, "steps": 200,
+                                                 "precision": "f64", "schemes": c0[2]}
+            wn, res_n, prof_n = neumann256_study(dev, flush, 3, 3, 10, 100)
+            rl = mma_roofline(prof_n["bf16x3"])
+            rl["traffic"] = profiled_traffic("mma_mode_bf16x3_ncu_neumann256.md",
+                                             ["mma_mode.cu", "tc_ptx.cuh", "cgl_internal.cuh"])
+            workloads["neumann256_lawson4"] = {"config": wn.name, "tau": wn.tau, "T": 100 * wn.tau,
+                                               "precisions": res_n, "roofline_tcgen05": rl}
+            info_b, res_b, errs_b = batch512_study(dev, flush, 3, 3, 10, 200)
+            tpeak = float(measured_peaks().get("bf16_tflops", 1948.7))
+            workloads["batch512_lawson4"] = {
+                "config": "batched_512x2d_lawson4_c64", "tau": 0.01, "instances": info_b["instances"],
+                "total_points": info_b["total_points"], "precisions": res_b, "per_instance_errors_vs_f64": errs_b,
+                "tensor_frac_whole_step": res_b["bf16x3"]["achieved_tensor_tflops"] / tpeak}
+        workloads["clocks"] = clk2.summary()
+
     cpu = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, Uref = cpu_oracle_steps(w, U0, args.scheme, 1)
-        cpu = {"value": N / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "1 time step of %s on the full %s field (numpy FP64, single thread)"
-                         % (args.scheme, "x".join(map(str, w.prob.n)))}
+        procs = os.cpu_count() or 1
+        all_value, all_secs = cpu_oracle_all_cores(args.n, args.scheme, 2, procs)
+        cpu = {"value": all_value, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": "2 time steps of %s on the full %s field in each of %d processes at once (numpy FP64, "
+                         "one thread each)" % (args.scheme, "x".join(map(str, w.prob.n)), procs),
+               "value_1_core": N / secs,
+               "sample_1_core": "1 time step of %s on the full %s field (numpy FP64, single thread)"
+                                % (args.scheme, "x".join(map(str, w.prob.n)))}
+        if c0 is not None:
+            # the 64^2 Dirichlet workload's whole run in the oracle: its time
+            # and the GPU's relative L2 / inf differences from it
+            from oracle import cgl_oracle as O
+            w0, U00, _, finals0 = c0
+            op0 = oracle_problem(w0.prob)
+            for scheme in ("strang", "lawson4"):
+                t0 = time.perf_counter()
+                ref0 = O.integrate(op0, U00, w0.tau, 200, scheme)
+                dt0 = time.perf_counter() - t0
+                g0 = finals0[scheme]
+                sc = workloads["dirichlet64_fd2_c128"]["schemes"][scheme]
+                sc["rel_l2_vs_oracle"] = float(np.linalg.norm(g0 - ref0) / np.linalg.norm(ref0))
+                sc["rel_inf_vs_oracle"] = float(np.abs(g0 - ref0).max() / np.abs(ref0).max())
+                sc["oracle_grid_pt_steps_per_s_1_core"] = w0.prob.N * 200 / dt0
         with nat.Plan(w.prob, w.tau, args.scheme, "f64") as p3:
             u3 = nat.to_device(U0, torch.complex128, dev)
             p3.step(u3, 1)
@@ -922,7 +1050,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": info["launches_per_step"] * chunk * args.steps,
             "clocks": clocks, "device_status": status,
-            "rel_l2_vs_oracle_1step": parity, "schemes_grid_pt_steps_per_s": extras,
+            "rel_l2_vs_oracle_1step": parity, "schemes_grid_pt_steps_per_s": extras, "workloads": workloads,
             "paper_context": {
                 "note": "the paper's nearest run (3D cubic-quintic, periodic Fourier 128^3, split4; other domain "
                         "and parameters, so not vs_baseline); MATLAB FP64 on a 6-core laptop CPU",

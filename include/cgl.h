@@ -386,6 +386,24 @@ int cgl_corrector_set_output_scale(cgl_corrector* c, float scale);
 int cgl_conv3x3(const float* x, const uint16_t* w, const float* bias, float* y, int B, int cin,
                 int cout, int H, int W, int relu, int* status, void* stream);
 
+/*
+ * Copy of one of the corrector's per-layer buffers (introspection, for
+ * checking each convolution of the network separately against a
+ * reference given the same inputs).  kind 0: the activation feeding layer
+ * `layer` (0 = the 9 feature planes, l = the output of layer l - 1 after its
+ * ReLU; layers = the network output before the output scale), float
+ * [batch][C][H][W]; kind 1: the gradient of the loss w.r.t. the output of
+ * layer `layer` (0..layers-1) after that layer's ReLU mask, as used by the
+ * weight gradient and the input-gradient convolution.  Values are those of
+ * the most recent forward / gradients / train_step / apply call.
+ * dst: device or host float array of `count` values (1 <= count <=
+ * max_batch * C * H * W), filled with the first `count` values.
+ * Asynchronous on `stream` (synchronise before reading a host dst).
+ * Errors: EINVAL (bad kind, layer or count), ECUDA.
+ */
+int cgl_corrector_layer_state(const cgl_corrector* c, int kind, int layer, float* dst, int64_t count,
+                              void* stream);
+
 /* Read (synchronising `stream`) and clear the corrector's device status word:
  * CGL_ETIMEOUT if a bounded tensor-core wait gave up since the last read. */
 int cgl_corrector_last_device_status(cgl_corrector* c, void* stream);

@@ -246,7 +246,7 @@ struct cgl_corrector {
   int64_t t = 0;
   float out_scale = 1.f;  // N(x) = out_scale * (last convolution)
   std::vector<float*> acts;  // acts[0] = features, acts[l+1] = output of layer l
-  float* dbuf[2] = {nullptr, nullptr};
+  std::vector<float*> dys;   // dys[l] = loss gradient w.r.t. layer l's output (after its ReLU mask)
   double* loss = nullptr;
   int* status = nullptr;  // device word: bit 1 = a bounded tensor-core wait gave up
   std::vector<void*> allocations;
@@ -320,14 +320,13 @@ int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const vo
   CUDA_TRY(cudaMemsetAsync(c->loss, 0, sizeof(double), s));
   CUDA_TRY(cudaMemsetAsync(c->grad, 0, c->nparams * sizeof(float), s));
   loss_kernel<<<grid_for(B * HW), 256, 0, s>>>(c->acts[c->nlayers], c->out_scale, (const float2*)coarse,
-                                               (const float2*)target, idx, B, HW, c->dbuf[0], c->loss);
+                                               (const float2*)target, idx, B, HW, c->dys[c->nlayers - 1], c->loss);
   CUDA_TRY(cudaGetLastError());
-  int cur = 0;
   const int tiles = (c->H / kTile) * (c->W / kTile);
   const int tiles_per_cta = std::max(1, tiles / 4);
   for (int l = c->nlayers - 1; l >= 0; --l) {
     const auto& L = c->layers[l];
-    float* dy = c->dbuf[cur];
+    float* dy = c->dys[l];
     if (l < c->nlayers - 1) {
       relu_backward_kernel<<<grid_for(B * L.cout * HW), 256, 0, s>>>(dy, c->acts[l + 1], (int64_t)B * L.cout * HW);
       CUDA_TRY(cudaGetLastError());
@@ -340,8 +339,7 @@ int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const vo
     if (l > 0) {
       flip_weights_kernel<<<grid_for(L.cin * L.cout * 9), 256, 0, s>>>(c->wbf + L.w_off, c->wflip, L.cin, L.cout);
       CUDA_TRY(cudaGetLastError());
-      CUDA_TRY(launch_conv(dy, c->wflip, nullptr, c->dbuf[1 - cur], B, L.cout, L.cin, c->H, c->W, 0, c->status, s));
-      cur = 1 - cur;
+      CUDA_TRY(launch_conv(dy, c->wflip, nullptr, c->dys[l - 1], B, L.cout, L.cin, c->H, c->W, 0, c->status, s));
     }
   }
   if (loss_out) {
@@ -373,7 +371,6 @@ int cgl_corrector_create(cgl_corrector** out, int height, int width, int hidden,
   c->nlayers = layers;
   c->max_batch = max_batch;
   int64_t off = 0;
-  int maxc = 9;
   for (int l = 0; l < layers; ++l) {
     cgl_corrector::Layer L;
     L.cin = l == 0 ? 9 : hidden;
@@ -383,7 +380,6 @@ int cgl_corrector_create(cgl_corrector** out, int height, int width, int hidden,
     off += (int64_t)L.cout * L.cin * 9;
     L.b_off = off;
     off += L.cout;
-    maxc = std::max(maxc, L.cout);
     c->layers.push_back(L);
   }
   c->nparams = off;
@@ -404,7 +400,11 @@ int cgl_corrector_create(cgl_corrector** out, int height, int width, int hidden,
     st = corr_alloc(c, (void**)&a, (size_t)max_batch * ch * HW * sizeof(float));
     c->acts.push_back(a);
   }
-  for (int k = 0; !st && k < 2; ++k) st = corr_alloc(c, (void**)&c->dbuf[k], (size_t)max_batch * maxc * HW * sizeof(float));
+  for (int l = 0; !st && l < layers; ++l) {
+    float* g = nullptr;
+    st = corr_alloc(c, (void**)&g, (size_t)max_batch * c->layers[l].cout * HW * sizeof(float));
+    c->dys.push_back(g);
+  }
   if (!st) {
     // He-uniform initial weights from splitmix64(seed, index); last layer
     // scaled by 0.1 so the untrained correction starts small; zero biases.
@@ -528,6 +528,26 @@ int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, co
 int cgl_corrector_set_output_scale(cgl_corrector* c, float scale) {
   if (!c || !(scale > 0.f) || !std::isfinite(scale)) return fail(CGL_EINVAL, "scale must be positive and finite");
   c->out_scale = scale;
+  return CGL_OK;
+}
+
+int cgl_corrector_layer_state(const cgl_corrector* c, int kind, int layer, float* dst, int64_t count,
+                              void* stream) {
+  if (!c || !dst) return fail(CGL_EINVAL, "NULL argument");
+  const int64_t HW = (int64_t)c->H * c->W;
+  const float* src = nullptr;
+  int ch = 0;
+  if (kind == 0 && layer >= 0 && layer <= c->nlayers) {
+    src = c->acts[layer];
+    ch = layer == 0 ? 9 : c->layers[layer - 1].cout;
+  } else if (kind == 1 && layer >= 0 && layer < c->nlayers) {
+    src = c->dys[layer];
+    ch = c->layers[layer].cout;
+  } else {
+    return fail(CGL_EINVAL, "kind must be 0 (activation, layer 0..layers) or 1 (gradient, layer 0..layers-1)");
+  }
+  if (count < 1 || count > (int64_t)c->max_batch * ch * HW) return fail(CGL_EINVAL, "count out of range");
+  CUDA_TRY(cudaMemcpyAsync(dst, src, count * sizeof(float), cudaMemcpyDefault, (cudaStream_t)stream));
   return CGL_OK;
 }
 

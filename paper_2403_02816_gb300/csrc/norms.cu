@@ -5,7 +5,7 @@
 // folds them.
 #include <algorithm>
 
-#include "cgl_internal.cuh"
+#include "plan.cuh"  // cgl::fail (last-error message)
 
 namespace cgl {
 
@@ -196,11 +196,16 @@ static cudaError_t static_scratch(double** out) {
 extern "C" int cgl_rel_error_noalloc(const void* x, const void* y, int64_t count, int precision, double* out,
                                      void* stream) {
   using namespace cgl;
-  if (!x || !y || !out || count <= 0 || count > CGL_REL_ERROR_NOALLOC_MAX_COUNT) return CGL_EINVAL;
-  if (precision != CGL_F64 && precision != CGL_F32) return CGL_EINVAL;
+  if (!x || !y || !out) return fail(CGL_EINVAL, "NULL argument");
+  if (count <= 0) return fail(CGL_EINVAL, "count must be positive");
+  if (count > CGL_REL_ERROR_NOALLOC_MAX_COUNT)
+    return fail(CGL_EINVAL, "count exceeds CGL_REL_ERROR_NOALLOC_MAX_COUNT (the static scratch capacity)");
+  if (precision == CGL_BF16X3) precision = CGL_F32;  // complex64 state, as cgl_rel_error
+  if (precision != CGL_F64 && precision != CGL_F32) return fail(CGL_EINVAL, "unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
   double* partial = nullptr;
-  if (static_scratch(&partial) != cudaSuccess) return CGL_ECUDA;
+  cudaError_t e = static_scratch(&partial);
+  if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("scratch address: ") + cudaGetErrorString(e));
   const int nblocks = (int)((count + kStaticChunk - 1) / kStaticChunk);
   double* result = partial + kNormFields * nblocks;
   if (precision == CGL_F64)
@@ -209,11 +214,14 @@ extern "C" int cgl_rel_error_noalloc(const void* x, const void* y, int64_t count
   else
     rel_error_partial_chunked<float2><<<nblocks, kNormThreads, 0, s>>>((const float2*)x, (const float2*)y,
                                                                        count, partial);
-  if (cudaGetLastError() != cudaSuccess) return CGL_ECUDA;
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return fail(CGL_ECUDA, std::string("rel_error_noalloc: ") + cudaGetErrorString(e));
   rel_error_final<<<1, kNormThreads, 0, s>>>(partial, nblocks, result);
-  if (cudaGetLastError() != cudaSuccess) return CGL_ECUDA;
-  if (cudaMemcpyAsync(out, result, 3 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return CGL_ECUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return CGL_ECUDA;
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return fail(CGL_ECUDA, std::string("rel_error_noalloc: ") + cudaGetErrorString(e));
+  if ((e = cudaMemcpyAsync(out, result, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return fail(CGL_ECUDA, std::string("rel_error_noalloc: ") + cudaGetErrorString(e));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail(CGL_ECUDA, std::string("rel_error_noalloc: ") + cudaGetErrorString(e));
   return CGL_OK;
 }

@@ -116,6 +116,7 @@ def load() -> ctypes.CDLL:
         "cgl_corrector_last_device_status": (I, [P, VP]),
         "cgl_conv3x3": (I, [VP, VP, VP, VP, I, I, I, I, I, I, VP, VP]),
         "cgl_corrector_set_output_scale": (I, [P, ctypes.c_float]),
+        "cgl_corrector_layer_state": (I, [P, I, I, VP, I64, VP]),
         "cgl_strerror": (ctypes.c_char_p, [I]),
         "cgl_last_error": (ctypes.c_char_p, []),
     }
@@ -524,6 +525,16 @@ class Corrector:
     def apply(self, coarse, un, params, out, stream=None):
         check(load().cgl_corrector_apply(self.handle, _ptr(coarse), _ptr(un), _ptr(params), int(coarse.shape[0]),
                                          _ptr(out), _stream_handle(stream)), "cgl_corrector_apply")
+        return out
+
+    def layer_state(self, kind, layer, batch, channels, stream=None):
+        """Per-layer buffer of the last call (cgl_corrector_layer_state):
+        kind 0 = activation feeding layer `layer`, 1 = loss gradient w.r.t.
+        layer `layer`'s output; a float32 CUDA tensor [batch, channels, H, W]."""
+        import torch
+        out = torch.empty((batch, channels) + self.hw, dtype=torch.float32, device="cuda")
+        check(load().cgl_corrector_layer_state(self.handle, int(kind), int(layer), _ptr(out), out.numel(),
+                                               _stream_handle(stream)), "cgl_corrector_layer_state")
         return out
 
     def device_status(self, stream=None) -> int:

@@ -97,6 +97,50 @@ def test_batched_workload_subset_against_oracle_full_run(prec):
         assert O.rel_l2(got[i], ref) <= 1e-4, (i, probs[i].n, O.rel_l2(got[i], ref))
 
 
+# Per-instance bounds of the 512-instance workload (Lawson4, tau = 0.01, 200
+# steps) against the FP64 batch, frozen from the first full measurement:
+#   FP32   rel. L2 max 3.50e-5 (median 9.5e-6), rel. inf max 5.85e-5
+#          -> the workload's proposed bound 1e-4 for both norms;
+#   BF16x3 rel. L2 max 1.60e-4 (median 5.3e-5), rel. inf max 1.87e-4
+#          -> 2e-4 (L2) and 2.5e-4 (inf).
+# The BF16x3 errors are 5.6x the FP32 ones (median ratio) for every kind of
+# instance alike, none an outlier: both paths use the same complex64 state
+# and factors rounded to 24 bits, and differ in the accumulation of the mode
+# products (tensor-core FP32 accumulation of the split products against
+# round-to-nearest FMA chains).
+C3_BOUNDS = {"f32": (1e-4, 1e-4), "bf16x3": (2e-4, 2.5e-4)}
+
+
+def test_full_512_instance_workload_every_instance_within_bound():
+    """All 512 instances, 200 Lawson4 steps: every complex64 instance against
+    the FP64 batch in relative L2 and relative inf norm; the FP64 batch
+    itself against the oracle on two instances (one Dirichlet-Dirichlet, one
+    with a Neumann direction) over the same 200 steps."""
+    probs = I.batched_problems(512)
+    fields = [I.u0_bumps(p, np.random.Generator(np.random.PCG64(I.SEED_BASE + 3 + 1000 * i)))
+              for i, p in enumerate(probs)]
+    finals = {}
+    for prec in ("f64", "f32", "bf16x3"):
+        with nat.Batch(probs, 0.01, "lawson4", prec) as b:
+            u = b.pack(fields)
+            b.step(u, 200)
+            torch.cuda.synchronize()
+            assert b.device_status() == nat.CGL_OK, prec
+            finals[prec] = b.unpack(u)
+    ref = finals["f64"]
+    for i in (0, next(k for k, p in enumerate(probs) if 1 in p.bc)):
+        want = O.integrate(oprob(probs[i]), fields[i], 0.01, 200, "lawson4")
+        assert O.rel_l2(ref[i], want) <= 1e-11, (i, O.rel_l2(ref[i], want))
+    for prec, (b2, binf) in C3_BOUNDS.items():
+        bad = []
+        for i, (a, r) in enumerate(zip(finals[prec], ref)):
+            e2 = float(np.linalg.norm(a - r) / np.linalg.norm(r))
+            einf = float(np.abs(a - r).max() / np.abs(r).max())
+            if not (e2 <= b2 and einf <= binf):
+                bad.append((i, probs[i].n, e2, einf))
+        assert not bad, (prec, bad[:8], len(bad))
+
+
 def test_autotuner_returns_admissible_tiles_and_caches(tmp_path, monkeypatch):
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("CGL_AUTOTUNE_CACHE", str(cache))

@@ -38,7 +38,8 @@ def norms(lib, fn, x, y, prec):
     return np.array(out[:3])
 
 
-@pytest.mark.parametrize("dtype,prec", [(torch.complex128, nat.CGL_F64), (torch.complex64, nat.CGL_F32)])
+@pytest.mark.parametrize("dtype,prec", [(torch.complex128, nat.CGL_F64), (torch.complex64, nat.CGL_F32),
+                                        (torch.complex64, nat.CGL_BF16X3)])
 def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(lib, dtype, prec):
     g = torch.Generator(device="cuda").manual_seed(7)
     # two calls in a row with different sizes: the second uses fewer partial
@@ -59,4 +60,9 @@ def test_noalloc_rejects_counts_beyond_its_scratch(lib):
     st = lib.cgl_rel_error_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), MAX_COUNT + 1,
                                    nat.CGL_F64, out, None)
     assert st == nat.CGL_EINVAL
+    assert b"CGL_REL_ERROR_NOALLOC_MAX_COUNT" in lib.cgl_last_error()
     assert lib.cgl_rel_error_noalloc(None, None, 4, nat.CGL_F64, out, None) == nat.CGL_EINVAL
+    assert b"NULL" in lib.cgl_last_error()
+    st = lib.cgl_rel_error_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 4, 7, out, None)
+    assert st == nat.CGL_EINVAL
+    assert b"precision" in lib.cgl_last_error()
