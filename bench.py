@@ -177,6 +177,23 @@ def mma_roofline(prof_bf16):
             "frac_of_sustained": achieved / float(peaks.get("bf16_tflops_sustained", 1712.8))}
 
 
+def oz_roofline(prof_oz):
+    """tcgen05 pass of the FP64-accurate path: issued tensor flops (28 digit
+    products) over its per-launch CUDA-event time, against the measured BF16
+    peak; the share of the step it takes."""
+    peaks = measured_peaks()
+    k = [r for r in prof_oz if r["name"] == "oz_mode_f64tc"][0]
+    achieved = k["flops"] / (k["total_ms"] / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops", 1948.7))
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel": "oz_mode_f64tc", "launches_profiled": k["launches"],
+            "avg_launch_ms": k["total_ms"] / k["launches"],
+            "flops_counted": "issued: 28 digit products x 8 n real flops per point per mode",
+            "algorithmic_fp64_tflops": achieved / 28,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
+            "share": k["total_ms"] / sum(r["total_ms"] for r in prof_oz)}
+
+
 def batch512_study(dev, flush, K, warmup, chunk, t1_steps, precisions=("bf16x3", "f32", "f64"), single=False):
     """The 512-instance batch, Lawson4, tau = 0.01: ms per time step of each
     precision, the per-instance errors after t1_steps steps against the FP64
@@ -378,7 +395,8 @@ def run_neumann256(args):
     chunk = args.chunk
     with Clocks(0) as clk:
         w, res, prof = neumann256_study(dev, flush, args.steps, args.warmup, chunk, args.t1_steps,
-                                        n=args.n if args.n != 128 else 256)
+                                        n=args.n if args.n != 128 else 256,
+                                        precisions=("bf16x3", "f32", "f64tc", "f64"))
     roofline = mma_roofline(prof["bf16x3"])
     roofline["traffic"] = profiled_traffic("mma_mode_bf16x3_ncu_neumann256.md",
                                            ["mma_mode.cu", "tc_ptx.cuh", "cgl_internal.cuh"])
@@ -391,7 +409,7 @@ def run_neumann256(args):
         "config": {"workload": w.name, "scheme": "lawson4", "tau": w.tau, "grid": list(w.prob.n),
                    "time_steps_per_bench_step": chunk, "T": args.t1_steps * w.tau,
                    "l2": "flushed (256 MiB write) between timed iterations"},
-        "precisions": res, "roofline": roofline,
+        "precisions": res, "roofline": roofline, "roofline_f64tc": oz_roofline(prof["f64tc"]),
         "simt_kernels": {
             "mode_pass_f64": {"achieved_tflops": f64k["flops"] / (f64k["total_ms"] / 1e3) / 1e12,
                               "frac_of_fp64_peak": f64k["flops"] / (f64k["total_ms"] / 1e3) / 1e12 / fp64_peak_tflops()},
@@ -991,12 +1009,14 @@ def main():
             c0 = dirichlet64_gpu(dev, flush, 3, 3)
             workloads["dirichlet64_fd2_c128"] = {"config": c0[0].name, "tau": c0[0].tau, "steps": 200,
                                                  "precision": "f64", "schemes": c0[2]}
-            wn, res_n, prof_n = neumann256_study(dev, flush, 3, 3, 10, 100)
+            wn, res_n, prof_n = neumann256_study(dev, flush, 3, 3, 10, 100,
+                                                 precisions=("bf16x3", "f32", "f64tc", "f64"))
             rl = mma_roofline(prof_n["bf16x3"])
             rl["traffic"] = profiled_traffic("mma_mode_bf16x3_ncu_neumann256.md",
                                              ["mma_mode.cu", "tc_ptx.cuh", "cgl_internal.cuh"])
             workloads["neumann256_lawson4"] = {"config": wn.name, "tau": wn.tau, "T": 100 * wn.tau,
-                                               "precisions": res_n, "roofline_tcgen05": rl}
+                                               "precisions": res_n, "roofline_tcgen05": rl,
+                                               "roofline_f64tc": oz_roofline(prof_n["f64tc"])}
             info_b, res_b, errs_b = batch512_study(dev, flush, 3, 3, 10, 200)
             tpeak = float(measured_peaks().get("bf16_tflops", 1948.7))
             workloads["batch512_lawson4"] = {

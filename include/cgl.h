@@ -67,8 +67,18 @@ enum cgl_scheme {
  *              accumulation (about FP32 accuracy); pointwise work in FP32.
  *              Finite differences only, every n_mu <= 256 (internally the
  *              factors are zero-padded to a multiple of 16 and the BF16
- *              planes' first direction to a multiple of 64). */
-enum cgl_precision { CGL_F64 = 0, CGL_F32 = 1, CGL_BF16X3 = 2 };
+ *              planes' first direction to a multiple of 64).
+ *   CGL_F64_TC complex128 state; FP64-accurate mu-mode products on the
+ *              tensor cores by the Ozaki splitting: each fiber of the state
+ *              and each row of the factor is scaled by a power of two and
+ *              cut into seven signed 7-bit digits, exact in BF16; the 28
+ *              digit products with a + b <= 6 accumulate exactly (levels
+ *              0..5) in FP32 tensor memory and are combined in integer
+ *              arithmetic, so a product is accurate to about 2^-46 of the
+ *              scales (FP64-class).  Pointwise work in FP64.  Finite
+ *              differences only, every n_mu <= 256; not for batches or the
+ *              coupled system. */
+enum cgl_precision { CGL_F64 = 0, CGL_F32 = 1, CGL_BF16X3 = 2, CGL_F64_TC = 3 };
 
 enum cgl_status {
     CGL_OK = 0,

@@ -186,7 +186,7 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
   for (int x = 0; x < kMaxExtra; ++x) f.extra[x] = slot_ptr(p, bufs, sw.extra[x], sw.extra_f[x]);
   const double Nd = (double)p->N;
   const double es = (double)p->elem;
-  const bool f64 = p->precision == CGL_F64;
+  const bool f64 = p->elem == sizeof(double2);
 
   if (sw.stencil) {
     StencilArgs a{};
@@ -218,6 +218,77 @@ int enqueue_sweep(cgl_plan* p, const Sweep& sw, void* u, cudaStream_t s) {
     if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("stencil: ") + cudaGetErrorString(e));
     tm.done(f64 ? "kron_stencil_f64" : "kron_stencil_f32", (8.0 * p->d + 4 + epi_flops(p, sw.op)) * Nd,
             (1.0 + sw.nextra + sw.nout) * Nd * es);
+    return CGL_OK;
+  }
+
+  if (p->precision == CGL_F64_TC) {
+    // FP64 prologue -> per mode: digit slicing + tensor-core pass -> FP64 epilogue
+    OzSeg g{};
+    g.in[0] = static_cast<const double2*>(f.in[0]);
+    g.in[1] = static_cast<const double2*>(f.in[1]);
+    g.nin = sw.nin;
+    g.op = sw.op;
+    for (int r = 0; r < 2; ++r) g.z[r] = static_cast<double*>(p->oz_z[r < sw.nrhs ? r : 0]);
+    for (int x = 0; x < kMaxExtra; ++x) g.ex[x] = static_cast<const double2*>(f.extra[x]);
+    g.nextra = sw.nextra;
+    g.out[0] = static_cast<double2*>(f.out[0]);
+    g.out[1] = static_cast<double2*>(f.out[1]);
+    g.nout = sw.nout;
+    g.N = p->N;
+    g.n1 = p->n[0];
+    g.pitch = p->pitch;
+    g.Npad = p->Npad;
+    {
+      Timer tm(p, s);
+      cudaError_t e = launch_oz_prologue(g, sw.nrhs, s);
+      if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("FP64 prologue: ") + cudaGetErrorString(e));
+      tm.done("oz_prologue", pro_flops(p, sw.op) * Nd, (sw.nin * 16.0 + sw.nrhs * 16.0) * Nd);
+    }
+    for (int mu = 0; mu < p->d; ++mu) {
+      for (int r = 0; r < sw.nrhs; ++r) {
+        OzSliceArgs sl{};
+        sl.z = static_cast<const double*>(p->oz_z[r]);
+        sl.dst = static_cast<__nv_bfloat16*>(p->oz_dig[r]);
+        sl.exps = p->oz_exp[r];
+        sl.n = (int)p->n[mu];
+        sl.P = mma_axis_P(p, mu);
+        sl.Q = mma_axis_Q(p, mu);
+        sl.N = p->Npad;
+        sl.pitch = p->pitch;
+        sl.status = p->status;
+        Timer tm(p, s);
+        cudaError_t e = launch_oz_slice(sl, s);
+        if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("digit slicing: ") + cudaGetErrorString(e));
+        tm.done("oz_slice", 0.0, (16.0 + 28.0) * Nd);
+      }
+      OzLaunch L{};
+      L.n = (int)p->n[mu];
+      L.P = mma_axis_P(p, mu);
+      L.Q = mma_axis_Q(p, mu);
+      L.N = p->Npad;
+      L.pitch = p->pitch;
+      L.nrhs = sw.nrhs;
+      for (int r = 0; r < 2; ++r) {
+        const int rr = r < sw.nrhs ? r : 0;
+        L.tmA[r] = p->oz_tmA[mu][rr];
+        L.tmB[r] = p->tmB[sw.fac[rr]][mu];
+        L.aexp[r] = p->oz_exp[rr];
+        L.bexp[r] = p->fexp[sw.fac[rr]][mu];
+        L.out[r] = static_cast<double*>(p->oz_z[rr]);
+      }
+      L.status = p->status;
+      Timer tm(p, s);
+      cudaError_t e = launch_oz_pass(L, s);
+      if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("tensor-core FP64 pass: ") + cudaGetErrorString(e));
+      // issued tensor flops: 28 digit products of a (2n x 2n) real GEMM per fiber
+      tm.done("oz_mode_f64tc", 28.0 * 8.0 * (double)p->n[mu] * Nd * sw.nrhs, (28.0 + 16.0) * Nd * sw.nrhs);
+    }
+    {
+      Timer tm(p, s);
+      cudaError_t e = launch_oz_epilogue(g, sw.nrhs, p->status, s);
+      if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("FP64 epilogue: ") + cudaGetErrorString(e));
+      tm.done("oz_epilogue", epi_flops(p, sw.op) * Nd, (sw.nrhs * 16.0 + (sw.nextra + sw.nout) * 16.0) * Nd);
+    }
     return CGL_OK;
   }
 
@@ -363,6 +434,12 @@ int launches_per_step(const cgl_plan* p) {
   if (!p->periodic && (p->scheme == CGL_RK4 || p->scheme == CGL_RK2)) return (int)p->sweeps.size();  // stencils
   int per = p->periodic ? 2 * p->d - 1 : p->d;
   if (p->precision == CGL_BF16X3) per = p->d + 2;  // split prologue + d mode passes + plane epilogue
+  if (p->precision == CGL_F64_TC) {
+    // prologue, per mode one slicing launch per rhs and the pass, epilogue
+    int total = 0;
+    for (const Sweep& sw : p->sweeps) total += 2 + p->d * (sw.nrhs + 1);
+    return total;
+  }
   return (int)p->sweeps.size() * per;
 }
 
@@ -414,7 +491,7 @@ int dev_alloc(cgl_plan* p, void** ptr, size_t bytes) {
 
 // Copy an FP64 vector to a working-precision buffer.
 int make_working(cgl_plan* p, const double2* src64, int64_t count, void** dst, cudaStream_t s) {
-  if (p->precision == CGL_F64) {
+  if (p->elem == sizeof(double2)) {
     *dst = (void*)src64;
     return CGL_OK;
   }
@@ -453,6 +530,7 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
           p->fac64[c][mu] = p->fac64[c][same];
           p->fac[c][mu] = p->fac[c][same];
           p->fsplit[c][mu] = p->fsplit[c][same];
+          p->fexp[c][mu] = p->fexp[c][same];
           std::memcpy(p->tmB[c][mu], p->tmB[c][same], kTensorMapBytes);
           continue;
         }
@@ -466,6 +544,12 @@ int build_factors(cgl_plan* p, cudaStream_t s) {
           if ((st = dev_alloc(p, &p->fsplit[c][mu], mma_factor_bytes(n)))) return st;
           CUDA_TRY(launch_factor_split(p->fac64[c][mu], n, p->fsplit[c][mu], s));
           CUDA_TRY(make_factor_tmap(p->tmB[c][mu], p->fsplit[c][mu], n));
+        }
+        if (p->precision == CGL_F64_TC) {
+          if ((st = dev_alloc(p, &p->fsplit[c][mu], oz_factor_bytes(n)))) return st;
+          if ((st = dev_alloc(p, (void**)&p->fexp[c][mu], (size_t)mma_pad16(n) * sizeof(int)))) return st;
+          CUDA_TRY(launch_oz_factor_slice(p->fac64[c][mu], n, p->fsplit[c][mu], p->fexp[c][mu], s));
+          CUDA_TRY(make_factor_tmap(p->tmB[c][mu], p->fsplit[c][mu], n, 7, oz_rows_per_cta(mma_pad16(n))));
         }
         // the host copy of A must stay alive until the upload has completed
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -752,6 +836,7 @@ cudaError_t prepare_kernels(int dev) {
   if ((e = prepare_mode_pass<double>()) != cudaSuccess) return e;
   if ((e = prepare_mode_pass<float>()) != cudaSuccess) return e;
   if ((e = prepare_mma_pass()) != cudaSuccess) return e;
+  if ((e = prepare_oz_pass()) != cudaSuccess) return e;
   if (dev >= 0 && dev < 64) done[dev] = true;
   return cudaSuccess;
 }
@@ -825,7 +910,7 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   if (!(a1 > 0)) return fail(CGL_EINVAL, "alpha1 must be positive");
   if (!(tau > 0)) return fail(CGL_EINVAL, "tau must be positive");
   if (scheme < CGL_STRANG || scheme > CGL_SPLIT4_3T) return fail(CGL_EINVAL, "unknown scheme");
-  if (precision != CGL_F64 && precision != CGL_F32 && precision != CGL_BF16X3)
+  if (precision != CGL_F64 && precision != CGL_F32 && precision != CGL_BF16X3 && precision != CGL_F64_TC)
     return fail(CGL_EINVAL, "unknown precision");
   int nper = 0;
   for (int m = 0; m < d; ++m) {
@@ -842,7 +927,8 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
     if (nper != d) return fail(CGL_EUNSUPPORTED, "the coupled system is periodic (Fourier) only");
     if (scheme == CGL_STRANG3T || scheme == CGL_SPLIT4_3T)
       return fail(CGL_EUNSUPPORTED, "the coupled system has no three-term splittings");
-    if (precision == CGL_BF16X3) return fail(CGL_EUNSUPPORTED, "the coupled system runs in CGL_F64 or CGL_F32");
+    if (precision == CGL_BF16X3 || precision == CGL_F64_TC)
+      return fail(CGL_EUNSUPPORTED, "the coupled system runs in CGL_F64 or CGL_F32");
   }
   const bool periodic = nper == d;
   for (int m = 0; m < d; ++m) {
@@ -860,10 +946,11 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
         if (!std::isfinite(A[m][k])) return fail(CGL_EINVAL, "direction matrices must be finite");
     }
   }
-  if (precision == CGL_BF16X3) {
-    if (periodic) return fail(CGL_EUNSUPPORTED, "BF16x3 applies to the finite-difference mode products only");
+  if (precision == CGL_BF16X3 || precision == CGL_F64_TC) {
+    if (periodic)
+      return fail(CGL_EUNSUPPORTED, "the tensor-core precisions apply to the finite-difference mode products only");
     for (int m = 0; m < d; ++m)
-      if (n[m] > 256) return fail(CGL_EUNSUPPORTED, "BF16x3 needs every n_mu <= 256");
+      if (n[m] > 256) return fail(CGL_EUNSUPPORTED, "the tensor-core precisions need every n_mu <= 256");
   }
 
   cgl_plan* p = new cgl_plan();
@@ -890,7 +977,8 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
   p->precision = precision;
   p->periodic = periodic;
   p->cubic = (a4 == 0.0 && b4 == 0.0);
-  p->elem = precision == CGL_F64 ? sizeof(double2) : sizeof(float2);  // F32 and BF16x3: complex64
+  // F64 and F64_TC: complex128; F32 and BF16x3: complex64
+  p->elem = (precision == CGL_F64 || precision == CGL_F64_TC) ? sizeof(double2) : sizeof(float2);
   switch (scheme) {
     case CGL_STRANG:
     case CGL_STRANG3T:
@@ -955,6 +1043,31 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
       for (int mu = 0; !st && mu < d; ++mu) {
         e = make_state_tmap(p->tmA[mu][r], (mu & 1) ? p->splits_alt[r] : p->splits[r], (int)p->n[mu],
                             mma_axis_P(p, mu), mma_axis_Q(p, mu), p->Npad, p->pitch);
+        if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("tensor map: ") + cudaGetErrorString(e));
+      }
+    }
+  }
+  if (!st && precision == CGL_F64_TC && !minimal) {
+    // FP64 planes and digit planes with the first direction padded to a
+    // multiple of 64, zeroed once (the padding stays zero: the prologue
+    // writes grid points only, slicing turns zero planes into zero digits and
+    // the passes store rows i < n); per-fiber exponents for the largest
+    // fiber count over the modes
+    p->pitch = mma_pitch(p->n[0]);
+    p->Npad = p->N / p->n[0] * p->pitch;
+    int64_t fibers = 0;
+    for (int mu = 0; mu < d; ++mu) fibers = std::max<int64_t>(fibers, p->Npad / p->n[mu]);
+    const int nr = (scheme == CGL_STRANG || scheme == CGL_STRANG3T) ? 1 : 2;
+    for (int r = 0; !st && r < nr; ++r) {
+      st = dev_alloc(p, &p->oz_z[r], 16 * (size_t)p->Npad);
+      if (!st) st = dev_alloc(p, &p->oz_dig[r], 28 * (size_t)p->Npad);
+      if (!st) st = dev_alloc(p, (void**)&p->oz_exp[r], (size_t)fibers * sizeof(int));
+      if (!st && (cudaMemsetAsync(p->oz_z[r], 0, 16 * (size_t)p->Npad, s) != cudaSuccess ||
+                  cudaMemsetAsync(p->oz_dig[r], 0, 28 * (size_t)p->Npad, s) != cudaSuccess))
+        st = fail(CGL_ECUDA, "memset planes");
+      for (int mu = 0; !st && mu < d; ++mu) {
+        e = make_state_tmap(p->oz_tmA[mu][r], p->oz_dig[r], (int)p->n[mu], mma_axis_P(p, mu), mma_axis_Q(p, mu),
+                            p->Npad, p->pitch, 7);
         if (e != cudaSuccess) st = fail(CGL_ECUDA, std::string("tensor map: ") + cudaGetErrorString(e));
       }
     }
@@ -1162,6 +1275,7 @@ int cgl_rel_error(const void* x, const void* y, int64_t count, int precision, do
   if (!x || !y || !out) return fail(CGL_EINVAL, "NULL argument");
   if (count <= 0) return fail(CGL_EINVAL, "count must be positive");
   if (precision == CGL_BF16X3) precision = CGL_F32;  // complex64 state
+  if (precision == CGL_F64_TC) precision = CGL_F64;   // complex128 state
   if (precision != CGL_F64 && precision != CGL_F32) return fail(CGL_EINVAL, "unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
   const int nb = rel_error_blocks(count);

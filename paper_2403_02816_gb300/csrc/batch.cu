@@ -460,7 +460,7 @@ int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, doubl
   *out = nullptr;
   if (count < 1 || !probs) return fail(CGL_EINVAL, "count must be >= 1 and probs non-NULL");
   if (precision != CGL_F64 && precision != CGL_F32 && precision != CGL_BF16X3)
-    return fail(precision < CGL_F64 || precision > CGL_BF16X3 ? CGL_EINVAL : CGL_EUNSUPPORTED,
+    return fail(precision < CGL_F64 || precision > CGL_F64_TC ? CGL_EINVAL : CGL_EUNSUPPORTED,
                 "batches run in CGL_F64, CGL_F32 or CGL_BF16X3");
   if (scheme != CGL_STRANG && scheme != CGL_SPLIT4 && scheme != CGL_LAWSON4 && scheme != CGL_LAWSON2 &&
       scheme != CGL_STRANG3T && scheme != CGL_SPLIT4_3T)

@@ -554,9 +554,11 @@ inline int mma_rows_per_cta(int np) {
   if (np <= 128) return np;
   return (np / 2 + 15) / 16 * 16;
 }
+// nsplit: BF16 planes per component in the box (3 for BF16x3, 7 for the
+// Ozaki digits); rows: output rows per box (0: those of the BF16x3 pass).
 cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N,
-                            int64_t pitch);
-cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n);
+                            int64_t pitch, int nsplit = 3);
+cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n, int nsplit = 3, int rows = 0);
 size_t mma_factor_bytes(int n);
 size_t mma_smem_bytes(int nc);
 cudaError_t prepare_mma_pass();
@@ -593,6 +595,61 @@ cudaError_t launch_split_prologue(const SplitSeg& one, const SplitSeg* segs, int
 cudaError_t launch_plane_epilogue(const EpiSeg& one, const EpiSeg* segs, int nseg, int64_t max_n, int nrhs,
                                   int* status, cudaStream_t s);
 cudaError_t launch_factor_split(const double2* F, int n, void* out, cudaStream_t s);
+
+// oz_mode.cu: FP64-accurate mu-mode product on tcgen05 by the Ozaki
+// splitting (seven exact 7-bit BF16 digits per operand, 28 products in seven
+// exact FP32 level accumulators; complex128 state).
+struct OzLaunch {
+  int n;              // mode length n_mu (<= 256)
+  int64_t P, Q, N;    // faster (first direction padded) / slower products, plane length
+  int64_t pitch;      // mode 1: distance between fibers in the planes
+  int nrhs;
+  const void* tmA[kMaxRhs];  // CUtensorMap of each rhs's 14 digit planes ([digit][re, im])
+  const void* tmB[kMaxRhs];  // CUtensorMap of each rhs's factor digits
+  const int* aexp[kMaxRhs];  // per-fiber exponents of each rhs's state digits
+  const int* bexp[kMaxRhs];  // per-output-row exponents of each rhs's factor digits
+  double* out[kMaxRhs];      // FP64 planes (re, im) per rhs
+  int* status;
+};
+struct OzPassArgs {
+  int n, np;
+  int64_t P, Q, pitch, per_q;
+  int a_mn;
+  int64_t N;
+  int nc, nsub, tmem_cols;
+  const int* aexp[kMaxRhs];
+  const int* bexp[kMaxRhs];
+  double* out[kMaxRhs];
+  int* status;
+};
+struct OzSliceArgs {
+  const double* z;       // FP64 planes [2][N]
+  __nv_bfloat16* dst;    // 14 BF16 planes [digit][re, im][N]
+  int* exps;             // per-fiber exponents (fiber q (mode 1) or q P + p)
+  int n;
+  int64_t P, Q, N, pitch;
+  int* status;
+};
+struct OzSeg {
+  const double2* in[2];
+  int nin;
+  OpArgs op;
+  double* z[2];          // FP64 planes (re, im) per rhs, Npad values each
+  const double2* ex[kMaxExtra];
+  int nextra;
+  double2* out[2];
+  int nout;
+  int64_t N, n1, pitch, Npad;
+};
+int oz_rows_per_cta(int np);
+size_t oz_factor_bytes(int n);
+cudaError_t prepare_oz_pass();
+int64_t oz_build_args(const OzLaunch& L, OzPassArgs* out);
+cudaError_t launch_oz_pass(const OzLaunch& L, cudaStream_t s);
+cudaError_t launch_oz_slice(const OzSliceArgs& a, cudaStream_t s);
+cudaError_t launch_oz_factor_slice(const double2* F, int n, void* out, int* fexp, cudaStream_t s);
+cudaError_t launch_oz_prologue(const OzSeg& g, int nrhs, cudaStream_t s);
+cudaError_t launch_oz_epilogue(const OzSeg& g, int nrhs, int* status, cudaStream_t s);
 
 // norms.cu
 cudaError_t rel_error_device(const void* x, const void* y, int64_t count, int precision,

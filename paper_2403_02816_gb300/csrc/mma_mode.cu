@@ -482,7 +482,7 @@ static CUtensorMapSwizzle k_major_swizzle() {
 //     box (64, K, 2, 1, 3), 128-byte swizzle: [s][two 64-fiber halves][K j][64],
 // K = kStageK; positions j >= n and fiber groups p >= P read as zero.
 cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P, int64_t Q, int64_t N,
-                            int64_t pitch) {
+                            int64_t pitch, int nsplit) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   if ((P > 1 && P % 64 != 0) || (P == 1 && (pitch < n || pitch % 8 != 0))) return cudaErrorInvalidValue;
@@ -491,16 +491,16 @@ cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P,
   CUresult r;
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   if (P == 1) {
-    const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)Q, 2, 3};
+    const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)Q, 2, (cuuint64_t)nsplit};
     const cuuint64_t strides[3] = {(cuuint64_t)pitch * 2, (cuuint64_t)N * 2, (cuuint64_t)N * 4};
-    const cuuint32_t box[4] = {(cuuint32_t)kStageK, (cuuint32_t)kMmaM, 1, 3};
+    const cuuint32_t box[4] = {(cuuint32_t)kStageK, (cuuint32_t)kMmaM, 1, (cuuint32_t)nsplit};
     r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(splits), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, k_major_swizzle(), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {
-    const cuuint64_t dims[5] = {64, (cuuint64_t)n, (cuuint64_t)(P / 64), (cuuint64_t)(2 * Q), 3};
+    const cuuint64_t dims[5] = {64, (cuuint64_t)n, (cuuint64_t)(P / 64), (cuuint64_t)(2 * Q), (cuuint64_t)nsplit};
     const cuuint64_t strides[4] = {(cuuint64_t)P * 2, 128, (cuuint64_t)P * n * 2, (cuuint64_t)N * 4};
-    const cuuint32_t box[5] = {64, (cuuint32_t)kStageK, 2, 1, 3};
+    const cuuint32_t box[5] = {64, (cuuint32_t)kStageK, 2, 1, (cuuint32_t)nsplit};
     r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(splits), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -513,15 +513,15 @@ cudaError_t make_state_tmap(void* map_out, const void* splits, int n, int64_t P,
 // in planes of its first two dimensions, so these are the large ones); one
 // box = nc output rows x kStageK positions j of one component, all three
 // splits ([s][nc rows][K]); rows past 2np read as zero.
-cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n) {
-  const int np = mma_pad16(n), nc = mma_rows_per_cta(np);
+cudaError_t make_factor_tmap(void* map_out, const void* fsplit, int n, int nsplit, int rows) {
+  const int np = mma_pad16(n), nc = rows > 0 ? rows : mma_rows_per_cta(np);
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_out);
   std::memset(m, 0, sizeof(CUtensorMap));
-  const cuuint64_t dims[4] = {(cuuint64_t)np, (cuuint64_t)2 * np, 2, 3};
+  const cuuint64_t dims[4] = {(cuuint64_t)np, (cuuint64_t)2 * np, 2, (cuuint64_t)nsplit};
   const cuuint64_t strides[3] = {(cuuint64_t)4 * np, (cuuint64_t)2 * np, (cuuint64_t)8 * np * np};
-  const cuuint32_t box[4] = {(cuuint32_t)kStageK, (cuuint32_t)nc, 1, 3};
+  const cuuint32_t box[4] = {(cuuint32_t)kStageK, (cuuint32_t)nc, 1, (cuuint32_t)nsplit};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(fsplit), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, k_major_swizzle(), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -201,6 +201,7 @@ extern "C" int cgl_rel_error_noalloc(const void* x, const void* y, int64_t count
   if (count > CGL_REL_ERROR_NOALLOC_MAX_COUNT)
     return fail(CGL_EINVAL, "count exceeds CGL_REL_ERROR_NOALLOC_MAX_COUNT (the static scratch capacity)");
   if (precision == CGL_BF16X3) precision = CGL_F32;  // complex64 state, as cgl_rel_error
+  if (precision == CGL_F64_TC) precision = CGL_F64;   // complex128 state
   if (precision != CGL_F64 && precision != CGL_F32) return fail(CGL_EINVAL, "unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
   double* partial = nullptr;

@@ -91,6 +91,14 @@ struct cgl_plan {
   void* fsplit[2][3] = {{nullptr}};
   alignas(64) unsigned char tmA[3][2][cgl::kTensorMapBytes];
   alignas(64) unsigned char tmB[2][3][cgl::kTensorMapBytes];
+  // FP64-accurate tensor-core path (CGL_F64_TC): per-rhs FP64 planes, 14
+  // BF16 digit planes and per-fiber exponents, their TMA maps per mode; the
+  // factor digits use fsplit / tmB, their per-row exponents fexp
+  void* oz_z[2] = {nullptr, nullptr};
+  void* oz_dig[2] = {nullptr, nullptr};
+  int* oz_exp[2] = {nullptr, nullptr};
+  int* fexp[2][3] = {{nullptr}};
+  alignas(64) unsigned char oz_tmA[3][2][cgl::kTensorMapBytes];
 
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;

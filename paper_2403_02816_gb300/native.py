@@ -24,12 +24,12 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "cgl.h")
 CGL_BC_DIRICHLET, CGL_BC_NEUMANN, CGL_BC_PERIODIC = 0, 1, 2
 CGL_STRANG, CGL_SPLIT4, CGL_LAWSON4, CGL_RK4, CGL_LAWSON2, CGL_RK2 = 0, 1, 2, 3, 4, 5
 CGL_STRANG3T, CGL_SPLIT4_3T = 6, 7
-CGL_F64, CGL_F32, CGL_BF16X3 = 0, 1, 2
+CGL_F64, CGL_F32, CGL_BF16X3, CGL_F64_TC = 0, 1, 2, 3
 CGL_OK, CGL_EINVAL, CGL_ENOMEM, CGL_ECUDA, CGL_EUNSUPPORTED, CGL_ETIMEOUT, CGL_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 
 SCHEMES = {"strang": CGL_STRANG, "split4": CGL_SPLIT4, "lawson4": CGL_LAWSON4, "rk4": CGL_RK4,
            "lawson2": CGL_LAWSON2, "rk2": CGL_RK2, "strang3t": CGL_STRANG3T, "split4_3t": CGL_SPLIT4_3T}
-PRECISIONS = {"f64": CGL_F64, "f32": CGL_F32, "bf16x3": CGL_BF16X3}
+PRECISIONS = {"f64": CGL_F64, "f32": CGL_F32, "bf16x3": CGL_BF16X3, "f64tc": CGL_F64_TC}
 
 
 class CglError(RuntimeError):
@@ -257,7 +257,7 @@ class Plan:
     @property
     def dtype(self):
         import torch
-        return torch.complex128 if self.prec == CGL_F64 else torch.complex64
+        return torch.complex128 if self.prec in (CGL_F64, CGL_F64_TC) else torch.complex64
 
     def _field(self, u):
         count = self.nfield * self.prob.N
@@ -412,7 +412,7 @@ class Batch:
     @property
     def dtype(self):
         import torch
-        return torch.complex128 if self.prec == CGL_F64 else torch.complex64
+        return torch.complex128 if self.prec in (CGL_F64, CGL_F64_TC) else torch.complex64
 
     def pack(self, fields, device="cuda"):
         """numpy arrays (n_1..n_d), one per instance -> packed device tensor."""
