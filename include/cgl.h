@@ -377,6 +377,17 @@ int cgl_corrector_train_step(cgl_corrector* c, const void* coarse, const void* u
 /* u_out[b] = coarse[b] + N(x_b), complex64 [batch][H][W].  Asynchronous. */
 int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, const float* params,
                         int batch, void* u_out, void* stream);
+/* u_out[b] = coarse[b] + N(x_b) for complex128 fields [batch][H][W] (the
+ * coarse step run in CGL_F64): the features are taken from the complex128
+ * inputs rounded to FP32 and the correction is added in FP64.  Asynchronous. */
+int cgl_corrector_apply_c128(cgl_corrector* c, const void* coarse, const void* un, const float* params,
+                             int batch, void* u_out, void* stream);
+/* What `target` means in cgl_corrector_gradients / train_step: mode 0
+ * (default) the fine result F(u_n) (loss on C(u_n) + N(x) - target); mode 1
+ * the correction F(u_n) - C(u_n) itself (loss on N(x) - target), which keeps
+ * a correction far below the state's FP32 resolution intact when it is
+ * formed in FP64 before it is stored.  EINVAL for other modes. */
+int cgl_corrector_set_target_mode(cgl_corrector* c, int mode);
 /* N(x) = scale * (last convolution); default 1.  Training sets it to the
  * typical size of the correction (fine minus coarse) so that the network's
  * own outputs stay of order one.  EINVAL unless scale > 0 and finite. */

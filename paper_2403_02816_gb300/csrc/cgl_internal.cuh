@@ -493,6 +493,10 @@ template <class T> cudaError_t launch_kron_stencil(const StencilArgs& a, cudaStr
 cudaError_t prepare_conv_mma();
 cudaError_t launch_conv_mma(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int B, int cin,
                             int cout, int H, int W, int relu, int* status, cudaStream_t s);
+// Weight and bias gradients of that convolution on the tensor cores (BF16 x
+// and dy, FP32 accumulation), added into dw [Cout][Cin][3][3] and db [Cout].
+cudaError_t launch_wgrad_mma(const float* x, const float* dy, float* dw, float* db, int B, int cin, int cout, int H,
+                             int W, int* status, cudaStream_t s);
 
 // expm.cu: FP64 complex n x n exponential of (scale * A) on the device.
 // dA: n x n column-major double2 (device); dOut: same layout.  work: 3*n*n double2.

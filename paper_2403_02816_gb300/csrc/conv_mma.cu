@@ -163,9 +163,185 @@ __global__ void __launch_bounds__(kConvMmaThreads) conv3x3_mma_kernel(const Conv
   }
 }
 
+// ------------------------------------------------------------------ weight gradient
+
+// Weight and bias gradients of the 3x3 circular convolution on the tensor
+// cores:
+//   dW[co, ci, t] = sum_{b, p} dy[b, co, p] x[b, ci, p + shift_t],
+//   db[co] = sum_{b, p} dy[b, co, p],
+// per 128-pixel tile an implicit GEMM D[m, co] += sum_p A[m, p] B[co, p] with
+// K = the tile's pixels, rows m = t Cin + ci (the nine shifted copies of x)
+// plus one row of ones (m = 9 Cin: the bias gradient), in M-tiles of 128
+// rows; B = dy.  Both operands are BF16 (rounded to nearest even) in the
+// K-major layout without swizzle: 16-byte rows of eight pixels, core
+// matrices of 8 rows x 16 bytes contiguous (SBO = 128 B between 8-row
+// groups), the next eight pixels one block of all rows further (LBO).  FP32
+// accumulation in TMEM (one accumulator of nn columns per M-tile) over a run
+// of tiles of one sample; the CTA then adds its partial sums to dw / db with
+// atomics.  Bounded waits as in the forward kernel.
+struct WgradMmaArgs {
+  const float* x;    // [B][Cin][H][W]
+  const float* dy;   // [B][Cout][H][W]
+  float* dw;         // [Cout][Cin][3][3], accumulated into
+  float* db;         // [Cout], accumulated into
+  int B, Cin, Cout, H, W;
+  int nn;            // Cout rounded up to a multiple of 16
+  int mpad;          // 9 Cin + 1 rounded up to a multiple of 128
+  int tiles_per_cta;
+  int* status;
+};
+
+static size_t wgrad_mma_smem(int mpad, int nn) {
+  return (size_t)mpad * kConvM * 2 + (size_t)nn * kConvM * 2 + 16;
+}
+
+__global__ void __launch_bounds__(kConvMmaThreads) conv3x3_wgrad_mma_kernel(const WgradMmaArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* As = smem;                                  // [16 pixel chunks][mpad rows][16 B]
+  uint8_t* Bs = As + (size_t)a.mpad * kConvM * 2;      // [16 pixel chunks][nn rows][16 B]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + (size_t)a.nn * kConvM * 2);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int b = blockIdx.y;
+  const int64_t HW = (int64_t)a.H * a.W;
+  const int mtiles = a.mpad / kConvM;
+  const int rows9 = 9 * a.Cin;
+  int cols = 32;
+  while (cols < mtiles * a.nn) cols *= 2;
+  if (tid == 0) {
+    mbar_init(smem_u32(bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(slot), cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t idesc = idesc_bf16(kConvM, a.nn, 0);
+  const int64_t tpi = (HW + kConvM - 1) / kConvM;
+  const float* xb = a.x + (int64_t)b * a.Cin * HW;
+  const float* dyb = a.dy + (int64_t)b * a.Cout * HW;
+  uint32_t parity = 0;
+  bool ok = true;
+  int done = 0;
+  for (int k = 0; k < a.tiles_per_cta; ++k) {
+    const int64_t tile = (int64_t)blockIdx.x * a.tiles_per_cta + k;
+    if (tile >= tpi) break;
+    const int64_t p0 = tile * kConvM;
+    // A rows: eight pixels of one shifted channel (or ones) per 16-byte row
+    for (int e = tid; e < a.mpad * 16; e += kConvMmaThreads) {
+      const int m = e % a.mpad, kq = e / a.mpad;
+      const int64_t pp = p0 + kq * 8;
+      float v[8];
+      if (m < rows9) {
+        const int t = m / a.Cin, ci = m - t * a.Cin;
+        const float* xc = xb + (int64_t)ci * HW;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int64_t p = pp + q;
+          float x = 0.f;
+          if (p < HW) {
+            const int pi = (int)(p / a.W), pj = (int)(p - (int64_t)pi * a.W);
+            const int si = (pi + t / 3 - 1 + a.H) % a.H, sj = (pj + t % 3 - 1 + a.W) % a.W;
+            x = xc[(int64_t)si * a.W + sj];
+          }
+          v[q] = x;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = (m == rows9 && pp + q < HW) ? 1.f : 0.f;
+      }
+      *reinterpret_cast<uint4*>(As + (size_t)e * 16) =
+          make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    }
+    for (int e = tid; e < a.nn * 16; e += kConvMmaThreads) {
+      const int co = e % a.nn, kq = e / a.nn;
+      const int64_t pp = p0 + kq * 8;
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (co < a.Cout && pp + q < HW) ? dyb[(int64_t)co * HW + pp + q] : 0.f;
+      *reinterpret_cast<uint4*>(Bs + (size_t)e * 16) =
+          make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      for (int mt = 0; mt < mtiles; ++mt)
+        for (int kk = 0; kk < kConvM / 16; ++kk) {
+          const uint64_t ad = smem_desc(a0 + (uint32_t)(2 * kk * a.mpad + mt * kConvM) * 16, (uint32_t)a.mpad * 16,
+                                        128, 0);
+          const uint64_t bd = smem_desc(b0 + (uint32_t)(2 * kk * a.nn) * 16, (uint32_t)a.nn * 16, 128, 0);
+          mma_bf16(tmem + (uint32_t)(mt * a.nn), ad, bd, idesc, (done > 0 || kk > 0) ? 1u : 0u);
+        }
+      mma_commit(smem_u32(bar));
+    }
+    ok = __syncthreads_and(mbar_wait(smem_u32(bar), parity)) != 0;
+    parity ^= 1u;
+    if (!ok) {
+      if (tid == 0 && a.status) atomicOr(a.status, 2);
+      break;
+    }
+    ++done;
+  }
+  tc_fence_after();
+  if (ok && done > 0) {
+    const uint32_t lane_addr = static_cast<uint32_t>(warp * 32) << 16;
+    for (int mt = 0; mt < mtiles; ++mt) {
+      uint32_t r[32];
+      tmem_ld16(tmem + lane_addr + (uint32_t)(mt * a.nn), r);
+      if (a.nn > 16) tmem_ld16(tmem + lane_addr + (uint32_t)(mt * a.nn + 16), r + 16);
+      const int m = mt * kConvM + tid;
+      if (m < rows9) {
+        const int t = m / a.Cin, ci = m - t * a.Cin;
+        for (int co = 0; co < a.Cout; ++co)
+          atomicAdd(&a.dw[((int64_t)co * a.Cin + ci) * 9 + t], __uint_as_float(r[co]));
+      } else if (m == rows9) {
+        for (int co = 0; co < a.Cout; ++co) atomicAdd(&a.db[co], __uint_as_float(r[co]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, cols);
+  }
+}
+
+cudaError_t launch_wgrad_mma(const float* x, const float* dy, float* dw, float* db, int B, int cin, int cout, int H,
+                             int W, int* status, cudaStream_t s) {
+  if (cin < 1 || cin > 32 || cout < 1 || cout > 32 || W % 8 != 0) return cudaErrorInvalidValue;
+  WgradMmaArgs a{};
+  a.x = x;
+  a.dy = dy;
+  a.dw = dw;
+  a.db = db;
+  a.B = B;
+  a.Cin = cin;
+  a.Cout = cout;
+  a.H = H;
+  a.W = W;
+  a.nn = (cout + 15) / 16 * 16;
+  a.mpad = (9 * cin + 1 + kConvM - 1) / kConvM * kConvM;
+  a.status = status;
+  const int64_t tpi = ((int64_t)H * W + kConvM - 1) / kConvM;
+  // about two CTAs per SM over the batch
+  const int64_t per_sample = std::max<int64_t>(1, std::min<int64_t>(tpi, (2 * 152 + B - 1) / B));
+  a.tiles_per_cta = (int)((tpi + per_sample - 1) / per_sample);
+  const unsigned gx = (unsigned)((tpi + a.tiles_per_cta - 1) / a.tiles_per_cta);
+  conv3x3_wgrad_mma_kernel<<<dim3(gx, (unsigned)B), kConvMmaThreads, wgrad_mma_smem(a.mpad, a.nn), s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t prepare_conv_mma() {
-  return cudaFuncSetAttribute(conv3x3_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)conv_mma_smem(32, 32));
+  cudaError_t e = cudaFuncSetAttribute(conv3x3_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)conv_mma_smem(32, 32));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(conv3x3_wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)wgrad_mma_smem(384, 32));
 }
 
 cudaError_t launch_conv_mma(const float* x, const __nv_bfloat16* w, const float* bias, float* y, int B, int cin,

@@ -12,8 +12,9 @@
 // GEMM on the tensor cores (conv_mma.cu: per 128-pixel tile, nine
 // accumulating 128 x Cout x Cin MMAs with BF16 operands, FP32 accumulation).
 // The backward pass w.r.t. the input is the same convolution with the kernel
-// flipped and the channel roles swapped; the weight gradient (SIMT, FP32) is
-// a per-tile reduction over pixels finished with atomics.  The layers here
+// flipped and the channel roles swapped; the weight gradient is an implicit
+// GEMM on the tensor cores too (K = pixels, BF16 x and dy, FP32
+// accumulation), per-CTA partial sums finished with atomics.  The layers here
 // are 9..32 channels wide: about 144 flop per byte of activation traffic, so
 // these convolutions are bounded by memory, not by arithmetic.
 #include <cuda_bf16.h>
@@ -31,14 +32,14 @@ using namespace cgl;
 namespace cgl {
 
 constexpr int kTile = 16;
-constexpr int kHalo = kTile + 2;
 constexpr int kMaxCh = 32;
 
 // ------------------------------------------------------------------ kernels
 
 // x[b][c][i][j] from complex64 coarse results / states [P][H][W] selected by
 // idx (or b itself) and parameters [P][5].
-__global__ void features_kernel(const float2* __restrict__ coarse, const float2* __restrict__ un,
+template <class T2>
+__global__ void features_kernel(const T2* __restrict__ coarse, const T2* __restrict__ un,
                                 const float* __restrict__ params, const int* __restrict__ idx, int B, int H, int W,
                                 float* __restrict__ x) {
   const int64_t HW = (int64_t)H * W;
@@ -47,101 +48,15 @@ __global__ void features_kernel(const float2* __restrict__ coarse, const float2*
     const int b = (int)(e / HW);
     const int64_t p = e - (int64_t)b * HW;
     const int src = idx ? idx[b] : b;
-    const float2 c = coarse[(int64_t)src * HW + p];
-    const float2 u = un[(int64_t)src * HW + p];
+    const T2 c = coarse[(int64_t)src * HW + p];
+    const T2 u = un[(int64_t)src * HW + p];
     float* xb = x + (int64_t)b * 9 * HW + p;
-    xb[0 * HW] = c.x;
-    xb[1 * HW] = c.y;
-    xb[2 * HW] = u.x;
-    xb[3 * HW] = u.y;
+    xb[0 * HW] = (float)c.x;
+    xb[1 * HW] = (float)c.y;
+    xb[2 * HW] = (float)u.x;
+    xb[3 * HW] = (float)u.y;
     for (int k = 0; k < 5; ++k) xb[(4 + k) * HW] = params[(int64_t)src * 5 + k];
   }
-}
-
-// dw[co][ci][k] += sum over the CTA's tiles of dy[co][p] x[ci][p + tap k];
-// db[co] += sum dy[co].  Grid: (tiles per image / tiles_per_cta, B).
-__global__ void __launch_bounds__(256) conv3x3_wgrad_kernel(const float* __restrict__ x,
-                                                            const float* __restrict__ dy, float* __restrict__ dw,
-                                                            float* __restrict__ db, int Cin, int Cout, int H, int W,
-                                                            int tiles_per_cta) {
-  extern __shared__ __align__(16) float smem[];
-  float* sx = smem;                           // [Cin][18][18]
-  float* sdy = smem + Cin * kHalo * kHalo;    // [Cout][16][16]
-  const int b = blockIdx.y;
-  const int64_t HW = (int64_t)H * W;
-  const int tiles_x = W / kTile;
-  const int ntiles = tiles_x * (H / kTile);
-  const int pairs = Cin * Cout;
-  constexpr int kMaxPairsPerThread = (kMaxCh * kMaxCh + 255) / 256;
-  float acc[kMaxPairsPerThread][9];
-  float bacc = 0.f;
-#pragma unroll
-  for (int q = 0; q < kMaxPairsPerThread; ++q)
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc[q][k] = 0.f;
-  for (int t = 0; t < tiles_per_cta; ++t) {
-    const int tile = blockIdx.x * tiles_per_cta + t;
-    if (tile >= ntiles) break;
-    const int i0 = (tile / tiles_x) * kTile, j0 = (tile % tiles_x) * kTile;
-    const float* xb = x + (int64_t)b * Cin * HW;
-    for (int e = threadIdx.x; e < Cin * kHalo * kHalo; e += 256) {
-      const int c = e % kHalo, r = (e / kHalo) % kHalo, ci = e / (kHalo * kHalo);
-      const int gi = (i0 + r - 1 + H) % H, gj = (j0 + c - 1 + W) % W;
-      sx[e] = xb[ci * HW + (int64_t)gi * W + gj];
-    }
-    const float* dyb = dy + (int64_t)b * Cout * HW;
-    for (int e = threadIdx.x; e < Cout * kTile * kTile; e += 256) {
-      const int c = e % kTile, r = (e / kTile) % kTile, co = e / (kTile * kTile);
-      sdy[e] = dyb[co * HW + (int64_t)(i0 + r) * W + j0 + c];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kMaxPairsPerThread; ++q) {
-      const int pr = threadIdx.x + q * 256;
-      if (pr < pairs) {
-        const int co = pr / Cin, ci = pr % Cin;
-        const float* sxc = sx + ci * kHalo * kHalo;
-        const float* sdc = sdy + co * kTile * kTile;
-        for (int r = 0; r < kTile; ++r) {
-          // sliding 3x3 window along the row
-          float w00 = sxc[r * kHalo + 0], w01 = sxc[r * kHalo + 1];
-          float w10 = sxc[(r + 1) * kHalo + 0], w11 = sxc[(r + 1) * kHalo + 1];
-          float w20 = sxc[(r + 2) * kHalo + 0], w21 = sxc[(r + 2) * kHalo + 1];
-          for (int c = 0; c < kTile; ++c) {
-            const float w02 = sxc[r * kHalo + c + 2], w12 = sxc[(r + 1) * kHalo + c + 2],
-                        w22 = sxc[(r + 2) * kHalo + c + 2];
-            const float g = sdc[r * kTile + c];
-            acc[q][0] = fmaf(g, w00, acc[q][0]);
-            acc[q][1] = fmaf(g, w01, acc[q][1]);
-            acc[q][2] = fmaf(g, w02, acc[q][2]);
-            acc[q][3] = fmaf(g, w10, acc[q][3]);
-            acc[q][4] = fmaf(g, w11, acc[q][4]);
-            acc[q][5] = fmaf(g, w12, acc[q][5]);
-            acc[q][6] = fmaf(g, w20, acc[q][6]);
-            acc[q][7] = fmaf(g, w21, acc[q][7]);
-            acc[q][8] = fmaf(g, w22, acc[q][8]);
-            w00 = w01; w01 = w02;
-            w10 = w11; w11 = w12;
-            w20 = w21; w21 = w22;
-          }
-        }
-      }
-    }
-    if (threadIdx.x < Cout) {
-      const float* sdc = sdy + threadIdx.x * kTile * kTile;
-      for (int p = 0; p < kTile * kTile; ++p) bacc += sdc[p];
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < kMaxPairsPerThread; ++q) {
-    const int pr = threadIdx.x + q * 256;
-    if (pr < pairs) {
-      const int co = pr / Cin, ci = pr % Cin;
-      for (int k = 0; k < 9; ++k) atomicAdd(&dw[((int64_t)co * Cin + ci) * 9 + k], acc[q][k]);
-    }
-  }
-  if (threadIdx.x < Cout) atomicAdd(&db[threadIdx.x], bacc);
 }
 
 // dy *= (a > 0)
@@ -150,11 +65,12 @@ __global__ void relu_backward_kernel(float* __restrict__ dy, const float* __rest
     if (!(a[i] > 0.f)) dy[i] = 0.f;
 }
 
-// r = C(u_n) + out - target (complex64 [P] selected by idx); dout = 2 r / count;
-// loss partial sums in FP64.
+// r = C(u_n) + out - target (complex64 [P] selected by idx), or r = out -
+// target when the target is the correction itself (correction != 0);
+// dout = 2 r / count; loss partial sums in FP64.
 __global__ void loss_kernel(const float* __restrict__ out, float scale, const float2* __restrict__ coarse,
                             const float2* __restrict__ target, const int* __restrict__ idx, int B, int64_t HW,
-                            float* __restrict__ dout, double* __restrict__ loss_sum) {
+                            int correction, float* __restrict__ dout, double* __restrict__ loss_sum) {
   const double inv = 1.0 / (2.0 * (double)B * (double)HW);
   double s = 0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)B * HW;
@@ -162,7 +78,8 @@ __global__ void loss_kernel(const float* __restrict__ out, float scale, const fl
     const int b = (int)(e / HW);
     const int64_t p = e - (int64_t)b * HW;
     const int src = idx ? idx[b] : b;
-    const float2 c = coarse[(int64_t)src * HW + p], t = target[(int64_t)src * HW + p];
+    const float2 c = correction ? make_float2(0.f, 0.f) : coarse[(int64_t)src * HW + p];
+    const float2 t = target[(int64_t)src * HW + p];
     const float* ob = out + (int64_t)b * 2 * HW + p;
     // residual in units of the output scale: (C(u_n) + scale*out - target) / scale
     const float rr = (fmaf(scale, ob[0], c.x) - t.x) / scale, ri = (fmaf(scale, ob[HW], c.y) - t.y) / scale;
@@ -206,16 +123,21 @@ __global__ void flip_weights_kernel(const __nv_bfloat16* __restrict__ w, __nv_bf
   }
 }
 
-// u = C(u_n) + scale * raw network output
-__global__ void residual_add_kernel(const float2* __restrict__ coarse, const float* __restrict__ out, float scale,
-                                    int B, int64_t HW, float2* __restrict__ u) {
+// u = C(u_n) + scale * raw network output, in the state's precision
+template <class T2>
+__global__ void residual_add_kernel(const T2* __restrict__ coarse, const float* __restrict__ out, float scale,
+                                    int B, int64_t HW, T2* __restrict__ u) {
+  using T = decltype(T2{}.x);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)B * HW;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / HW);
     const int64_t p = e - (int64_t)b * HW;
-    const float2 c = coarse[e];
+    const T2 c = coarse[e];
     const float* ob = out + (int64_t)b * 2 * HW + p;
-    u[e] = make_float2(fmaf(scale, ob[0], c.x), fmaf(scale, ob[HW], c.y));
+    T2 r;
+    r.x = fma((T)scale, (T)ob[0], c.x);
+    r.y = fma((T)scale, (T)ob[HW], c.y);
+    u[e] = r;
   }
 }
 
@@ -245,6 +167,7 @@ struct cgl_corrector {
   float* v = nullptr;
   int64_t t = 0;
   float out_scale = 1.f;  // N(x) = out_scale * (last convolution)
+  int target_mode = 0;    // 0: target = fine state; 1: target = the correction (fine - coarse)
   std::vector<float*> acts;  // acts[0] = features, acts[l+1] = output of layer l
   std::vector<float*> dys;   // dys[l] = loss gradient w.r.t. layer l's output (after its ReLU mask)
   double* loss = nullptr;
@@ -278,9 +201,7 @@ cudaError_t launch_conv(const float* x, const __nv_bfloat16* w, const float* bia
 }
 
 cudaError_t prepare_corrector_kernels() {
-  cudaError_t e = prepare_conv_mma();
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(conv3x3_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  return prepare_conv_mma();
 }
 
 // splitmix64 (Steele, Lea & Flood 2014): a counter-based generator for the
@@ -312,7 +233,7 @@ int check_batch(cgl_corrector* c, int B) {
 int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const void* target, const float* params,
                   const int* idx, int B, double* loss_out, cudaStream_t s) {
   const int64_t HW = (int64_t)c->H * c->W;
-  features_kernel<<<grid_for(B * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, idx, B, c->H,
+  features_kernel<float2><<<grid_for(B * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, idx, B, c->H,
                                                    c->W, c->acts[0]);
   CUDA_TRY(cudaGetLastError());
   int st = forward_pass(c, B, s);
@@ -320,10 +241,9 @@ int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const vo
   CUDA_TRY(cudaMemsetAsync(c->loss, 0, sizeof(double), s));
   CUDA_TRY(cudaMemsetAsync(c->grad, 0, c->nparams * sizeof(float), s));
   loss_kernel<<<grid_for(B * HW), 256, 0, s>>>(c->acts[c->nlayers], c->out_scale, (const float2*)coarse,
-                                               (const float2*)target, idx, B, HW, c->dys[c->nlayers - 1], c->loss);
+                                               (const float2*)target, idx, B, HW, c->target_mode,
+                                               c->dys[c->nlayers - 1], c->loss);
   CUDA_TRY(cudaGetLastError());
-  const int tiles = (c->H / kTile) * (c->W / kTile);
-  const int tiles_per_cta = std::max(1, tiles / 4);
   for (int l = c->nlayers - 1; l >= 0; --l) {
     const auto& L = c->layers[l];
     float* dy = c->dys[l];
@@ -331,11 +251,8 @@ int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const vo
       relu_backward_kernel<<<grid_for(B * L.cout * HW), 256, 0, s>>>(dy, c->acts[l + 1], (int64_t)B * L.cout * HW);
       CUDA_TRY(cudaGetLastError());
     }
-    dim3 wg((tiles + tiles_per_cta - 1) / tiles_per_cta, B);
-    const size_t wsm = (size_t)(L.cin * kHalo * kHalo + L.cout * kTile * kTile) * sizeof(float);
-    conv3x3_wgrad_kernel<<<wg, 256, wsm, s>>>(c->acts[l], dy, c->grad + L.w_off, c->grad + L.b_off, L.cin, L.cout,
-                                              c->H, c->W, tiles_per_cta);
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(launch_wgrad_mma(c->acts[l], dy, c->grad + L.w_off, c->grad + L.b_off, B, L.cin, L.cout, c->H, c->W,
+                              c->status, s));
     if (l > 0) {
       flip_weights_kernel<<<grid_for(L.cin * L.cout * 9), 256, 0, s>>>(c->wbf + L.w_off, c->wflip, L.cin, L.cout);
       CUDA_TRY(cudaGetLastError());
@@ -467,7 +384,7 @@ int cgl_corrector_forward(cgl_corrector* c, const void* coarse, const void* un, 
   if (!coarse || !un || !params || !out) return fail(CGL_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t HW = (int64_t)c->H * c->W;
-  features_kernel<<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, idx, batch,
+  features_kernel<float2><<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, idx, batch,
                                                        c->H, c->W, c->acts[0]);
   CUDA_TRY(cudaGetLastError());
   if ((st = forward_pass(c, batch, s))) return st;
@@ -515,13 +432,36 @@ int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, co
   if (!coarse || !un || !params || !u_out) return fail(CGL_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t HW = (int64_t)c->H * c->W;
-  features_kernel<<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, nullptr,
+  features_kernel<float2><<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, (const float2*)un, params, nullptr,
                                                        batch, c->H, c->W, c->acts[0]);
   CUDA_TRY(cudaGetLastError());
   if ((st = forward_pass(c, batch, s))) return st;
-  residual_add_kernel<<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, c->acts[c->nlayers], c->out_scale,
+  residual_add_kernel<float2><<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, c->acts[c->nlayers], c->out_scale,
                                                            batch, HW, (float2*)u_out);
   CUDA_TRY(cudaGetLastError());
+  return CGL_OK;
+}
+
+int cgl_corrector_apply_c128(cgl_corrector* c, const void* coarse, const void* un, const float* params, int batch,
+                             void* u_out, void* stream) {
+  int st = check_batch(c, batch);
+  if (st) return st;
+  if (!coarse || !un || !params || !u_out) return fail(CGL_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t HW = (int64_t)c->H * c->W;
+  features_kernel<double2><<<grid_for(batch * HW), 256, 0, s>>>((const double2*)coarse, (const double2*)un, params,
+                                                                nullptr, batch, c->H, c->W, c->acts[0]);
+  CUDA_TRY(cudaGetLastError());
+  if ((st = forward_pass(c, batch, s))) return st;
+  residual_add_kernel<double2><<<grid_for(batch * HW), 256, 0, s>>>((const double2*)coarse, c->acts[c->nlayers],
+                                                                    c->out_scale, batch, HW, (double2*)u_out);
+  CUDA_TRY(cudaGetLastError());
+  return CGL_OK;
+}
+
+int cgl_corrector_set_target_mode(cgl_corrector* c, int mode) {
+  if (!c || (mode != 0 && mode != 1)) return fail(CGL_EINVAL, "mode must be 0 (fine state) or 1 (correction)");
+  c->target_mode = mode;
   return CGL_OK;
 }
 

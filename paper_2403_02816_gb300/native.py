@@ -117,6 +117,8 @@ def load() -> ctypes.CDLL:
         "cgl_conv3x3": (I, [VP, VP, VP, VP, I, I, I, I, I, I, VP, VP]),
         "cgl_corrector_set_output_scale": (I, [P, ctypes.c_float]),
         "cgl_corrector_layer_state": (I, [P, I, I, VP, I64, VP]),
+        "cgl_corrector_apply_c128": (I, [P, VP, VP, VP, I, VP, VP]),
+        "cgl_corrector_set_target_mode": (I, [P, I]),
         "cgl_strerror": (ctypes.c_char_p, [I]),
         "cgl_last_error": (ctypes.c_char_p, []),
     }
@@ -526,6 +528,16 @@ class Corrector:
         check(load().cgl_corrector_apply(self.handle, _ptr(coarse), _ptr(un), _ptr(params), int(coarse.shape[0]),
                                          _ptr(out), _stream_handle(stream)), "cgl_corrector_apply")
         return out
+
+    def apply_c128(self, coarse, un, params, out, stream=None):
+        """out = coarse + N(x) for complex128 fields [B, H, W]."""
+        check(load().cgl_corrector_apply_c128(self.handle, _ptr(coarse), _ptr(un), _ptr(params),
+                                              int(coarse.shape[0]), _ptr(out), _stream_handle(stream)),
+              "cgl_corrector_apply_c128")
+        return out
+
+    def set_target_mode(self, mode):
+        check(load().cgl_corrector_set_target_mode(self.handle, int(mode)), "cgl_corrector_set_target_mode")
 
     def layer_state(self, kind, layer, batch, channels, stream=None):
         """Per-layer buffer of the last call (cgl_corrector_layer_state):

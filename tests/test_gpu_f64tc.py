@@ -77,8 +77,12 @@ def test_linear_flow(n, bc):
 
 def test_product_equals_fp64_product_of_the_plan_factors():
     """The Tucker operator on the tensor cores against the same product in
-    FP64 (numpy) with the plan's own FP64 factors: isolates the digit
-    arithmetic from the factor computation, to 1e-14."""
+    FP64 (numpy) with the plan's own FP64 factors, isolating the digit
+    arithmetic from the factor computation.  Each of the K = 2n products of
+    a sum is truncated below 2^-46 of the product of its row scales (the
+    per-fiber and per-row powers of two above the largest entries), so a
+    sum of random-sign terms errs by about sqrt(K) 2^-46 of the scales, a
+    few 1e-13 relative to the result; bound 1e-12 (as one linear flow)."""
     for n, bc in (((48, 7), (0, 1)), ((256, 40), (1, 0)), ((30, 20, 70), (1, 1, 0))):
         p, rng = rand_problem(3, n, bc)
         U = rng.standard_normal(p.n) + 1j * rng.standard_normal(p.n)
@@ -90,7 +94,7 @@ def test_product_equals_fp64_product_of_the_plan_factors():
         want = U
         for mu, F in enumerate(fac):
             want = np.moveaxis(np.tensordot(F, want, axes=([1], [mu])), 0, mu)
-        assert O.rel_l2(got, want) <= 1e-14, (n, O.rel_l2(got, want))
+        assert O.rel_l2(got, want) <= 1e-12, (n, O.rel_l2(got, want))
 
 
 SCHEME_CASES = [((128, 32), (0, 1)), ((128, 16, 32), (1, 0, 1)), ((64,), (0,)), ((50, 33), (0, 1)),
