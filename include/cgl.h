@@ -388,6 +388,13 @@ int cgl_corrector_apply_c128(cgl_corrector* c, const void* coarse, const void* u
  * a correction far below the state's FP32 resolution intact when it is
  * formed in FP64 before it is stored.  EINVAL for other modes. */
 int cgl_corrector_set_target_mode(cgl_corrector* c, int mode);
+/* How N(x) is scaled: mode 0 (default) N = s a, s the output scale, a the
+ * last convolution; mode 1 N_b = s r_b a_b per sample b, r_b the RMS over
+ * the sample of |C(u_n) - u_n| (the coarse increment), so that the network
+ * predicts the correction relative to the size of the step it corrects.
+ * Applies to forward, gradients / train_step (the loss is measured in units
+ * of each sample's scale) and both apply calls.  EINVAL for other modes. */
+int cgl_corrector_set_scale_mode(cgl_corrector* c, int mode);
 /* N(x) = scale * (last convolution); default 1.  Training sets it to the
  * typical size of the correction (fine minus coarse) so that the network's
  * own outputs stay of order one.  EINVAL unless scale > 0 and finite. */

@@ -111,8 +111,9 @@ def loss_and_grads(weights, x, coarse, target, round_weights=True, out_scale=1.0
     of out_scale (i.e. the mean of ((C + N - F) / out_scale)^2); gradients by
     backpropagation (BF16 weights in the forward pass, gradients taken with
     respect to those weights; with round_acts the incoming gradient of each
-    input-gradient convolution is rounded to BF16 too, the weight gradients
-    use the unrounded activations and gradients).  Returns (loss, grads, N(x))."""
+    input-gradient convolution is rounded to BF16 too, and so are both
+    operands of each weight-gradient product -- the operand precision of a
+    BF16 tensor-core implementation).  Returns (loss, grads, N(x))."""
     acts = forward(weights, x, round_weights, round_acts)
     out = out_scale * acts[-1]
     pred_re = coarse.real + out[:, 0]
@@ -126,7 +127,10 @@ def loss_and_grads(weights, x, coarse, target, round_weights=True, out_scale=1.0
         w, b = weights[l]
         if l < len(weights) - 1:
             dy = dy * (acts[l + 1] > 0)
-        dw, db = conv3x3_weight_grad(acts[l], dy)
+        if round_acts:
+            dw, db = conv3x3_weight_grad(bf16_round(acts[l]).astype(np.float64), bf16_round(dy).astype(np.float64))
+        else:
+            dw, db = conv3x3_weight_grad(acts[l], dy)
         grads[l] = (dw, db)
         if l > 0:
             dy = conv3x3_adjoint(bf16_round(dy) if round_acts else dy, bf16_round(w) if round_weights else w)

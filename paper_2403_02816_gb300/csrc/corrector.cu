@@ -68,7 +68,8 @@ __global__ void relu_backward_kernel(float* __restrict__ dy, const float* __rest
 // r = C(u_n) + out - target (complex64 [P] selected by idx), or r = out -
 // target when the target is the correction itself (correction != 0);
 // dout = 2 r / count; loss partial sums in FP64.
-__global__ void loss_kernel(const float* __restrict__ out, float scale, const float2* __restrict__ coarse,
+__global__ void loss_kernel(const float* __restrict__ out, const float* __restrict__ scales,
+                            const float2* __restrict__ coarse,
                             const float2* __restrict__ target, const int* __restrict__ idx, int B, int64_t HW,
                             int correction, float* __restrict__ dout, double* __restrict__ loss_sum) {
   const double inv = 1.0 / (2.0 * (double)B * (double)HW);
@@ -78,6 +79,7 @@ __global__ void loss_kernel(const float* __restrict__ out, float scale, const fl
     const int b = (int)(e / HW);
     const int64_t p = e - (int64_t)b * HW;
     const int src = idx ? idx[b] : b;
+    const float scale = scales[b];
     const float2 c = correction ? make_float2(0.f, 0.f) : coarse[(int64_t)src * HW + p];
     const float2 t = target[(int64_t)src * HW + p];
     const float* ob = out + (int64_t)b * 2 * HW + p;
@@ -125,8 +127,8 @@ __global__ void flip_weights_kernel(const __nv_bfloat16* __restrict__ w, __nv_bf
 
 // u = C(u_n) + scale * raw network output, in the state's precision
 template <class T2>
-__global__ void residual_add_kernel(const T2* __restrict__ coarse, const float* __restrict__ out, float scale,
-                                    int B, int64_t HW, T2* __restrict__ u) {
+__global__ void residual_add_kernel(const T2* __restrict__ coarse, const float* __restrict__ out,
+                                    const float* __restrict__ scales, int B, int64_t HW, T2* __restrict__ u) {
   using T = decltype(T2{}.x);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)B * HW;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -134,6 +136,7 @@ __global__ void residual_add_kernel(const T2* __restrict__ coarse, const float* 
     const int64_t p = e - (int64_t)b * HW;
     const T2 c = coarse[e];
     const float* ob = out + (int64_t)b * 2 * HW + p;
+    const float scale = scales[b];
     T2 r;
     r.x = fma((T)scale, (T)ob[0], c.x);
     r.y = fma((T)scale, (T)ob[HW], c.y);
@@ -141,9 +144,43 @@ __global__ void residual_add_kernel(const T2* __restrict__ coarse, const float* 
   }
 }
 
-__global__ void scale_copy_kernel(const float* __restrict__ a, float scale, float* __restrict__ b, int64_t n) {
+// b = scale_s * a for sample s of each [per_sample] block
+__global__ void scale_copy_kernel(const float* __restrict__ a, const float* __restrict__ scale,
+                                  float* __restrict__ b, int64_t n, int64_t per_sample) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = scale * a[i];
+    b[i] = scale[i / per_sample] * a[i];
+}
+
+// Output scale of each sample: mode 0, the output scale itself; mode 1, the
+// output scale times the RMS over the sample of |C(u_n) - u_n| (the coarse
+// increment), which follows the size of the correction from sample to
+// sample.  One block per sample; samples selected by idx (or b).
+template <class T2>
+__global__ void sample_scale_kernel(const T2* __restrict__ coarse, const T2* __restrict__ un,
+                                    const int* __restrict__ idx, int64_t HW, float out_scale, int mode,
+                                    float* __restrict__ scale) {
+  const int b = blockIdx.x;
+  if (mode == 0) {
+    if (threadIdx.x == 0) scale[b] = out_scale;
+    return;
+  }
+  const int src = idx ? idx[b] : b;
+  double acc = 0;
+  for (int64_t p = threadIdx.x; p < HW; p += blockDim.x) {
+    const T2 c = coarse[(int64_t)src * HW + p], u = un[(int64_t)src * HW + p];
+    const double dx = (double)c.x - (double)u.x, dy = (double)c.y - (double)u.y;
+    acc += dx * dx + dy * dy;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    const float r = (float)sqrt(t / (double)HW);
+    scale[b] = out_scale * (r > 0.f ? r : 1.f);
+  }
 }
 
 }  // namespace cgl
@@ -168,6 +205,8 @@ struct cgl_corrector {
   int64_t t = 0;
   float out_scale = 1.f;  // N(x) = out_scale * (last convolution)
   int target_mode = 0;    // 0: target = fine state; 1: target = the correction (fine - coarse)
+  int scale_mode = 0;     // 0: N = out_scale a; 1: N = out_scale rms(C(u_n) - u_n) a, per sample
+  float* sample_scale = nullptr;  // device [max_batch]: the scale of each sample of the last call
   std::vector<float*> acts;  // acts[0] = features, acts[l+1] = output of layer l
   std::vector<float*> dys;   // dys[l] = loss gradient w.r.t. layer l's output (after its ReLU mask)
   double* loss = nullptr;
@@ -240,7 +279,10 @@ int loss_backward(cgl_corrector* c, const void* coarse, const void* un, const vo
   if (st) return st;
   CUDA_TRY(cudaMemsetAsync(c->loss, 0, sizeof(double), s));
   CUDA_TRY(cudaMemsetAsync(c->grad, 0, c->nparams * sizeof(float), s));
-  loss_kernel<<<grid_for(B * HW), 256, 0, s>>>(c->acts[c->nlayers], c->out_scale, (const float2*)coarse,
+  sample_scale_kernel<float2><<<B, 256, 0, s>>>((const float2*)coarse, (const float2*)un, idx, HW, c->out_scale,
+                                                c->scale_mode, c->sample_scale);
+  CUDA_TRY(cudaGetLastError());
+  loss_kernel<<<grid_for(B * HW), 256, 0, s>>>(c->acts[c->nlayers], c->sample_scale, (const float2*)coarse,
                                                (const float2*)target, idx, B, HW, c->target_mode,
                                                c->dys[c->nlayers - 1], c->loss);
   CUDA_TRY(cudaGetLastError());
@@ -309,6 +351,7 @@ int cgl_corrector_create(cgl_corrector** out, int height, int width, int hidden,
   if (!st) st = corr_alloc(c, (void**)&c->m, off * sizeof(float));
   if (!st) st = corr_alloc(c, (void**)&c->v, off * sizeof(float));
   if (!st) st = corr_alloc(c, (void**)&c->loss, sizeof(double));
+  if (!st) st = corr_alloc(c, (void**)&c->sample_scale, (size_t)max_batch * sizeof(float));
   if (!st) st = corr_alloc(c, (void**)&c->status, sizeof(int));
   if (!st && cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) st = fail(CGL_ECUDA, "memset status");
   for (int l = 0; !st && l <= layers; ++l) {
@@ -388,8 +431,11 @@ int cgl_corrector_forward(cgl_corrector* c, const void* coarse, const void* un, 
                                                        c->H, c->W, c->acts[0]);
   CUDA_TRY(cudaGetLastError());
   if ((st = forward_pass(c, batch, s))) return st;
-  scale_copy_kernel<<<grid_for(batch * 2 * HW), 256, 0, s>>>(c->acts[c->nlayers], c->out_scale, out,
-                                                             (int64_t)batch * 2 * HW);
+  sample_scale_kernel<float2><<<batch, 256, 0, s>>>((const float2*)coarse, (const float2*)un, idx, HW,
+                                                    c->out_scale, c->scale_mode, c->sample_scale);
+  CUDA_TRY(cudaGetLastError());
+  scale_copy_kernel<<<grid_for(batch * 2 * HW), 256, 0, s>>>(c->acts[c->nlayers], c->sample_scale, out,
+                                                             (int64_t)batch * 2 * HW, 2 * HW);
   CUDA_TRY(cudaGetLastError());
   return CGL_OK;
 }
@@ -436,8 +482,11 @@ int cgl_corrector_apply(cgl_corrector* c, const void* coarse, const void* un, co
                                                        batch, c->H, c->W, c->acts[0]);
   CUDA_TRY(cudaGetLastError());
   if ((st = forward_pass(c, batch, s))) return st;
-  residual_add_kernel<float2><<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, c->acts[c->nlayers], c->out_scale,
-                                                           batch, HW, (float2*)u_out);
+  sample_scale_kernel<float2><<<batch, 256, 0, s>>>((const float2*)coarse, (const float2*)un, nullptr, HW,
+                                                    c->out_scale, c->scale_mode, c->sample_scale);
+  CUDA_TRY(cudaGetLastError());
+  residual_add_kernel<float2><<<grid_for(batch * HW), 256, 0, s>>>((const float2*)coarse, c->acts[c->nlayers],
+                                                                   c->sample_scale, batch, HW, (float2*)u_out);
   CUDA_TRY(cudaGetLastError());
   return CGL_OK;
 }
@@ -453,9 +502,18 @@ int cgl_corrector_apply_c128(cgl_corrector* c, const void* coarse, const void* u
                                                                 nullptr, batch, c->H, c->W, c->acts[0]);
   CUDA_TRY(cudaGetLastError());
   if ((st = forward_pass(c, batch, s))) return st;
-  residual_add_kernel<double2><<<grid_for(batch * HW), 256, 0, s>>>((const double2*)coarse, c->acts[c->nlayers],
-                                                                    c->out_scale, batch, HW, (double2*)u_out);
+  sample_scale_kernel<double2><<<batch, 256, 0, s>>>((const double2*)coarse, (const double2*)un, nullptr, HW,
+                                                     c->out_scale, c->scale_mode, c->sample_scale);
   CUDA_TRY(cudaGetLastError());
+  residual_add_kernel<double2><<<grid_for(batch * HW), 256, 0, s>>>((const double2*)coarse, c->acts[c->nlayers],
+                                                                    c->sample_scale, batch, HW, (double2*)u_out);
+  CUDA_TRY(cudaGetLastError());
+  return CGL_OK;
+}
+
+int cgl_corrector_set_scale_mode(cgl_corrector* c, int mode) {
+  if (!c || (mode != 0 && mode != 1)) return fail(CGL_EINVAL, "mode must be 0 (global) or 1 (per sample)");
+  c->scale_mode = mode;
   return CGL_OK;
 }
 

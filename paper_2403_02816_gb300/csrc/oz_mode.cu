@@ -10,22 +10,25 @@
 // 2^e above its largest magnitude and cut into seven signed 7-bit digits:
 //   x = 2^e sum_{a=0..6} d_a 2^{-7(a+1)} + r,   |d_0| <= 128, |d_a| <= 64,
 //   |r| <= 2^{e-50}.
-// Small integers are exact in BF16, and the products d_a d'_b are exact in
-// the FP32 tensor-memory accumulators.  Products of one level L = a + b
-// share the weight 2^{-7(L+2)}, so a level is one accumulator: with K = 2n
-// <= 512 terms its partial sums stay below 2^24 for L <= 5
-// (K (2 * 128 * 64 + (L - 1) 64 * 64) <= 2^24), i.e. they are exact whatever
-// the accumulation order and rounding; level 6 (relative weight 2^-42) is
-// kept with FP32 accumulation.  Levels 0..6 are 28 BF16 GEMMs; the dropped
-// products (a + b >= 7) and the remainders r are below 2^-46 of the row
-// scales' product.  The epilogue converts the seven accumulators to
-// integers, combines them in 64-bit integer arithmetic, converts once to
-// FP64 and applies the two power-of-two scales.
+// Digit a is stored as the BF16 value d_a 2^{-7a} (exact: 8 significant
+// bits, and the exponent range holds the scale), so the product of digits a
+// and b carries its weight 2^{-7(a+b)} itself.  Products of one level
+// L = a + b then share one power-of-two scale, and a level is one FP32
+// tensor-memory accumulator whose partial sums are that scale times an
+// integer below 2^24 for L <= 3 (K = 2n <= 512 terms: K (2 * 128 * 64 +
+// (L - 1) 64 * 64) <= 2^24), i.e. exact whatever the accumulation order and
+// rounding.  Levels 4..6 (relative weights 2^-28..2^-42) share a fifth
+// accumulator with FP32 accumulation, whose rounding stays below 2^-46 of
+// level 0.  The 28 products with a + b <= 6 are BF16 GEMMs; the dropped
+// products (a + b >= 7) and the digit remainders r are below 2^-46 of the
+// row scales' product.  The epilogue scales each accumulator by 2^31, converts
+// it to a 64-bit integer (exact for the four exact levels), sums them,
+// converts once to FP64 and applies the two power-of-two scales.
 //
 // A pass is: slice the FP64 state planes of the mode's fibers (per-fiber
 // exponent), then the tensor-core GEMM writing FP64 planes.  One CTA =
-// 128 fibers (TMEM lanes) x nc <= 64 output rows of one component; the seven
-// level accumulators take 7 nc <= 448 TMEM columns.  Pipeline, copy / MMA
+// 128 fibers (TMEM lanes) x nc <= 96 output rows of one component; the five
+// level accumulators take 5 nc <= 480 TMEM columns.  Pipeline, copy / MMA
 // thread roles, bounded waits and the abort path follow the BF16x3 pass.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -87,6 +90,11 @@ __device__ __forceinline__ void digits7(long long v, int* d) {
   d[6] = static_cast<int>(v);
 }
 
+// Digit d (|d| <= 128) of position s as the BF16 value d 2^{-7s} (exact).
+__device__ __forceinline__ __nv_bfloat16 digit_bf16(int d, int s) {
+  return __float2bfloat16_rn(static_cast<float>(d) * __int_as_float((127 - 7 * s) << 23));
+}
+
 __device__ __forceinline__ int64_t oz_plane_index(int64_t i, int64_t n1, int64_t pitch) {
   return pitch == n1 ? i : i + (pitch - n1) * (i / n1);
 }
@@ -115,8 +123,8 @@ __global__ void oz_slice_rows_kernel(const OzSliceArgs a) {
       const int64_t o = a.pitch * q + j;
 #pragma unroll
       for (int s = 0; s < 7; ++s) {
-        a.dst[(2 * s) * a.N + o] = __int2bfloat16_rn(dr[s]);
-        a.dst[(2 * s + 1) * a.N + o] = __int2bfloat16_rn(di[s]);
+        a.dst[(2 * s) * a.N + o] = digit_bf16(dr[s], s);
+        a.dst[(2 * s + 1) * a.N + o] = digit_bf16(di[s], s);
       }
     }
   }
@@ -145,8 +153,8 @@ __global__ void oz_slice_cols_kernel(const OzSliceArgs a) {
       digits7(fixed49(a.z[a.N + o], e), di);
 #pragma unroll
       for (int s = 0; s < 7; ++s) {
-        a.dst[(2 * s) * a.N + o] = __int2bfloat16_rn(dr[s]);
-        a.dst[(2 * s + 1) * a.N + o] = __int2bfloat16_rn(di[s]);
+        a.dst[(2 * s) * a.N + o] = digit_bf16(dr[s], s);
+        a.dst[(2 * s + 1) * a.N + o] = digit_bf16(di[s], s);
       }
     }
   }
@@ -188,8 +196,8 @@ __global__ void oz_factor_slice_kernel(const double2* F, int n, int np, __nv_bfl
     digits7(fixed49(v1, e), d1);
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
-      out[s * total + static_cast<int64_t>(i) * K + col] = __int2bfloat16_rn(d0[s]);
-      out[s * total + static_cast<int64_t>(np + i) * K + col] = __int2bfloat16_rn(d1[s]);
+      out[s * total + static_cast<int64_t>(i) * K + col] = digit_bf16(d0[s], s);
+      out[s * total + static_cast<int64_t>(np + i) * K + col] = digit_bf16(d1[s], s);
     }
   }
 }
@@ -252,7 +260,8 @@ __device__ __forceinline__ double pow2(int k) {
 }
 
 // CTA (tile, half, sub): 128 fibers x output rows [sub nc, (sub + 1) nc) of
-// component c' = half; TMEM columns [L nc, (L + 1) nc) hold level L.
+// component c' = half; TMEM columns [k nc, (k + 1) nc) hold level k for
+// k < 4 and levels 4..6 for k = 4.
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_mode_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
@@ -346,11 +355,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         const bool first = kb == 0 && ks == 0;
 #pragma unroll
         for (int L = 0; L < 7; ++L) {
+          const int acc = L < 4 ? L : 4;
 #pragma unroll
           for (int x = 0; x <= L; ++x) {
             const uint64_t ad = a0 + (so + x * a_sp + ks * a_ks);
             const uint64_t bd = b0 + (so + (L - x) * b_sp + ks * b_ks);
-            mma_bf16(tmem + static_cast<uint32_t>(L * nc), ad, bd, idesc, (first && x == 0) ? 0u : 1u);
+            // the first product into each accumulator overwrites it: (0, L)
+            // for the exact levels, (0, 4) for the shared one
+            mma_bf16(tmem + static_cast<uint32_t>(acc * nc), ad, bd, idesc, (first && x == 0 && L <= 4) ? 0u : 1u);
           }
         }
       }
@@ -400,21 +412,19 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int pitch_s = nc + 1;  // mode 1: FP64 staging tile [128][nc + 1]
     double* stage = reinterpret_cast<double*>(base);
     for (int c0 = 0; c0 < nc; c0 += 16) {
-      uint32_t r[7][16];
+      uint32_t r[5][16];
 #pragma unroll
-      for (int L = 0; L < 7; ++L) tmem_ld16_nowait(tmem + lane_addr + static_cast<uint32_t>(L * nc + c0), r[L]);
+      for (int L = 0; L < 5; ++L) tmem_ld16_nowait(tmem + lane_addr + static_cast<uint32_t>(L * nc + c0), r[L]);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         const int i = sub * nc + c0 + t;  // output row of component `half`
-        long long I = static_cast<long long>(__float2int_rn(__uint_as_float(r[0][t]))) * (1ll << 31);
-        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[1][t]))) * (1ll << 24);
-        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[2][t]))) * (1ll << 17);
-        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[3][t]))) * (1ll << 10);
-        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[4][t]))) * (1ll << 3);
-        I += (__float2int_rn(__uint_as_float(r[5][t])) + 8) >> 4;
-        I += (__float2int_rn(__uint_as_float(r[6][t])) + 1024) >> 11;
-        // sum_L level_L 2^{-7(L+2)} = I 2^{-45}, times 2^{ea + fe[i]}
+        // accumulator k holds 2^{-7k} x an integer (k < 4): times 2^31 it is
+        // an integer; the shared tail is rounded to one
+        long long I = 0;
+#pragma unroll
+        for (int L = 0; L < 5; ++L) I += __float2ll_rn(__uint_as_float(r[L][t]) * 2147483648.0f);
+        // sum_{a,b} d_a d'_b 2^{-7(a+b+2)} = I 2^{-45}, times 2^{ea + fe[i]}
         const double v = static_cast<double>(I) * pow2(ea + (i < np ? fe[i] : 0) - 45);
         if (a.a_mn) {
           if (store_mn && i < n) out[tile0 + a.P * i + m] = v;
@@ -446,7 +456,25 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
 static size_t oz_smem_bytes(int nc) { return kOzStages * static_cast<size_t>(oz_stage_bytes(nc)) + 1024 + 256; }
 
-int oz_rows_per_cta(int np) { return np <= 64 ? np : 64; }
+// Output rows per CTA: the whole np up to 96 rows, else the split of np into
+// blocks of 64..96 rows (rounded up to 16) with the fewest rows past np (five
+// accumulators of nc columns fit the 512 of TMEM up to nc = 96).  Measured on the 256^3 Lawson4
+// step: blocks of 64 rows (four per component) 14.7 ms for the six passes
+// against 16.1 ms with blocks of 96 (three, the last a third past np): the
+// pass runs at the same fraction of the tensor peak with either width, so
+// the rows computed past np decide.
+int oz_rows_per_cta(int np) {
+  if (np <= 96) return np;
+  int best = 0, waste = 1 << 30;
+  for (int nsub = (np + 95) / 96; nsub <= (np + 63) / 64; ++nsub) {
+    const int nc = ((np + nsub - 1) / nsub + 15) / 16 * 16;
+    if (nsub * nc - np < waste) {
+      waste = nsub * nc - np;
+      best = nc;
+    }
+  }
+  return best;
+}
 
 size_t oz_factor_bytes(int n) {
   const size_t np = mma_pad16(n);
@@ -455,7 +483,7 @@ size_t oz_factor_bytes(int n) {
 
 cudaError_t prepare_oz_pass() {
   return cudaFuncSetAttribute(oz_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(oz_smem_bytes(64)));
+                              static_cast<int>(oz_smem_bytes(96)));
 }
 
 int64_t oz_build_args(const OzLaunch& L, OzPassArgs* out) {
@@ -471,7 +499,7 @@ int64_t oz_build_args(const OzLaunch& L, OzPassArgs* out) {
   a.nc = oz_rows_per_cta(a.np);
   a.nsub = (a.np + a.nc - 1) / a.nc;
   int cols = 32;
-  while (cols < 7 * a.nc) cols *= 2;
+  while (cols < 5 * a.nc) cols *= 2;
   a.tmem_cols = cols;
   for (int r = 0; r < kMaxRhs; ++r) {
     a.aexp[r] = L.aexp[r];

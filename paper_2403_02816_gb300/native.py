@@ -119,6 +119,7 @@ def load() -> ctypes.CDLL:
         "cgl_corrector_layer_state": (I, [P, I, I, VP, I64, VP]),
         "cgl_corrector_apply_c128": (I, [P, VP, VP, VP, I, VP, VP]),
         "cgl_corrector_set_target_mode": (I, [P, I]),
+        "cgl_corrector_set_scale_mode": (I, [P, I]),
         "cgl_strerror": (ctypes.c_char_p, [I]),
         "cgl_last_error": (ctypes.c_char_p, []),
     }
@@ -538,6 +539,9 @@ class Corrector:
 
     def set_target_mode(self, mode):
         check(load().cgl_corrector_set_target_mode(self.handle, int(mode)), "cgl_corrector_set_target_mode")
+
+    def set_scale_mode(self, mode):
+        check(load().cgl_corrector_set_scale_mode(self.handle, int(mode)), "cgl_corrector_set_scale_mode")
 
     def layer_state(self, kind, layer, batch, channels, stream=None):
         """Per-layer buffer of the last call (cgl_corrector_layer_state):
