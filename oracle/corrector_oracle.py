@@ -108,17 +108,22 @@ def forward(weights, x, round_weights=True, round_acts=False):
 def loss_and_grads(weights, x, coarse, target, round_weights=True, out_scale=1.0, round_acts=False):
     """Mean squared difference between C(u_n) + N(x), N(x) = out_scale * a_L,
     and the fine result over all B x 2 x H x W real values, measured in units
-    of out_scale (i.e. the mean of ((C + N - F) / out_scale)^2); gradients by
+    of out_scale (i.e. the mean of ((C + N - F) / out_scale)^2; out_scale may
+    hold one value per sample); gradients by
     backpropagation (BF16 weights in the forward pass, gradients taken with
     respect to those weights; with round_acts the incoming gradient of each
     input-gradient convolution is rounded to BF16 too, and so are both
     operands of each weight-gradient product -- the operand precision of a
     BF16 tensor-core implementation).  Returns (loss, grads, N(x))."""
     acts = forward(weights, x, round_weights, round_acts)
-    out = out_scale * acts[-1]
+    # out_scale: one number, or one per sample (shape (B,) or broadcastable to it)
+    s = np.reshape(np.asarray(out_scale, dtype=np.float64), (-1,))
+    s = s if s.size > 1 else s[:1]
+    s4, s3 = s[:, None, None, None], s[:, None, None]
+    out = s4 * acts[-1]
     pred_re = coarse.real + out[:, 0]
     pred_im = coarse.imag + out[:, 1]
-    r_re, r_im = (pred_re - target.real) / out_scale, (pred_im - target.imag) / out_scale
+    r_re, r_im = (pred_re - target.real) / s3, (pred_im - target.imag) / s3
     count = out.size
     loss = float((np.sum(r_re * r_re) + np.sum(r_im * r_im)) / count)
     dy = np.stack([2 * r_re / count, 2 * r_im / count], axis=1)

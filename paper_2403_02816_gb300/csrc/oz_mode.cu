@@ -21,9 +21,10 @@
 // accumulator with FP32 accumulation, whose rounding stays below 2^-46 of
 // level 0.  The 28 products with a + b <= 6 are BF16 GEMMs; the dropped
 // products (a + b >= 7) and the digit remainders r are below 2^-46 of the
-// row scales' product.  The epilogue scales each accumulator by 2^31, converts
-// it to a 64-bit integer (exact for the four exact levels), sums them,
-// converts once to FP64 and applies the two power-of-two scales.
+// row scales' product.  The epilogue turns the four exact levels into their
+// integers (exact 32-bit conversions), rounds the tail at 2^-31 of level 0,
+// combines them in 64-bit integer arithmetic, converts once to FP64 and
+// applies the two power-of-two scales.
 //
 // A pass is: slice the FP64 state planes of the mode's fibers (per-fiber
 // exponent), then the tensor-core GEMM writing FP64 planes.  One CTA =
@@ -419,11 +420,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         const int i = sub * nc + c0 + t;  // output row of component `half`
-        // accumulator k holds 2^{-7k} x an integer (k < 4): times 2^31 it is
-        // an integer; the shared tail is rounded to one
-        long long I = 0;
-#pragma unroll
-        for (int L = 0; L < 5; ++L) I += __float2ll_rn(__uint_as_float(r[L][t]) * 2147483648.0f);
+        // accumulator k < 4 holds 2^{-7k} x an integer below 2^24: scaled by
+        // 2^{7k} it converts to int32 exactly; the shared tail (below 0.06 in
+        // level-0 units) is rounded at 2^-31 of them.  (Conversions to 32-bit
+        // integers: a float-to-int64 conversion per accumulator made the pass
+        // 20% slower.)
+        long long I = static_cast<long long>(__float2int_rn(__uint_as_float(r[0][t]))) * (1ll << 31);
+        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[1][t]) * 128.0f)) * (1ll << 24);
+        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[2][t]) * 16384.0f)) * (1ll << 17);
+        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[3][t]) * 2097152.0f)) * (1ll << 10);
+        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[4][t]) * 2147483648.0f));
         // sum_{a,b} d_a d'_b 2^{-7(a+b+2)} = I 2^{-45}, times 2^{ea + fe[i]}
         const double v = static_cast<double>(I) * pow2(ea + (i < np ? fe[i] : 0) - 45);
         if (a.a_mn) {
