@@ -67,6 +67,8 @@ def parse():
                          "problem at 256^3 in complex64 (HBM roofline, cuFFT yardstick); neumann256: the 3D "
                          "Neumann precision study (FP64 / FP32 / BF16x3 tensor cores)")
     ap.add_argument("--t1-steps", type=int, default=100, help="neumann256: steps of the T=1 error run")
+    ap.add_argument("--precisions", default="bf16x3,f32,f64tc,f64",
+                    help="neumann256: comma-separated precisions to run (errors need f64)")
     ap.add_argument("--corr-traj", type=int, default=96, help="corrector: training trajectories")
     ap.add_argument("--corr-iters", type=int, default=3000, help="corrector: training iterations")
     ap.add_argument("--corr-test", type=int, default=8, help="corrector: held-out trajectories")
@@ -391,28 +393,31 @@ def run_neumann256(args):
     with Clocks(0) as clk:
         w, res, prof = neumann256_study(dev, flush, args.steps, args.warmup, chunk, args.t1_steps,
                                         n=args.n if args.n != 128 else 256,
-                                        precisions=("bf16x3", "f32", "f64tc", "f64"))
-    roofline = mma_roofline(prof["bf16x3"])
-    roofline["traffic"] = profiled_traffic("mma_mode_bf16x3_ncu_neumann256.md",
-                                           ["mma_mode.cu", "tc_ptx.cuh", "cgl_internal.cuh"])
-    f64k = [r for r in prof["f64"] if r["name"] == "mode_pass_f64"][0]
-    f32k = [r for r in prof["f32"] if r["name"] == "mode_pass_f32"][0]
+                                        precisions=tuple(args.precisions.split(",")))
+    head = "bf16x3" if "bf16x3" in res else next(iter(res))
+    rooflines = {}
+    if "bf16x3" in prof:
+        rooflines["roofline"] = mma_roofline(prof["bf16x3"])
+        rooflines["roofline"]["traffic"] = profiled_traffic("mma_mode_bf16x3_ncu_neumann256.md",
+                                                            ["mma_mode.cu", "tc_ptx.cuh", "cgl_internal.cuh"])
+    if "f64tc" in prof:
+        rooflines["roofline_f64tc"] = oz_roofline(prof["f64tc"])
+    simt = {}
+    for prec, name, peak in (("f64", "mode_pass_f64", fp64_peak_tflops()), ("f32", "mode_pass_f32", FP32_PEAK_TFLOPS)):
+        if prec in prof:
+            k = [r for r in prof[prec] if r["name"] == name][0]
+            tf = k["flops"] / (k["total_ms"] / 1e3) / 1e12
+            simt[name] = {"achieved_tflops": tf, "frac_of_peak": tf / peak}
     line = {
-        "metric": METRIC, "value": res["bf16x3"]["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": res["bf16x3"]["ms_per_time_step"] * chunk,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+        "metric": METRIC, "value": res[head]["grid_pt_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": res[head]["ms_per_time_step"] * chunk,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
         "config": {"workload": w.name, "scheme": "lawson4", "tau": w.tau, "grid": list(w.prob.n),
                    "time_steps_per_bench_step": chunk, "T": args.t1_steps * w.tau,
                    "l2": "flushed (256 MiB write) between timed iterations"},
-        "precisions": res, "roofline": roofline, "roofline_f64tc": oz_roofline(prof["f64tc"]),
-        "simt_kernels": {
-            "mode_pass_f64": {"achieved_tflops": f64k["flops"] / (f64k["total_ms"] / 1e3) / 1e12,
-                              "frac_of_fp64_peak": f64k["flops"] / (f64k["total_ms"] / 1e3) / 1e12 / fp64_peak_tflops()},
-            "mode_pass_f32": {"achieved_tflops": f32k["flops"] / (f32k["total_ms"] / 1e3) / 1e12,
-                              "frac_of_fp32_peak": f32k["flops"] / (f32k["total_ms"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
-            "fma_microbenchmark_tflops": measured_fma_peaks()},
-        "kernels": prof, "clocks": clk.summary(),
+        "precisions": res, "simt_kernels": simt, "kernels": prof, "clocks": clk.summary(),
     }
+    line.update(rooflines)
     print(json.dumps(line))
 
 

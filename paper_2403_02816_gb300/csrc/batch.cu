@@ -1,15 +1,18 @@
 // Batched integration of many independent CGL instances (uneven grids,
-// boundary conditions and parameters) with one persistent grouped launch per
-// mu-mode pass and the whole time step replayed as one CUDA graph.
+// boundary conditions and parameters): FP64 / FP32 take one persistent launch
+// per time step (every mu-mode pass of every sweep in one work list, ordered
+// per instance by dependency counters), BF16x3 one grouped launch per
+// pointwise stage and mu-mode pass; the step is replayed as one CUDA graph.
 //
 // Each instance gets its own FP64-computed factors exp(c tau A_mu) (a factor-
 // only plan).  All fields live in one packed buffer: instance i's N_i values
 // start at offset_i = sum_{j<i} N_j.  For every pass (sweep, mode) the host
 // builds a work list of (instance, first fiber, fibers per tile) items ordered
-// by decreasing cost; a fixed grid of CTAs (SMs x resident CTAs) drains it
-// through an atomic counter, so large and small instances share the machine
-// without a launch per instance.  Passes are separated by kernel boundaries:
-// no CTA ever waits for another.
+// by decreasing cost; the lists of a step's passes are concatenated, and a
+// fixed grid of CTAs (SMs x resident CTAs) drains them through an atomic
+// counter, so large and small instances share the machine without a launch
+// per instance or per pass.  An item waits (bounded) until its instance's
+// previous pass has finished; it never waits on a later item.
 //
 // Fibers per tile come from an autotuner: for each (n, contiguous fibers or
 // not, precision, right-hand sides, SM count) it times the mode-pass kernel on
@@ -52,12 +55,19 @@ struct cgl_batch {
   struct Pass {
     int sweep = 0, mu = 0, nrhs = 1;
     size_t smem = 0;
-    int grid = 0;
     int nitems = 0;
-    ModePassArgs* table = nullptr;  // device, one entry per instance
-    BatchItem* items = nullptr;     // device
+    ModePassArgs* table = nullptr;  // device, one entry per instance (inside `tables`)
   };
   std::vector<Pass> passes;
+  // SIMT precisions: the whole step as one persistent launch over every
+  // pass's items (StepArgs); tables of all passes in one array
+  ModePassArgs* tables = nullptr;  // device [npass][count]
+  StepItem* step_items = nullptr;
+  int* need = nullptr;
+  int* prev = nullptr;
+  int step_nitems = 0;
+  size_t step_smem = 0;
+  int step_grid = 0;
   // BF16x3: per sweep, grouped pointwise stages and one grouped tcgen05 pass
   // per mode
   struct MmaMode {
@@ -312,14 +322,22 @@ int enqueue_batch_step(cgl_batch* b, cudaStream_t s) {
     e = launch_plane_epilogue(enone, ms.epi, b->count, ms.max_n, ms.nrhs, b->status, s);
     if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched plane epilogue: ") + cudaGetErrorString(e));
   }
-  for (size_t k = 0; k < b->passes.size(); ++k) {
-    const auto& ps = b->passes[k];
-    CUDA_TRY(cudaMemsetAsync(b->counters + k, 0, sizeof(int), s));
-    cudaError_t e =
-        b->precision == CGL_F64
-            ? launch_batched_mode_pass<double>(ps.table, ps.items, ps.nitems, b->counters + k, ps.nrhs, ps.smem, ps.grid, s)
-            : launch_batched_mode_pass<float>(ps.table, ps.items, ps.nitems, b->counters + k, ps.nrhs, ps.smem, ps.grid, s);
-    if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched mode pass: ") + cudaGetErrorString(e));
+  if (!b->passes.empty()) {
+    const int npass = (int)b->passes.size();
+    CUDA_TRY(cudaMemsetAsync(b->counters, 0, (2 + (size_t)npass * b->count) * sizeof(int), s));
+    StepArgs a{};
+    a.table = b->tables;
+    a.items = b->step_items;
+    a.nitems = b->step_nitems;
+    a.need = b->need;
+    a.prev = b->prev;
+    a.npass = npass;
+    a.count = b->count;
+    a.counter = b->counters;
+    a.status = b->status;
+    cudaError_t e = b->precision == CGL_F64 ? launch_batched_step<double>(a, b->step_smem, b->step_grid, s)
+                                            : launch_batched_step<float>(a, b->step_smem, b->step_grid, s);
+    if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
   }
   return CGL_OK;
 }
@@ -504,6 +522,7 @@ int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, doubl
   const int sms = st ? 0 : sm_count();
   const int nsweeps = (st || precision == CGL_BF16X3) ? 0 : (int)b->plans[0]->sweeps.size();
   const int d_max = 3;
+  std::vector<StepItem> step_items;
   for (int sw = 0; !st && sw < nsweeps; ++sw) {
     for (int mu = 0; !st && mu < d_max; ++mu) {
       // instances with at least mu+1 directions take part in this pass
@@ -538,18 +557,42 @@ int cgl_batch_create(cgl_batch** out, int count, const cgl_problem* probs, doubl
       std::vector<BatchItem> sorted(items.size());
       for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
       ps.nitems = (int)sorted.size();
-      st = batch_alloc(b, (void**)&ps.items, sorted.size() * sizeof(BatchItem));
-      if (!st && cudaMemcpy(ps.items, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) !=
-                     cudaSuccess)
-        st = fail(CGL_ECUDA, "upload work list");
-      if (!st) st = batch_alloc(b, (void**)&ps.table, (size_t)count * sizeof(ModePassArgs));
-      const int per_sm = precision == CGL_F64 ? batched_mode_blocks_per_sm<double>(ps.nrhs, ps.smem)
-                                              : batched_mode_blocks_per_sm<float>(ps.nrhs, ps.smem);
-      ps.grid = (int)std::min<int64_t>((int64_t)per_sm * sms, std::max(1, ps.nitems));
+      const int k = (int)b->passes.size();
+      for (const BatchItem& it : sorted) step_items.push_back(StepItem{k, it.inst, it.tb, it.b0});
       b->passes.push_back(ps);
     }
   }
-  if (!st) st = batch_alloc(b, (void**)&b->counters, std::max<size_t>(1, b->passes.size()) * sizeof(int));
+  // the step list, its dependency tables and the pass tables in one array
+  if (!st && !b->passes.empty()) {
+    const int npass = (int)b->passes.size();
+    std::vector<int> need((size_t)npass * count, 0), prev((size_t)npass * count, -1), last(count, -1);
+    for (const StepItem& it : step_items) need[(size_t)it.pass * count + it.inst] += 1;
+    for (int k = 0; k < npass; ++k)
+      for (int i = 0; i < count; ++i)
+        if (need[(size_t)k * count + i] > 0) {
+          prev[(size_t)k * count + i] = last[i];
+          last[i] = k;
+        }
+    b->step_nitems = (int)step_items.size();
+    for (const auto& ps : b->passes) b->step_smem = std::max(b->step_smem, ps.smem);
+    st = batch_alloc(b, (void**)&b->step_items, step_items.size() * sizeof(StepItem));
+    if (!st) st = batch_alloc(b, (void**)&b->need, need.size() * sizeof(int));
+    if (!st) st = batch_alloc(b, (void**)&b->prev, prev.size() * sizeof(int));
+    if (!st) st = batch_alloc(b, (void**)&b->tables, (size_t)npass * count * sizeof(ModePassArgs));
+    if (!st && (cudaMemcpy(b->step_items, step_items.data(), step_items.size() * sizeof(StepItem),
+                           cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(b->need, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(b->prev, prev.data(), prev.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+      st = fail(CGL_ECUDA, "upload work list");
+    for (int k = 0; !st && k < npass; ++k) b->passes[k].table = b->tables + (size_t)k * count;
+    if (!st) {
+      const int per_sm = precision == CGL_F64 ? batched_step_blocks_per_sm<double>(b->step_smem)
+                                              : batched_step_blocks_per_sm<float>(b->step_smem);
+      b->step_grid = (int)std::min<int64_t>((int64_t)per_sm * sms, std::max(1, b->step_nitems));
+    }
+    if (!st) st = batch_alloc(b, (void**)&b->counters, (2 + (size_t)npass * count) * sizeof(int));
+  }
+  if (!st && !b->counters) st = batch_alloc(b, (void**)&b->counters, 2 * sizeof(int));
   if (st) {
     free_batch(b);
     return st;
@@ -570,7 +613,7 @@ int cgl_batch_info(const cgl_batch* b, int64_t* total_points, int64_t* offsets, 
     *workspace_bytes = (size_t)nw * b->total * b->elem;
   }
   if (launches_per_step) {
-    int l = (int)b->passes.size();
+    int l = b->passes.empty() ? 0 : 1;  // SIMT precisions: one persistent launch per step
     for (const auto& ms : b->msweeps) l += 2 + (int)ms.modes.size();
     *launches_per_step = l;
   }

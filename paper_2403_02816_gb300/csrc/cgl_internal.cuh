@@ -455,7 +455,7 @@ template <class T> cudaError_t prepare_fft_pass();
 template <class T> cudaError_t prepare_mode_pass();
 
 // Mode pass with an explicit number of fibers per CTA (tb), and the
-// persistent grouped variant over many instances (batch.cu).
+// persistent step kernel over many instances (batch.cu).
 struct BatchItem {
   int inst;     // index into the per-instance ModePassArgs table
   int tb;       // fibers per tile
@@ -463,12 +463,28 @@ struct BatchItem {
 };
 int mode_tb_max(int n, int nrhs, size_t elem);
 size_t mode_smem_bytes(int n, int nrhs, size_t elem, int tb);
+// One launch per time step over many instances (batch.cu): the work items of
+// every pass of the step in one list; an item of pass k for instance i runs
+// once every item of instance i's previous pass has finished.
+struct StepItem {
+  int pass;     // pass (sweep, mode) of the step
+  int inst;     // instance
+  int tb;       // fibers per tile
+  int64_t b0;   // first fiber
+};
+struct StepArgs {
+  const ModePassArgs* table;  // [npass][count] pass arguments
+  const StepItem* items;      // pass-major
+  int nitems;
+  const int* need;            // [npass][count]: items of (pass, instance)
+  const int* prev;            // [npass][count]: the instance's previous pass, or -1
+  int npass, count;
+  int* counter;               // [2 + npass count], zeroed before the launch: next item, abort, done counts
+  int* status;
+};
+template <class T> cudaError_t launch_batched_step(const StepArgs& a, size_t smem, int grid, cudaStream_t s);
+template <class T> int batched_step_blocks_per_sm(size_t smem);
 template <class T> cudaError_t launch_mode_pass_tb(const ModePassArgs& a, int tb, cudaStream_t s);
-template <class T>
-cudaError_t launch_batched_mode_pass(const ModePassArgs* table, const BatchItem* items, int nitems, int* counter,
-                                     int nrhs, size_t smem, int grid, cudaStream_t s);
-template <class T> int batched_mode_blocks_per_sm(int nrhs, size_t smem);
-
 // stencil.cu: K x on finite-difference directions (eq. kronsumv as a
 // stencil) fused with a Runge-Kutta stage epilogue; out must not alias x.
 struct StencilArgs {

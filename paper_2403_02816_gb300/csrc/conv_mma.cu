@@ -192,14 +192,15 @@ struct WgradMmaArgs {
 };
 
 static size_t wgrad_mma_smem(int mpad, int nn) {
-  return (size_t)mpad * kConvM * 2 + (size_t)nn * kConvM * 2 + 16;
+  return (size_t)mpad * kConvM * 2 + (size_t)nn * kConvM * 2 + 9 * kConvM * sizeof(int) + 16;
 }
 
 __global__ void __launch_bounds__(kConvMmaThreads) conv3x3_wgrad_mma_kernel(const WgradMmaArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* As = smem;                                  // [16 pixel chunks][mpad rows][16 B]
   uint8_t* Bs = As + (size_t)a.mpad * kConvM * 2;      // [16 pixel chunks][nn rows][16 B]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + (size_t)a.nn * kConvM * 2);
+  int* soff = reinterpret_cast<int*>(Bs + (size_t)a.nn * kConvM * 2);   // [9 taps][128 pixels]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(soff + 9 * kConvM);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int b = blockIdx.y;
@@ -228,6 +229,18 @@ __global__ void __launch_bounds__(kConvMmaThreads) conv3x3_wgrad_mma_kernel(cons
     const int64_t tile = (int64_t)blockIdx.x * a.tiles_per_cta + k;
     if (tile >= tpi) break;
     const int64_t p0 = tile * kConvM;
+    // source offset of each pixel of the tile under each tap (circular
+    // neighbours), -1 past the image
+    {
+      const int64_t p = p0 + tid;
+      const int pi = p < HW ? (int)(p / a.W) : 0, pj = p < HW ? (int)(p - (int64_t)pi * a.W) : 0;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int si = (pi + t / 3 - 1 + a.H) % a.H, sj = (pj + t % 3 - 1 + a.W) % a.W;
+        soff[t * kConvM + tid] = p < HW ? si * a.W + sj : -1;
+      }
+    }
+    __syncthreads();
     // A rows: eight pixels of one shifted channel (or ones) per 16-byte row
     for (int e = tid; e < a.mpad * 16; e += kConvMmaThreads) {
       const int m = e % a.mpad, kq = e / a.mpad;
@@ -236,16 +249,11 @@ __global__ void __launch_bounds__(kConvMmaThreads) conv3x3_wgrad_mma_kernel(cons
       if (m < rows9) {
         const int t = m / a.Cin, ci = m - t * a.Cin;
         const float* xc = xb + (int64_t)ci * HW;
+        const int* so = soff + t * kConvM + kq * 8;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int64_t p = pp + q;
-          float x = 0.f;
-          if (p < HW) {
-            const int pi = (int)(p / a.W), pj = (int)(p - (int64_t)pi * a.W);
-            const int si = (pi + t / 3 - 1 + a.H) % a.H, sj = (pj + t % 3 - 1 + a.W) % a.W;
-            x = xc[(int64_t)si * a.W + sj];
-          }
-          v[q] = x;
+          const int o = so[q];
+          v[q] = o >= 0 ? xc[o] : 0.f;
         }
       } else {
 #pragma unroll

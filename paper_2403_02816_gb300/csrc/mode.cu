@@ -22,8 +22,11 @@ namespace cgl {
 constexpr int kModeThreads = 256;
 constexpr int kModeMaxSmem = 96 * 1024;
 
+// Field loads go to L2 (each value is read once per pass; in the batched
+// step kernel, values another CTA wrote earlier in the same launch must not
+// come from a stale L1 line).
 template <class T2> __device__ __forceinline__ T2 ldm(const void* base, int64_t off) {
-  return reinterpret_cast<const T2*>(base)[off];
+  return __ldcg(reinterpret_cast<const T2*>(base) + off);
 }
 
 // acc += f * z
@@ -239,27 +242,79 @@ __global__ void __launch_bounds__(kModeThreads) mode_pass_kernel(const ModePassA
   mode_tile<T, NRHS>(a, tbmax, (int64_t)blockIdx.x * tbmax, smem_raw);
 }
 
-// Persistent grouped pass over many independent instances: a fixed grid of
-// CTAs pulls work items (instance, first fiber, fibers) from `items` through
-// the atomic `counter` (zeroed before the launch) until the list is empty.
-// Items are ordered by decreasing cost, so the long tiles start first.
-template <class T, int NRHS>
-__global__ void __launch_bounds__(kModeThreads) batched_mode_pass_kernel(const ModePassArgs* __restrict__ table,
-                                                                         const BatchItem* __restrict__ items,
-                                                                         int nitems, int* counter) {
+// Polls of a dependency wait (with a 128 ns sleep each) before the step
+// kernel gives up: about half a second.
+constexpr long long kStepSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// One persistent launch per time step of a batch: CTAs claim items of the
+// pass-major list through counter[0]; an item waits (thread 0, bounded) for
+// done[prev pass][instance] to reach that pass's item count for the
+// instance, runs the tile, and after a device-wide fence counts itself in
+// done[pass][instance].  Items are claimed in list order and only wait on
+// earlier items, which running CTAs hold, so the launch always progresses.
+// A wait that gives up sets bit 1 of *status and counter[1]; every CTA then
+// stops at its next claim.
+template <class T>
+__global__ void __launch_bounds__(kModeThreads) batched_step_kernel(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_item;
+  __shared__ int s_item, s_go;
+  int* abort_flag = a.counter + 1;
+  int* done = a.counter + 2;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    if (threadIdx.x == 0) {
+      s_go = ld_acquire(abort_flag) == 0;
+      s_item = s_go ? atomicAdd(a.counter, 1) : a.nitems;
+      if (s_go && s_item < a.nitems) {
+        const StepItem it = a.items[s_item];
+        const int pk = a.prev[it.pass * a.count + it.inst];
+        if (pk >= 0) {
+          const int* d = done + pk * a.count + it.inst;
+          const int want = a.need[pk * a.count + it.inst];
+          long long spins = 0;
+          while (ld_acquire(d) < want) {
+            if (++spins > kStepSpinLimit || ld_acquire(abort_flag)) {
+              s_go = 0;
+              break;
+            }
+            __nanosleep(128);
+          }
+          if (!s_go) {
+            atomicOr(a.status, 2);
+            atomicExch(abort_flag, 1);
+          }
+        }
+      }
+      __threadfence();
+    }
     __syncthreads();
-    const int it = s_item;
+    const int it = s_item, go = s_go;
     __syncthreads();
-    if (it >= nitems) break;
-    const BatchItem bi = items[it];
-    const ModePassArgs a = table[bi.inst];
-    mode_tile<T, NRHS>(a, bi.tb, bi.b0, smem_raw);
+    if (!go || it >= a.nitems) break;
+    const StepItem si = a.items[it];
+    const ModePassArgs pa = a.table[si.pass * a.count + si.inst];
+    if (pa.f.nrhs > 1) mode_tile<T, 2>(pa, si.tb, si.b0, smem_raw);
+    else mode_tile<T, 1>(pa, si.tb, si.b0, smem_raw);
+    __threadfence();
     __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(done + si.pass * a.count + si.inst, 1);
   }
+}
+
+template <class T> cudaError_t launch_batched_step(const StepArgs& a, size_t smem, int grid, cudaStream_t s) {
+  batched_step_kernel<T><<<grid, kModeThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class T> int batched_step_blocks_per_sm(size_t smem) {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_step_kernel<T>, kModeThreads, smem);
+  return std::max(b, 1);
 }
 
 static int mode_tb(int n, int nrhs, size_t elem, int64_t npencils) {
@@ -292,25 +347,6 @@ template <class T> cudaError_t launch_mode_pass_tb(const ModePassArgs& a, int tb
   return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t launch_batched_mode_pass(const ModePassArgs* table, const BatchItem* items, int nitems, int* counter,
-                                     int nrhs, size_t smem, int grid, cudaStream_t s) {
-  if (nrhs > 1)
-    batched_mode_pass_kernel<T, 2><<<grid, kModeThreads, smem, s>>>(table, items, nitems, counter);
-  else
-    batched_mode_pass_kernel<T, 1><<<grid, kModeThreads, smem, s>>>(table, items, nitems, counter);
-  return cudaGetLastError();
-}
-
-template <class T> int batched_mode_blocks_per_sm(int nrhs, size_t smem) {
-  int b = 0;
-  if (nrhs > 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_mode_pass_kernel<T, 2>, kModeThreads, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_mode_pass_kernel<T, 1>, kModeThreads, smem);
-  return std::max(b, 1);
-}
-
 template <class T> cudaError_t launch_mode_pass(const ModePassArgs& a, cudaStream_t s) {
   using T2 = typename C2<T>::type;
   const int n = (int)a.g.n_ax;
@@ -333,10 +369,7 @@ template <class T> cudaError_t prepare_mode_pass() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(mode_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kModeMaxSmem + 4096);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(batched_mode_pass_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kModeMaxSmem + 4096);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(batched_mode_pass_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(batched_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kModeMaxSmem + 4096);
 }
 
@@ -344,12 +377,10 @@ template cudaError_t prepare_mode_pass<double>();
 template cudaError_t prepare_mode_pass<float>();
 template cudaError_t launch_mode_pass_tb<double>(const ModePassArgs&, int, cudaStream_t);
 template cudaError_t launch_mode_pass_tb<float>(const ModePassArgs&, int, cudaStream_t);
-template cudaError_t launch_batched_mode_pass<double>(const ModePassArgs*, const BatchItem*, int, int*, int, size_t,
-                                                      int, cudaStream_t);
-template cudaError_t launch_batched_mode_pass<float>(const ModePassArgs*, const BatchItem*, int, int*, int, size_t,
-                                                     int, cudaStream_t);
-template int batched_mode_blocks_per_sm<double>(int, size_t);
-template int batched_mode_blocks_per_sm<float>(int, size_t);
+template cudaError_t launch_batched_step<double>(const StepArgs&, size_t, int, cudaStream_t);
+template cudaError_t launch_batched_step<float>(const StepArgs&, size_t, int, cudaStream_t);
+template int batched_step_blocks_per_sm<double>(size_t);
+template int batched_step_blocks_per_sm<float>(size_t);
 
 template cudaError_t launch_mode_pass<double>(const ModePassArgs&, cudaStream_t);
 template cudaError_t launch_mode_pass<float>(const ModePassArgs&, cudaStream_t);

@@ -50,6 +50,9 @@ def test_batch_equals_single_plans_and_oracle(prec, scheme):
     tau, nsteps = 0.01, 4
     dt = torch.complex128 if prec == "f64" else torch.complex64
     with nat.Batch(probs, tau, scheme, prec) as b:
+        # FP64 / FP32: every pass of a step in one persistent launch
+        if prec != "bf16x3":
+            assert b.launches_per_step == 1
         u = b.pack(fields)
         b.step(u, nsteps)
         torch.cuda.synchronize()
