@@ -20,11 +20,11 @@
 // fastest, in memory and in the text file named by $CGL_AUTOTUNE_CACHE.
 //
 // BF16x3 batches run every mode pass on the tensor cores: per sweep one
-// grouped split prologue (a segment per instance), one grouped tcgen05 pass
-// per mode (a device table of per-instance pass arguments and tensor maps;
-// CTA b finds its instance by the CTA prefix sums) and one grouped plane
-// epilogue, over the BF16 / FP32 planes, factor splits and maps that each
-// instance's plan owns.
+// grouped split prologue (a segment per instance), one persistent tcgen05
+// pass per mode (a device table of per-instance pass arguments and tensor
+// maps and a list of (instance, tile) records that the CTAs walk round-robin)
+// and one grouped plane epilogue, over the BF16 / FP32 planes and factor
+// splits that each instance's plan owns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,10 +73,9 @@ struct cgl_batch {
   struct MmaMode {
     void* passes = nullptr;  // device MmaPassArgs[npass]
     void* maps = nullptr;    // device CUtensorMap[4 npass]
-    int* start = nullptr;    // device CTA prefix sums [npass + 1]
+    void* tiles = nullptr;   // device int2 (pass, tile) of every tile per rhs
     int npass = 0;
-    int64_t ctas = 0;
-    size_t smem = 0;
+    int64_t ctas = 0;        // tiles per rhs
   };
   struct MmaSweep {
     int sweep = 0, nrhs = 1;
@@ -315,7 +314,7 @@ int enqueue_batch_step(cgl_batch* b, cudaStream_t s) {
     cudaError_t e = launch_split_prologue(none, ms.pro, b->count, ms.max_n, ms.nrhs, s);
     if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched split prologue: ") + cudaGetErrorString(e));
     for (const auto& md : ms.modes) {
-      e = launch_mma_group(md.passes, md.maps, md.start, md.npass, md.ctas, ms.nrhs, md.smem, s);
+      e = launch_mma_group(md.passes, md.maps, md.tiles, md.npass, md.ctas, ms.nrhs, s);
       if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched tensor-core pass: ") + cudaGetErrorString(e));
     }
     EpiSeg enone{};
@@ -408,6 +407,7 @@ int build_mma_sweeps(cgl_batch* b) {
         }
         L.out_fp32 = mu == p->d - 1;
         L.status = b->status;
+        L.grouped = 1;
         MmaPassArgs a;
         const int64_t c = mma_build_args(L, &a);
         if (c < 0) {
@@ -416,7 +416,13 @@ int build_mma_sweeps(cgl_batch* b) {
           return fail(CGL_EUNSUPPORTED, msg);
         }
         args.push_back(a);
-        for (const void* m : {L.tmA[0], L.tmA[1], L.tmB[0], L.tmB[1]}) {
+        // A maps as the plan's; B maps with the grouped pass's rows per tile
+        alignas(64) unsigned char fm[2][kTensorMapBytes];
+        for (int r = 0; r < 2; ++r) {
+          const int rr = r < w.nrhs ? r : 0;
+          CUDA_TRY(make_factor_tmap(fm[r], p->fsplit[w.fac[rr]][mu], L.n, 3, a.nc));
+        }
+        for (const void* m : {L.tmA[0], L.tmA[1], (const void*)fm[0], (const void*)fm[1]}) {
           const unsigned char* q = static_cast<const unsigned char*>(m);
           maps.insert(maps.end(), q, q + kTensorMapBytes);
         }
@@ -424,35 +430,36 @@ int build_mma_sweeps(cgl_batch* b) {
         cost.push_back((double)c * a.np);
       }
       if (args.empty()) continue;
-      // largest passes first: their CTAs start before the small ones'
+      // largest passes first, so that the CTAs' round-robin shares of the
+      // tiles come out even
       std::vector<size_t> order(args.size());
       std::iota(order.begin(), order.end(), 0);
       std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
       std::vector<MmaPassArgs> sargs(args.size());
       std::vector<unsigned char> smaps(maps.size());
-      std::vector<int> start(args.size() + 1, 0);
+      std::vector<int> tiles;  // (pass, tile) pairs
       cgl_batch::MmaMode md;
-      int64_t total = 0;
       for (size_t k = 0; k < order.size(); ++k) {
         const size_t o = order[k];
         sargs[k] = args[o];
         std::copy(maps.begin() + o * 4 * kTensorMapBytes, maps.begin() + (o + 1) * 4 * kTensorMapBytes,
                   smaps.begin() + k * 4 * kTensorMapBytes);
-        start[k] = (int)total;
-        total += ctas[o];
-        md.smem = std::max(md.smem, mma_smem_bytes(args[o].nc));
+        for (int64_t t = 0; t < ctas[o]; ++t) {
+          tiles.push_back((int)k);
+          tiles.push_back((int)t);
+        }
       }
-      if (total >= (int64_t)1 << 31) return fail(CGL_EUNSUPPORTED, "batch too large for one grouped pass");
-      start[order.size()] = (int)total;
+      const int64_t total = (int64_t)tiles.size() / 2;
+      if (total * ms.nrhs >= (int64_t)1 << 31) return fail(CGL_EUNSUPPORTED, "batch too large for one grouped pass");
       md.npass = (int)sargs.size();
       md.ctas = total;
       st = batch_alloc(b, &md.passes, sargs.size() * sizeof(MmaPassArgs));
       if (!st) st = batch_alloc(b, &md.maps, smaps.size());
-      if (!st) st = batch_alloc(b, (void**)&md.start, start.size() * sizeof(int));
+      if (!st) st = batch_alloc(b, &md.tiles, tiles.size() * sizeof(int));
       if (st) return st;
       CUDA_TRY(cudaMemcpy(md.passes, sargs.data(), sargs.size() * sizeof(MmaPassArgs), cudaMemcpyHostToDevice));
       CUDA_TRY(cudaMemcpy(md.maps, smaps.data(), smaps.size(), cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(md.start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(md.tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice));
       ms.modes.push_back(md);
     }
     b->msweeps.push_back(ms);

@@ -544,6 +544,7 @@ struct MmaLaunch {
   int out_fp32;       // 1: FP32 planes, 0: BF16x3 planes
   void* out[kMaxRhs];
   int* status;
+  int grouped = 0;    // 1: row blocking of the persistent grouped pass (launch_mma_group)
 };
 struct MmaPassArgs {
   int n;             // mode length n_mu (<= 256)
@@ -555,8 +556,9 @@ struct MmaPassArgs {
   int out_fp32;      // 1: FP32 planes (re, im); 0: BF16x3 planes (6)
   void* out[kMaxRhs];
   int64_t N;         // plane length (padded field size)
-  int nc;            // output rows of one component per CTA (multiple of 16, <= 128 when np > 128)
+  int nc;            // output rows per tile (multiple of 16, <= 128 when np > 128)
   int nsub;          // row blocks per component: ceil(np / nc)
+  int both;          // 1: a tile's nc = 2 np rows are both components (grouped pass, np <= 64)
   int tmem_cols;     // power of two >= 2 nc
   int stages;        // pipeline depth
   int* status;
@@ -586,11 +588,12 @@ cudaError_t prepare_mma_pass();
 // unsupported geometry.
 int64_t mma_build_args(const MmaLaunch& L, MmaPassArgs* out);
 cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s);
-// One launch over a group of passes: device arrays of MmaPassArgs, of four
-// CUtensorMaps per pass (A rhs 0 / 1, B rhs 0 / 1) and of npass + 1 CTA
-// prefix sums; smem = the largest mma_smem_bytes(nc) of the group.
-cudaError_t launch_mma_group(const void* passes, const void* maps, const int* start, int npass, int64_t ctas,
-                             int nrhs, size_t smem, cudaStream_t s);
+// One persistent launch over a group of passes (one CTA per SM): device
+// arrays of MmaPassArgs, of four CUtensorMaps per pass (A rhs 0 / 1, B rhs
+// 0 / 1) and of the ntiles (pass, tile within the pass) pairs (int2) of the
+// group, in the order the CTAs take them.
+cudaError_t launch_mma_group(const void* passes, const void* maps, const void* tiles, int npass, int64_t ntiles,
+                             int nrhs, cudaStream_t s);
 // Pointwise stages around the tensor-core passes, one field per segment
 // (planes: first direction padded to `pitch`, Npad values per plane).
 struct SplitSeg {

@@ -66,15 +66,6 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
 
 // ------------------------------------------------------------------ the GEMM pass
 
-// A group of passes in one launch (instances of a batch): CTA b belongs to
-// the pass k with start[k] <= b < start[k + 1].
-struct MmaTable {
-  const MmaPassArgs* passes;  // device, one per pass
-  const CUtensorMap* maps;    // device, four per pass: A of rhs 0 / 1, B of rhs 0 / 1
-  const int* start;           // device, npass + 1 prefix sums of the passes' CTA counts
-  int npass;
-};
-
 // One pipeline stage: three A splits (128 fibers x kStageK) and three B
 // splits (nc output rows x kStageK).
 static __host__ __device__ constexpr uint32_t mma_stage_bytes(int nc) {
@@ -87,31 +78,16 @@ static __host__ __device__ constexpr uint32_t mma_stage_bytes(int nc) {
 // accumulator keeps the accumulator rounding of the many small MMAs relative
 // to the small terms.  Rows i >= n (padding, or the other component's rows
 // when nsub nc > np) are computed and discarded.
-template <bool kTable>
 __global__ void __launch_bounds__(kMmaThreads, 1)
     mma_mode_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                     const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
-                    const MmaPassArgs args, const MmaTable table) {
+                    const MmaPassArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int rhs = blockIdx.y;
-  int64_t bx = blockIdx.x;
+  const int64_t bx = blockIdx.x;
   const CUtensorMap* tmA = rhs ? &tmA1 : &tmA0;
   const CUtensorMap* tmB = rhs ? &tmB1 : &tmB0;
-  int pass = 0;
-  if constexpr (kTable) {
-    int lo = 0, hi = table.npass - 1;  // last pass whose first CTA is <= blockIdx.x
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (table.start[mid] <= bx) lo = mid;
-      else hi = mid - 1;
-    }
-    pass = lo;
-    bx -= table.start[pass];
-    tmA = &table.maps[4 * pass + rhs];
-    tmB = &table.maps[4 * pass + 2 + rhs];
-  }
-  const MmaPassArgs a = kTable ? table.passes[pass] : args;
   const int n = a.n, np = a.np;
   // K = 2 np runs over (component c, position j); a stage holds kStageK
   // values of j of one component (the copies fill j >= n with zeros)
@@ -166,10 +142,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   // and phase advance incrementally (no divisions on the issuing threads).
   int* counters = abort_flag + 1;  // stages loaded / consumed / committed
   if (threadIdx.x == 32) {
-    if constexpr (kTable) {
-      tensormap_acquire(tmA);
-      tensormap_acquire(tmB);
-    }
     int slot = 0, c = 0, j0 = 0, loaded = 0;
     uint32_t phase = 0;
     bool ok = true;
@@ -371,6 +343,345 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   }
 }
 
+// ------------------------------------------------------------------ grouped persistent pass (batches)
+
+// The mode passes of a batch's instances in one persistent launch.  Work
+// item g = (tile g / nrhs of the group, rhs = g mod nrhs); CTA x takes items
+// x, x + G, x + 2G, ... (G = grid size, one CTA per SM).
+struct MmaTable {
+  const MmaPassArgs* passes;  // device, one per pass
+  const CUtensorMap* maps;    // device, four per pass: A of rhs 0 / 1, B of rhs 0 / 1
+  const int2* tiles;          // device, (pass, tile within the pass) of each tile of the group
+  int npass;
+  int nrhs;
+  int64_t items;              // tiles * nrhs
+};
+
+// Warps 0-15: epilogue, in four groups of four (warp w reads TMEM lanes
+// 32 (w mod 4) ...; group w / 4 takes every fourth 16-column chunk); warp 16:
+// copies; warp 17: MMAs and the TMEM allocation.  A ring of kGrpStages stage
+// slots sized for the largest stage (nc = 128) runs across items, and two
+// accumulator pairs in TMEM let the epilogue of one item run under the MMAs
+// of the next.  The epilogue is latency-bound (dependent TMEM loads, splits
+// and stores per chunk), hence its sixteen warps.
+constexpr int kGrpEpiWarps = 16;
+constexpr int kGrpEpiGroups = kGrpEpiWarps / 4;
+constexpr int kGrpCopyWarp = kGrpEpiWarps, kGrpMmaWarp = kGrpEpiWarps + 1;
+constexpr int kGrpThreads = 32 * (kGrpEpiWarps + 2);
+constexpr int kGrpStages = 4;
+constexpr uint32_t kGrpSlotBytes = mma_stage_bytes(128);
+constexpr uint32_t kGrpAccCols = 256;  // columns of one accumulator pair: main [0, nc), corrections [nc, 2nc)
+constexpr size_t kGrpSmem = (size_t)kGrpStages * kGrpSlotBytes + 1024 + 256;
+
+// One work item with its pass's arguments, read once into registers (the
+// inline-asm memory clobbers would otherwise make every use re-read them).
+struct GrpWork {
+  int pass, rhs;
+  int64_t bx;  // tile within the pass
+  int n, np, nc, nsub, both, a_mn, out_fp32;
+  int64_t per_q, P, Q, N, pitch;
+  void* out;
+};
+
+__device__ __forceinline__ GrpWork grp_work(const MmaTable& t, int64_t g) {
+  const int2 e = __ldg(&t.tiles[g / t.nrhs]);
+  GrpWork w;
+  w.pass = e.x;
+  w.bx = e.y;
+  w.rhs = (int)(g % t.nrhs);
+  const MmaPassArgs* a = &t.passes[w.pass];
+  w.n = __ldg(&a->n);
+  w.np = __ldg(&a->np);
+  w.nc = __ldg(&a->nc);
+  w.nsub = __ldg(&a->nsub);
+  w.both = __ldg(&a->both);
+  w.a_mn = __ldg(&a->a_mn);
+  w.out_fp32 = __ldg(&a->out_fp32);
+  w.per_q = __ldg(&a->per_q);
+  w.P = __ldg(&a->P);
+  w.Q = __ldg(&a->Q);
+  w.N = __ldg(&a->N);
+  w.pitch = __ldg(&a->pitch);
+  w.out = a->out[w.rhs];
+  return w;
+}
+
+// Tile bx of a pass: fiber tile, output component (half) and row block
+// (sub); with `both` a tile has every row of both components (half = sub = 0).
+struct GrpTile {
+  int64_t q0, p0;
+  int half, sub;
+};
+
+__device__ __forceinline__ GrpTile grp_tile(const GrpWork& a) {
+  GrpTile g;
+  const int parts = a.both ? 1 : 2 * a.nsub;
+  const int64_t tile = a.bx / parts;
+  const int part = (int)(a.bx % parts);
+  g.half = part / a.nsub;
+  g.sub = part % a.nsub;
+  if (a.a_mn) {
+    g.q0 = tile / a.per_q;
+    g.p0 = (tile - g.q0 * a.per_q) * kMmaM;
+  } else {
+    g.q0 = tile * kMmaM;
+    g.p0 = 0;
+  }
+  return g;
+}
+
+// Bounded wait that also gives up once another role of the CTA has.
+__device__ __forceinline__ bool grp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && *abort_flag) return false;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kGrpThreads, 1) mma_group_kernel(const MmaTable t) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kGrpStages * kGrpSlotBytes);
+  uint64_t* empty = full + kGrpStages;
+  uint64_t* tfull = empty + kGrpStages;  // [2] accumulator pair b written
+  uint64_t* tempty = tfull + 2;          // [2] accumulator pair b read out
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* counters = reinterpret_cast<int*>(tmem_slot + 2);  // stages loaded / consumed / committed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x;
+  constexpr uint32_t a_bytes = kMmaM * kStageK * 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGrpStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), kGrpEpiWarps);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    counters[0] = counters[1] = counters[2] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kGrpMmaWarp) tmem_alloc(smem_u32(tmem_slot), 2 * kGrpAccCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == kGrpCopyWarp && lane == 0) {
+    // copies: every stage of every item of this CTA, as ring slots free up;
+    // the next item's record and arguments are read one item ahead
+    int slot = 0, kc = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    GrpWork nxt;
+    if (blockIdx.x < t.items) nxt = grp_work(t, blockIdx.x);
+    for (int64_t g = blockIdx.x; g < t.items && ok; g += G) {
+      const GrpWork a = nxt;
+      if (g + G < t.items) nxt = grp_work(t, g + G);
+      const CUtensorMap* tmA = &t.maps[4 * a.pass + a.rhs];
+      const CUtensorMap* tmB = &t.maps[4 * a.pass + 2 + a.rhs];
+      tensormap_acquire(tmA);
+      tensormap_acquire(tmB);
+      const GrpTile tl = grp_tile(a);
+      const int np = a.np, nc = a.nc, a_mn = a.a_mn;
+      const int64_t Q = a.Q;
+      const int nk = 2 * ((np + kStageK - 1) / kStageK);
+      const uint32_t stage_bytes = mma_stage_bytes(nc);
+      const int rowB = tl.half * np + tl.sub * nc, pq = (int)(tl.p0 / 64);
+      int c = 0, j0 = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        // the slot's previous stage (kc - kGrpStages) must have been consumed
+        if (kc >= kGrpStages && !grp_wait(smem_u32(&empty[slot]), phase ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const uint32_t st = smem_u32(base + slot * kGrpSlotBytes), bar = smem_u32(&full[slot]);
+        mbar_expect_tx(bar, stage_bytes);
+        if (a_mn)
+          tma_load_5d(st, tmA, bar, 0, j0, pq, (int)(tl.q0 + Q * c), 0);
+        else
+          tma_load_4d(st, tmA, bar, j0, (int)tl.q0, c, 0);
+        tma_load_4d(st + 3 * a_bytes, tmB, bar, j0, rowB, c, 0);
+        ++kc;
+        if (++slot == kGrpStages) { slot = 0; phase ^= 1u; }
+        j0 += kStageK;
+        if (j0 >= np) { j0 = 0; ++c; }
+      }
+    }
+    counters[0] = kc;
+    if (!ok) *abort_flag = 1;
+  } else if (warp == kGrpMmaWarp && lane == 0) {
+    // MMAs: item i into accumulator pair i mod 2, once the epilogue has read
+    // that pair's previous item out
+    int slot = 0, consumed = 0, committed = 0, itn = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    constexpr uint32_t pa[6] = {2, 0, 1, 1, 0, 0};  // (l,h) (h,l) (m,m) (m,h) (h,m), then (h,h)
+    constexpr uint32_t pb[6] = {0, 2, 1, 0, 1, 0};
+    GrpWork nxt;
+    if (blockIdx.x < t.items) nxt = grp_work(t, blockIdx.x);
+    for (int64_t g = blockIdx.x; g < t.items && ok; g += G, ++itn) {
+      const GrpWork a = nxt;
+      if (g + G < t.items) nxt = grp_work(t, g + G);
+      const int np = a.np, nc = a.nc, a_mn = a.a_mn;
+      const int nk = 2 * ((np + kStageK - 1) / kStageK);
+      const int b = itn & 1, u = itn >> 1;
+      if (u >= 1 && !grp_wait(smem_u32(&tempty[b]), (uint32_t)(u - 1) & 1u, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_main = tmem + b * kGrpAccCols, d_corr = d_main + nc;
+      const uint32_t idesc = idesc_bf16(kMmaM, nc, a_mn);
+      const uint32_t b_bytes = static_cast<uint32_t>(nc) * kStageK * 2;
+      const uint64_t a0 = a_mn ? smem_desc(smem_u32(base), kStageK * 128u, 1024, 2)
+                               : smem_desc(smem_u32(base), 16, 8 * kKRowBytes, kKSwizzleDesc);
+      const uint64_t b0 = smem_desc(smem_u32(base + 3 * a_bytes), 16, 8 * kKRowBytes, kKSwizzleDesc);
+      const uint32_t a_ks = a_mn ? 2048u / 16 : 32u / 16, b_ks = 32u / 16;
+      const uint32_t a_sp = a_bytes / 16, b_sp = b_bytes / 16;
+      int j0 = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        if (!grp_wait(smem_u32(&full[slot]), phase, abort_flag)) { ok = false; break; }
+        ++consumed;
+        tc_fence_after();
+        const uint32_t so = slot * (kGrpSlotBytes / 16);
+        const int ksteps = min(kStageK, np - j0) / kMmaK;
+        for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+          for (int pr = 0; pr < 6; ++pr) {
+            const uint64_t ad = a0 + (so + pa[pr] * a_sp + ks * a_ks);
+            const uint64_t bd = b0 + (so + pb[pr] * b_sp + ks * b_ks);
+            const bool first = kb == 0 && ks == 0;
+            if (pr < 5) mma_bf16(d_corr, ad, bd, idesc, (!first || pr > 0) ? 1u : 0u);
+            else mma_bf16(d_main, ad, bd, idesc, first ? 0u : 1u);
+          }
+        }
+        mma_commit(smem_u32(&empty[slot]));
+        ++committed;
+        if (++slot == kGrpStages) { slot = 0; phase ^= 1u; }
+        j0 += kStageK;
+        if (j0 >= np) j0 = 0;
+      }
+      if (ok) mma_commit(smem_u32(&tfull[b]));
+    }
+    counters[1] = consumed;
+    counters[2] = committed;
+    if (!ok) *abort_flag = 1;
+  } else if (warp < kGrpEpiWarps) {
+    // epilogue: thread m = TMEM lane m = fiber m of the tile; results go
+    // straight from registers to global memory (strided fibers: a warp's
+    // stores cover 32 consecutive fibers; contiguous fibers: each thread
+    // writes 16 consecutive outputs of its fiber)
+    const int quarter = warp & 3, group = warp >> 2;
+    const int m = quarter * 32 + lane;
+    const uint32_t lane_addr = static_cast<uint32_t>(quarter * 32) << 16;
+    int itn = 0;
+    for (int64_t g = blockIdx.x; g < t.items; g += G, ++itn) {
+      const GrpWork a = grp_work(t, g);
+      const int n = a.n, nc = a.nc;
+      const int b = itn & 1, u = itn >> 1;
+      const bool okw = grp_wait(smem_u32(&tfull[b]), (uint32_t)u & 1u, abort_flag);
+      // the TMEM loads are warp-collective: one decision per warp
+      if (!__all_sync(0xffffffffu, okw)) break;
+      tc_fence_after();
+      const GrpTile tl = grp_tile(a);
+      const uint32_t d_main = tmem + b * kGrpAccCols + lane_addr, d_corr = d_main + nc;
+      const int64_t tile0 = tl.p0 + a.P * (int64_t)n * tl.q0;
+      const int64_t pvalid = a.P - tl.p0;
+      const bool fiber_ok = a.a_mn ? (m < pvalid) : (tl.q0 + m < a.Q);
+      for (int c0 = 16 * group; c0 < nc; c0 += 16 * kGrpEpiGroups) {
+        // component and first output row of this 16-column chunk (np is a
+        // multiple of 16, so a chunk never straddles the two components)
+        const int half = a.both ? c0 / a.np : tl.half;
+        const int i0 = a.both ? c0 - half * a.np : tl.sub * nc + c0;
+        uint32_t rm[16], rc[16];
+        tmem_ld16_issue(d_main + c0, rm);
+        tmem_ld16_issue(d_corr + c0, rc);
+        tmem_ld_wait();
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(rm[q]) + __uint_as_float(rc[q]);
+        if (!fiber_ok || i0 >= n) continue;
+        if (a.a_mn) {
+          if (a.out_fp32) {
+            float* o = reinterpret_cast<float*>(a.out) + (int64_t)half * a.N + tile0 + m;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (i0 + q < n) o[a.P * (i0 + q)] = v[q];
+          } else {
+            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out) + tile0 + m;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              if (i0 + q < n) {
+                __nv_bfloat16 sh, sm, sl;
+                split3(v[q], sh, sm, sl);
+                const int64_t off = a.P * (i0 + q);
+                o[(int64_t)(0 + half) * a.N + off] = sh;
+                o[(int64_t)(2 + half) * a.N + off] = sm;
+                o[(int64_t)(4 + half) * a.N + off] = sl;
+              }
+            }
+          }
+        } else {
+          // rows i0 .. i0 + 15 of fiber q: a chunk that starts below n ends
+          // at or below np <= the fiber pitch; its rows past n are zero rows
+          // of the padded factor
+          const int64_t off = a.pitch * (tl.q0 + m) + i0;
+          if (a.out_fp32) {
+            float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.out) + (int64_t)half * a.N + off);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          } else {
+            uint32_t w[3][8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+              split3(v[2 * k], h0, m0, l0);
+              split3(v[2 * k + 1], h1, m1, l1);
+              w[0][k] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+                        (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+              w[1][k] = static_cast<uint32_t>(__bfloat16_as_ushort(m0)) |
+                        (static_cast<uint32_t>(__bfloat16_as_ushort(m1)) << 16);
+              w[2][k] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
+                        (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+            }
+            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out);
+#pragma unroll
+            for (int sp = 0; sp < 3; ++sp) {
+              uint4* d = reinterpret_cast<uint4*>(o + (int64_t)(sp * 2 + half) * a.N + off);
+              d[0] = make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
+              d[1] = make_uint4(w[sp][4], w[sp][5], w[sp][6], w[sp][7]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    // give up: wait (bounded) for this CTA's own copies and MMAs in flight
+    if (t.npass > 0) atomicOr(t.passes[0].status, 2);
+    const int loaded = counters[0], consumed = counters[1], committed = counters[2];
+    for (int k = consumed; k < loaded; ++k) mbar_wait(smem_u32(&full[k % kGrpStages]), (k / kGrpStages) & 1);
+    if (committed > 0)
+      mbar_wait(smem_u32(&empty[(committed - 1) % kGrpStages]), ((committed - 1) / kGrpStages) & 1);
+  }
+  __syncthreads();
+  if (warp == kGrpMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * kGrpAccCols);
+  }
+}
+
 // ------------------------------------------------------------------ pointwise stages
 
 // Planes are laid out with the first direction padded to a pitch (a multiple
@@ -557,9 +868,9 @@ static size_t mma_smem_limit() {
 
 cudaError_t prepare_mma_pass() {
   const int lim = (int)mma_smem_limit();
-  cudaError_t e = cudaFuncSetAttribute(mma_mode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaError_t e = cudaFuncSetAttribute(mma_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mma_mode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = cudaFuncSetAttribute(mma_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem);
   return e;
 }
 
@@ -577,8 +888,18 @@ int64_t mma_build_args(const MmaLaunch& L, MmaPassArgs* out) {
   a.out[1] = L.out[1];
   a.N = L.N;
   const int64_t mtiles = a.a_mn ? a.per_q * L.Q : (L.Q + kMmaM - 1) / kMmaM;
-  a.nc = mma_rows_per_cta(a.np);
-  a.nsub = (a.np + a.nc - 1) / a.nc;
+  a.both = 0;
+  if (L.grouped) {
+    // persistent grouped pass (one CTA per SM, two accumulator pairs of at
+    // most 128 rows in TMEM): rows of both components in one tile when
+    // 2 np <= 128, else one component per tile, in two row blocks past 128
+    a.both = a.np <= 64 ? 1 : 0;
+    a.nc = a.both ? 2 * a.np : (a.np <= 128 ? a.np : mma_pad16((a.np + 1) / 2));
+    a.nsub = a.both ? 1 : (a.np + a.nc - 1) / a.nc;
+  } else {
+    a.nc = mma_rows_per_cta(a.np);
+    a.nsub = (a.np + a.nc - 1) / a.nc;
+  }
   int cols = 32;
   while (cols < 2 * a.nc) cols *= 2;
   a.tmem_cols = cols;
@@ -586,6 +907,7 @@ int64_t mma_build_args(const MmaLaunch& L, MmaPassArgs* out) {
   a.status = L.status;
   *out = a;
   if (L.n < 1 || L.n > 256 || (a.a_mn && L.P % 64 != 0) || (!a.a_mn && L.pitch < a.np)) return -1;
+  if (L.grouped) return (a.both ? 1 : 2 * a.nsub) * mtiles;  // tiles per rhs
   if (mma_smem_bytes(a.nc) > mma_smem_limit()) return -1;
   // mode 1 stages its FP32 tile [128][nc + 4] in the pipeline buffers
   if (!a.a_mn && (size_t)kMmaM * (a.nc + 4) * 4 > (size_t)a.stages * mma_stage_bytes(a.nc)) return -1;
@@ -601,18 +923,21 @@ cudaError_t launch_mma_pass(const MmaLaunch& L, cudaStream_t s) {
   const CUtensorMap* B0 = reinterpret_cast<const CUtensorMap*>(L.tmB[0]);
   const CUtensorMap* B1 = reinterpret_cast<const CUtensorMap*>(L.tmB[L.nrhs > 1 ? 1 : 0]);
   dim3 grid((unsigned)ctas, (unsigned)L.nrhs);
-  mma_mode_kernel<false><<<grid, kMmaThreads, mma_smem_bytes(a.nc), s>>>(*A0, *A1, *B0, *B1, a, MmaTable{});
+  mma_mode_kernel<<<grid, kMmaThreads, mma_smem_bytes(a.nc), s>>>(*A0, *A1, *B0, *B1, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mma_group(const void* passes, const void* maps, const int* start, int npass, int64_t ctas,
-                             int nrhs, size_t smem, cudaStream_t s) {
-  if (smem > mma_smem_limit() || npass < 1 || ctas < 1) return cudaErrorInvalidValue;
-  MmaTable t{static_cast<const MmaPassArgs*>(passes), static_cast<const CUtensorMap*>(maps), start, npass};
-  CUtensorMap dummy;
-  std::memset(&dummy, 0, sizeof(dummy));
-  dim3 grid((unsigned)ctas, (unsigned)nrhs);
-  mma_mode_kernel<true><<<grid, kMmaThreads, smem, s>>>(dummy, dummy, dummy, dummy, MmaPassArgs{}, t);
+cudaError_t launch_mma_group(const void* passes, const void* maps, const void* tiles, int npass, int64_t ntiles,
+                             int nrhs, cudaStream_t s) {
+  if (npass < 1 || ntiles < 1 || (nrhs != 1 && nrhs != 2)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const MmaTable t{static_cast<const MmaPassArgs*>(passes), static_cast<const CUtensorMap*>(maps),
+                   static_cast<const int2*>(tiles), npass, nrhs, ntiles * nrhs};
+  const int64_t grid = std::min<int64_t>(t.items, std::max(1, sms));
+  mma_group_kernel<<<(unsigned)grid, kGrpThreads, kGrpSmem, s>>>(t);
   return cudaGetLastError();
 }
 

@@ -44,8 +44,9 @@ def mixed_instances(seed=11):
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16x3"])
 @pytest.mark.parametrize("scheme", ["lawson4", "strang", "split4", "lawson2", "split4_3t"])
 def test_batch_equals_single_plans_and_oracle(prec, scheme):
-    """BF16x3: the grouped launches run the single plan's kernels per instance
-    (same splits, MMA order and epilogue), so batch and single plans agree."""
+    """BF16x3: the grouped persistent pass computes every output with the
+    single plan's splits, split products and accumulator order (only the
+    tiling of rows differs), so batch and single plans agree."""
     probs, fields = mixed_instances()
     tau, nsteps = 0.01, 4
     dt = torch.complex128 if prec == "f64" else torch.complex64
