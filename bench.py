@@ -288,7 +288,7 @@ def run_batch512(args):
         "speedup_batched_f32_vs_single_f64": f32["grid_pt_steps_per_s"] / res["single_plans_f64"]["grid_pt_steps_per_s"],
         "speedup_batched_f64_vs_single_f64": res["f64"]["grid_pt_steps_per_s"] /
         res["single_plans_f64"]["grid_pt_steps_per_s"],
-        "roofline": {"bound": "tensor", "kernel": "mma_mode_kernel (grouped)", "achieved": bf["achieved_tensor_tflops"],
+        "roofline": {"bound": "tensor", "kernel": "mma_group_kernel", "achieved": bf["achieved_tensor_tflops"],
                      "peak": tpeak, "unit": "TFLOP/s", "frac": bf["achieved_tensor_tflops"] / tpeak,
                      "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
                      "note": "issued tensor flops over the whole-step time (all launches, pointwise stages "
