@@ -17,19 +17,26 @@
 // tensor-memory accumulator whose partial sums are that scale times an
 // integer below 2^24 for L <= 3 (K = 2n <= 512 terms: K (2 * 128 * 64 +
 // (L - 1) 64 * 64) <= 2^24), i.e. exact whatever the accumulation order and
-// rounding.  Levels 4..6 (relative weights 2^-28..2^-42) share a fifth
-// accumulator with FP32 accumulation, whose rounding stays below 2^-46 of
-// level 0.  The 28 products with a + b <= 6 are BF16 GEMMs; the dropped
-// products (a + b >= 7) and the digit remainders r are below 2^-46 of the
-// row scales' product.  The epilogue turns the four exact levels into their
-// integers (exact 32-bit conversions), rounds the tail at 2^-31 of level 0,
-// combines them in 64-bit integer arithmetic, converts once to FP64 and
-// applies the two power-of-two scales.
+// rounding.  Levels 4..6 (relative weights 2^-28..2^-42) are FP32
+// accumulators too, summed into one tail in the epilogue, whose rounding
+// stays below 2^-46 of level 0.  The 28 products with a + b <= 6 are BF16
+// GEMMs; the dropped products (a + b >= 7) and the digit remainders r are
+// below 2^-46 of the row scales' product.  The epilogue turns the four exact
+// levels into their integers (exact 32-bit conversions), rounds the tail at
+// 2^-31 of level 0, combines them in 64-bit integer arithmetic, converts once
+// to FP64 and applies the two power-of-two scales.
+//
+// The seven level accumulators are consecutive blocks of nc TMEM columns
+// (level L at columns [L nc, (L + 1) nc)), and the factor's digit planes
+// are consecutive blocks of nc rows in shared memory, so one MMA of A digit a
+// against B digits b0..b1 (N = (b1 - b0 + 1) nc <= 256) writes product
+// (a, b) straight into block a + b, its level: about ten MMAs per K step
+// instead of 28, each reading its A digit from shared memory once.
 //
 // A pass is: slice the FP64 state planes of the mode's fibers (per-fiber
 // exponent), then the tensor-core GEMM writing FP64 planes.  One CTA =
-// 128 fibers (TMEM lanes) x nc <= 96 output rows of one component; the five
-// level accumulators take 5 nc <= 480 TMEM columns.  Pipeline, copy / MMA
+// 128 fibers (TMEM lanes) x nc <= 64 output rows of one component; the seven
+// level accumulators take 7 nc <= 448 TMEM columns.  Pipeline, copy / MMA
 // thread roles, bounded waits and the abort path follow the BF16x3 pass.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -261,8 +268,7 @@ __device__ __forceinline__ double pow2(int k) {
 }
 
 // CTA (tile, half, sub): 128 fibers x output rows [sub nc, (sub + 1) nc) of
-// component c' = half; TMEM columns [k nc, (k + 1) nc) hold level k for
-// k < 4 and levels 4..6 for k = 4.
+// component c' = half; TMEM columns [L nc, (L + 1) nc) hold level L.
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_mode_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
@@ -337,7 +343,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     if (!ok) *abort_flag = 1;
   }
   if (threadIdx.x == 0) {
-    const uint32_t idesc = idesc_bf16(kOzM, nc, a.a_mn);
+    // digits of B per MMA: N = span nc <= 256
+    const int span = min(7, 256 / nc);
     const uint64_t a0 = a.a_mn ? smem_desc(smem_u32(base), kOzStageK * 128u, 1024, 2)
                                : smem_desc(smem_u32(base), 16, 8 * kOzKRowBytes, kOzKSwizzleDesc);
     const uint64_t b0 = smem_desc(smem_u32(base + 7 * a_bytes), 16, 8 * kOzKRowBytes, kOzKSwizzleDesc);
@@ -354,16 +361,17 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int ksteps = min(kOzStageK, np - j0) / kOzK;
       for (int ks = 0; ks < ksteps; ++ks) {
         const bool first = kb == 0 && ks == 0;
+        // A digit x against B digits y0 .. y0 + cnt - 1 into level blocks
+        // x + y0 ..; the MMAs of digit 0 cover all seven blocks and come
+        // first, so at the first K step they overwrite and the rest add
 #pragma unroll
-        for (int L = 0; L < 7; ++L) {
-          const int acc = L < 4 ? L : 4;
-#pragma unroll
-          for (int x = 0; x <= L; ++x) {
-            const uint64_t ad = a0 + (so + x * a_sp + ks * a_ks);
-            const uint64_t bd = b0 + (so + (L - x) * b_sp + ks * b_ks);
-            // the first product into each accumulator overwrites it: (0, L)
-            // for the exact levels, (0, 4) for the shared one
-            mma_bf16(tmem + static_cast<uint32_t>(acc * nc), ad, bd, idesc, (first && x == 0 && L <= 4) ? 0u : 1u);
+        for (int x = 0; x < 7; ++x) {
+          const uint64_t ad = a0 + (so + x * a_sp + ks * a_ks);
+          for (int y0 = 0; y0 <= 6 - x; y0 += span) {
+            const int cnt = min(span, 7 - x - y0);
+            const uint64_t bd = b0 + (so + y0 * b_sp + ks * b_ks);
+            mma_bf16(tmem + static_cast<uint32_t>((x + y0) * nc), ad, bd, idesc_bf16(kOzM, cnt * nc, a.a_mn),
+                     (first && x == 0) ? 0u : 1u);
           }
         }
       }
@@ -413,23 +421,24 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int pitch_s = nc + 1;  // mode 1: FP64 staging tile [128][nc + 1]
     double* stage = reinterpret_cast<double*>(base);
     for (int c0 = 0; c0 < nc; c0 += 16) {
-      uint32_t r[5][16];
+      uint32_t r[7][16];
 #pragma unroll
-      for (int L = 0; L < 5; ++L) tmem_ld16_nowait(tmem + lane_addr + static_cast<uint32_t>(L * nc + c0), r[L]);
+      for (int L = 0; L < 7; ++L) tmem_ld16_nowait(tmem + lane_addr + static_cast<uint32_t>(L * nc + c0), r[L]);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         const int i = sub * nc + c0 + t;  // output row of component `half`
         // accumulator k < 4 holds 2^{-7k} x an integer below 2^24: scaled by
-        // 2^{7k} it converts to int32 exactly; the shared tail (below 0.06 in
-        // level-0 units) is rounded at 2^-31 of them.  (Conversions to 32-bit
+        // 2^{7k} it converts to int32 exactly; the tail, levels 4..6 (below
+        // 0.06 in level-0 units), is rounded at 2^-31 of them.  (Conversions to 32-bit
         // integers: a float-to-int64 conversion per accumulator made the pass
         // 20% slower.)
         long long I = static_cast<long long>(__float2int_rn(__uint_as_float(r[0][t]))) * (1ll << 31);
         I += static_cast<long long>(__float2int_rn(__uint_as_float(r[1][t]) * 128.0f)) * (1ll << 24);
         I += static_cast<long long>(__float2int_rn(__uint_as_float(r[2][t]) * 16384.0f)) * (1ll << 17);
         I += static_cast<long long>(__float2int_rn(__uint_as_float(r[3][t]) * 2097152.0f)) * (1ll << 10);
-        I += static_cast<long long>(__float2int_rn(__uint_as_float(r[4][t]) * 2147483648.0f));
+        const float tail = __uint_as_float(r[4][t]) + (__uint_as_float(r[5][t]) + __uint_as_float(r[6][t]));
+        I += static_cast<long long>(__float2int_rn(tail * 2147483648.0f));
         // sum_{a,b} d_a d'_b 2^{-7(a+b+2)} = I 2^{-45}, times 2^{ea + fe[i]}
         const double v = static_cast<double>(I) * pow2(ea + (i < np ? fe[i] : 0) - 45);
         if (a.a_mn) {
@@ -462,24 +471,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
 static size_t oz_smem_bytes(int nc) { return kOzStages * static_cast<size_t>(oz_stage_bytes(nc)) + 1024 + 256; }
 
-// Output rows per CTA: the whole np up to 96 rows, else the split of np into
-// blocks of 64..96 rows (rounded up to 16) with the fewest rows past np (five
-// accumulators of nc columns fit the 512 of TMEM up to nc = 96).  Measured on the 256^3 Lawson4
-// step: blocks of 64 rows (four per component) 14.7 ms for the six passes
-// against 16.1 ms with blocks of 96 (three, the last a third past np): the
-// pass runs at the same fraction of the tensor peak with either width, so
-// the rows computed past np decide.
+// Output rows per CTA: the whole np up to 64 rows, else blocks of 48 or 64
+// rows with the fewest rows past np (64 on ties): seven level accumulators of
+// nc columns fit the 512 of TMEM up to nc = 73.  (With five accumulators,
+// levels 4..6 sharing one, blocks of 64 and 96 rows ran at the same fraction
+// of the tensor peak on the 256^3 Lawson4 step, so the rows computed past np
+// decide.)
 int oz_rows_per_cta(int np) {
-  if (np <= 96) return np;
-  int best = 0, waste = 1 << 30;
-  for (int nsub = (np + 95) / 96; nsub <= (np + 63) / 64; ++nsub) {
-    const int nc = ((np + nsub - 1) / nsub + 15) / 16 * 16;
-    if (nsub * nc - np < waste) {
-      waste = nsub * nc - np;
-      best = nc;
-    }
-  }
-  return best;
+  if (np <= 64) return np;
+  const int w64 = (np + 63) / 64 * 64 - np, w48 = (np + 47) / 48 * 48 - np;
+  return w48 < w64 ? 48 : 64;
 }
 
 size_t oz_factor_bytes(int n) {
@@ -489,7 +490,7 @@ size_t oz_factor_bytes(int n) {
 
 cudaError_t prepare_oz_pass() {
   return cudaFuncSetAttribute(oz_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(oz_smem_bytes(96)));
+                              static_cast<int>(oz_smem_bytes(64)));
 }
 
 int64_t oz_build_args(const OzLaunch& L, OzPassArgs* out) {
@@ -505,7 +506,7 @@ int64_t oz_build_args(const OzLaunch& L, OzPassArgs* out) {
   a.nc = oz_rows_per_cta(a.np);
   a.nsub = (a.np + a.nc - 1) / a.nc;
   int cols = 32;
-  while (cols < 5 * a.nc) cols *= 2;
+  while (cols < 7 * a.nc) cols *= 2;
   a.tmem_cols = cols;
   for (int r = 0; r < kMaxRhs; ++r) {
     a.aexp[r] = L.aexp[r];
