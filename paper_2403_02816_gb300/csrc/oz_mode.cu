@@ -86,16 +86,17 @@ __device__ __forceinline__ long long fixed49(double x, int e) {
 }
 
 // Seven signed digits of v (|v| <= 2^49), most significant first:
-// v = sum_a d_a 2^{7(6 - a)}, |d_0| <= 128, |d_a| <= 64.
+// v = sum_a d_a 2^{7(6 - a)}, |d_0| <= 128, -64 <= d_a <= 63 for a >= 1.
+// Balanced base-128 recoding: with t = v + 64 sum_a 2^{7a}, every 7-bit field
+// of t below the top one is d_a + 64, and t >> 42 is d_0 + 64 (one 64-bit
+// add and seven field extractions instead of a rounding division per digit).
 __device__ __forceinline__ void digits7(long long v, int* d) {
+  constexpr long long kOff = 64ll * ((1ll << 42) + (1ll << 35) + (1ll << 28) + (1ll << 21) + (1ll << 14) +
+                                     (1ll << 7) + 1ll);
+  const long long t = v + kOff;
+  d[0] = static_cast<int>(t >> 42) - 64;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const int sh = 7 * (6 - k);
-    const long long q = (v + (1ll << (sh - 1))) >> sh;
-    d[k] = static_cast<int>(q);
-    v -= q * (1ll << sh);
-  }
-  d[6] = static_cast<int>(v);
+  for (int k = 1; k < 7; ++k) d[k] = static_cast<int>((t >> (7 * (6 - k))) & 127) - 64;
 }
 
 // Digit d (|d| <= 128) of position s as the BF16 value d 2^{-7s} (exact).
