@@ -691,11 +691,24 @@ __device__ __forceinline__ int64_t plane_index(int64_t i, int64_t n1, int64_t pi
   return pitch == n1 ? i : i + (pitch - n1) * (i / n1);
 }
 
+// A block's segment copied to shared memory: every thread reads its field
+// pointers and operator coefficients there instead of from global memory
+// (dependent loads ahead of every point's data loads).
+template <class Seg> __device__ __forceinline__ const Seg& stage_segment(const Seg* segs, Seg* smem_seg) {
+  static_assert(sizeof(Seg) % 8 == 0, "segment copied in 8-byte words");
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(segs + blockIdx.y);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(smem_seg);
+  for (int k = threadIdx.x; k < (int)(sizeof(Seg) / 8); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  return *smem_seg;
+}
+
 // Start of a sweep: prologue on complex64 inputs, BF16x3 planes of each rhs
 // (one field per segment; blockIdx.y selects the segment in table mode).
 template <bool kTable>
 __global__ void split_prologue_kernel(const SplitSeg one, const SplitSeg* __restrict__ segs, int nrhs) {
-  const SplitSeg& g = kTable ? segs[blockIdx.y] : one;
+  __shared__ __align__(16) SplitSeg sseg;
+  const SplitSeg& g = kTable ? stage_segment(segs, &sseg) : one;
   const int64_t P = g.Npad;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * blockDim.x) {
     float2 in[2], z[2];
@@ -721,7 +734,8 @@ __global__ void split_prologue_kernel(const SplitSeg one, const SplitSeg* __rest
 // End of a sweep: FP32 planes of each rhs + extras -> epilogue -> complex64.
 template <bool kTable>
 __global__ void plane_epilogue_kernel(const EpiSeg one, const EpiSeg* __restrict__ segs, int nrhs, int* status) {
-  const EpiSeg& g = kTable ? segs[blockIdx.y] : one;
+  __shared__ __align__(16) EpiSeg sseg;
+  const EpiSeg& g = kTable ? stage_segment(segs, &sseg) : one;
   const int64_t P = g.Npad;
   bool bad = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * blockDim.x) {
