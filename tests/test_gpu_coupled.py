@@ -33,8 +33,9 @@ def cprob(p):
 
 
 def check(got, ref, prec, what=""):
-    err = O.rel_l2(got, ref)
-    assert err <= TOL[prec], (what, err)
+    err, einf = O.rel_l2(got, ref), O.rel_inf(got, ref)
+    # per-value bounds: they hold in relative L2 and relative inf alike
+    assert err <= TOL[prec] and einf <= TOL[prec], (what, err, einf)
 
 
 # ------------------------------------------------------------ mixed radix, one field

@@ -1,6 +1,6 @@
 """CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerances (relative L2 over the whole field, also reported as rel. inf):
+Tolerances (relative L2 over the whole field and relative inf, both asserted):
   * FP64: 1e-11, the bound the workload statement sets for the FP64 path;
     short runs land near 1e-14.
   * FP32 (complex64 state, FP32 arithmetic): 2e-5 for the few-step cases
@@ -47,7 +47,9 @@ def check(got, ref, prec, label=""):
     e2 = O.rel_l2(got, ref)
     einf = O.rel_inf(got, ref)
     assert np.all(np.isfinite(got)), label
-    assert e2 <= TOL[prec], "%s rel L2 %.3e rel inf %.3e" % (label, e2, einf)
+    # the tolerances bound each value's error, so they hold in the relative
+    # inf norm (the paper's measure, Sec. 4) as well as in relative L2
+    assert e2 <= TOL[prec] and einf <= TOL[prec], "%s rel L2 %.3e rel inf %.3e" % (label, e2, einf)
     return e2
 
 
