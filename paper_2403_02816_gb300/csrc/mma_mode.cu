@@ -363,7 +363,8 @@ struct MmaTable {
 // slots sized for the largest stage (nc = 128) runs across items, and two
 // accumulator pairs in TMEM let the epilogue of one item run under the MMAs
 // of the next.  The epilogue is latency-bound (dependent TMEM loads, splits
-// and stores per chunk), hence its sixteen warps.
+// and stores per chunk): with four warps it held the pass back, with eight
+// or sixteen it does not.
 constexpr int kGrpEpiWarps = 16;
 constexpr int kGrpEpiGroups = kGrpEpiWarps / 4;
 constexpr int kGrpCopyWarp = kGrpEpiWarps, kGrpMmaWarp = kGrpEpiWarps + 1;
