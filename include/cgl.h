@@ -281,15 +281,16 @@ typedef struct cgl_batch cgl_batch;
  * periodic -> EUNSUPPORTED) sharing one step size and scheme (strang,
  * split4, lawson4, lawson2, strang_3t, split4_3t) in CGL_F64, CGL_F32 or
  * CGL_BF16X3 (complex64 state; every n_mu <= 256).  Each instance gets its
- * own FP64 factors exp(c tau A_mu) (Sec. 3.1).  Every mu-mode pass of a time
- * step is ONE launch over all instances.  F64 / F32: a fixed grid of CTAs
- * pulls (instance, fiber tile) work items, largest first, from a device
- * queue; the fibers per tile come from cgl_autotune_mode_tile.  BF16X3: one
- * grouped tensor-core launch per mode whose CTAs map to (instance, fiber
- * tile, output block) through a device table of per-instance arguments,
- * between one grouped split prologue and one grouped plane epilogue per
- * sweep.  The whole time step is replayed as one CUDA graph.  Synchronous
- * (set-up and autotuning).
+ * own FP64 factors exp(c tau A_mu) (Sec. 3.1).  F64 / F32: the whole time
+ * step is ONE persistent launch: a fixed grid of CTAs pulls (pass, instance,
+ * fiber tile) items of every mode pass of every sweep from one device work
+ * list, an item waiting (bounded) until its instance's previous pass is done;
+ * the fibers per tile come from cgl_autotune_mode_tile.  BF16X3: per sweep
+ * one grouped split prologue, one persistent tensor-core launch per mode (one
+ * CTA per SM walks the pass's (instance, tile) records, its copies, MMAs and
+ * epilogue overlapped across tiles) and one grouped plane epilogue.  The
+ * whole time step is replayed as one CUDA graph.  Synchronous (set-up and
+ * autotuning).
  * Errors: EINVAL (bad precision or scheme; per-instance validation as
  * cgl_plan_create, message names the instance), EUNSUPPORTED, ENOMEM, ECUDA.
  */
