@@ -110,8 +110,8 @@ def test_schemes_match_oracle(n, bc, cubic):
     for s in ("strang", "split4", "lawson4", "lawson2", "strang3t", "split4_3t", "rk4", "rk2"):
         ref = O.integrate(oprob(p), U0, tau, nsteps, s)
         got = run_gpu(p, U0, tau, nsteps, s)
-        e = O.rel_l2(got, ref)
-        assert e <= 1e-11, (s, cubic, e)
+        e, einf = O.rel_l2(got, ref), O.rel_inf(got, ref)
+        assert e <= 1e-11 and einf <= 1e-11, (s, cubic, e, einf)
 
 
 def test_workload_2d_dirichlet_full_run():
@@ -133,7 +133,8 @@ def test_workload_3d_neumann_full_size():
     U0 = I.u0_3d_neumann(w)
     ref = O.integrate(oprob(w.prob), U0, w.tau, 2, "lawson4")
     got = run_gpu(w.prob, U0, w.tau, 2, "lawson4")
-    assert O.rel_l2(got, ref) <= 1e-11, O.rel_l2(got, ref)
+    e2, einf = O.rel_l2(got, ref), O.rel_inf(got, ref)
+    assert e2 <= 1e-11 and einf <= 1e-11, (e2, einf)
 
 
 def test_deterministic_and_equal_to_fp64_path_within_bound():
