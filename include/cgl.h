@@ -319,6 +319,20 @@ int cgl_batch_last_device_status(cgl_batch* batch, void* stream);
 int cgl_batch_destroy(cgl_batch* batch);
 
 /*
+ * Fault injection for tests (the paper has no counterpart): with on != 0,
+ * every dependency wait of an FP64 / FP32 batch's time step (an item waiting
+ * for its instance's previous mode pass) waits for a count that is never
+ * reached and gives up after 1024 polls (about 0.15 ms) instead of the
+ * normal 2^22; the launch then stops at every CTA's next claim,
+ * cgl_batch_last_device_status returns CGL_ETIMEOUT, and the field is left
+ * in an unspecified state.  on = 0 restores normal waits.  Either call
+ * discards the step's CUDA graph, captured again at the next cgl_batch_step.
+ * Errors: EINVAL (NULL), EUNSUPPORTED (a BF16X3 batch: its tensor-core waits
+ * are not injected), ECUDA.
+ */
+int cgl_batch_inject_wait_failure(cgl_batch* batch, int on);
+
+/*
  * Tile-size autotuner of the mu-mode pass: times every admissible number of
  * fibers per CTA (2, 4, ..., 64, within 96 KiB of shared memory) for mode
  * length n, contiguous (mode 1) or strided fibers, precision (CGL_F64 /

@@ -85,6 +85,7 @@ struct cgl_batch {
     std::vector<MmaMode> modes;
   };
   std::vector<MmaSweep> msweeps;
+  int inject_wait_failure = 0;  // test hook: the step kernel's dependency waits cannot be met
   std::vector<void*> allocations;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -334,6 +335,8 @@ int enqueue_batch_step(cgl_batch* b, cudaStream_t s) {
     a.count = b->count;
     a.counter = b->counters;
     a.status = b->status;
+    a.spin_limit = b->inject_wait_failure ? kStepInjectedSpinLimit : kStepSpinLimit;
+    a.want_bias = b->inject_wait_failure ? 1 : 0;
     cudaError_t e = b->precision == CGL_F64 ? launch_batched_step<double>(a, b->step_smem, b->step_grid, s)
                                             : launch_batched_step<float>(a, b->step_smem, b->step_grid, s);
     if (e != cudaSuccess) return fail(CGL_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
@@ -647,6 +650,20 @@ int cgl_batch_last_device_status(cgl_batch* b, void* stream) {
   CUDA_TRY(cudaStreamSynchronize(s));
   if (h & 2) return fail(CGL_ETIMEOUT, "a device-side wait timed out");
   return (h & 1) ? CGL_ENONFINITE : CGL_OK;
+}
+
+int cgl_batch_inject_wait_failure(cgl_batch* b, int on) {
+  if (!b) return fail(CGL_EINVAL, "batch is NULL");
+  if (b->passes.empty()) return fail(CGL_EUNSUPPORTED, "wait-failure injection: FP64 / FP32 batches only");
+  CUDA_TRY(cudaSetDevice(b->dev));
+  b->inject_wait_failure = on ? 1 : 0;
+  if (b->exec) {  // the step's arguments are part of its graph: capture it again
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaGraphExecDestroy(b->exec));
+    b->exec = nullptr;
+    b->graph_u = nullptr;
+  }
+  return CGL_OK;
 }
 
 int cgl_batch_destroy(cgl_batch* b) {

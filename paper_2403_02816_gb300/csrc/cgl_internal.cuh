@@ -481,7 +481,13 @@ struct StepArgs {
   int npass, count;
   int* counter;               // [2 + npass count], zeroed before the launch: next item, abort, done counts
   int* status;
+  long long spin_limit;       // polls of a dependency wait before it gives up (kStepSpinLimit)
+  int want_bias;              // added to every dependency target: 1 makes each wait unreachable (fault injection)
 };
+// Polls of the batch step's dependency waits (128 ns apart: about 0.5 s).
+constexpr long long kStepSpinLimit = 1ll << 22;
+// Polls before an injected, unreachable wait gives up (about 0.15 ms).
+constexpr long long kStepInjectedSpinLimit = 1024;
 template <class T> cudaError_t launch_batched_step(const StepArgs& a, size_t smem, int grid, cudaStream_t s);
 template <class T> int batched_step_blocks_per_sm(size_t smem);
 template <class T> cudaError_t launch_mode_pass_tb(const ModePassArgs& a, int tb, cudaStream_t s);

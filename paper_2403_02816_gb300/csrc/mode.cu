@@ -244,7 +244,6 @@ __global__ void __launch_bounds__(kModeThreads) mode_pass_kernel(const ModePassA
 
 // Polls of a dependency wait (with a 128 ns sleep each) before the step
 // kernel gives up: about half a second.
-constexpr long long kStepSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -275,10 +274,10 @@ __global__ void __launch_bounds__(kModeThreads) batched_step_kernel(const StepAr
         const int pk = a.prev[it.pass * a.count + it.inst];
         if (pk >= 0) {
           const int* d = done + pk * a.count + it.inst;
-          const int want = a.need[pk * a.count + it.inst];
+          const int want = a.need[pk * a.count + it.inst] + a.want_bias;
           long long spins = 0;
           while (ld_acquire(d) < want) {
-            if (++spins > kStepSpinLimit || ld_acquire(abort_flag)) {
+            if (++spins > a.spin_limit || ld_acquire(abort_flag)) {
               s_go = 0;
               break;
             }

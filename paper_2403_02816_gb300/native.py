@@ -102,6 +102,7 @@ def load() -> ctypes.CDLL:
         "cgl_batch_step": (I, [P, VP, I64, VP]),
         "cgl_batch_last_device_status": (I, [P, VP]),
         "cgl_batch_destroy": (I, [P]),
+        "cgl_batch_inject_wait_failure": (I, [P, I]),
         "cgl_autotune_mode_tile": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "cgl_corrector_create": (I, [ctypes.POINTER(P), I, I, I, I, I, ctypes.c_uint64, VP]),
         "cgl_corrector_num_params": (I, [P, ctypes.POINTER(I64)]),
@@ -444,6 +445,11 @@ class Batch:
 
     def device_status(self, stream=None) -> int:
         return load().cgl_batch_last_device_status(self.handle, _stream_handle(stream))
+
+    def inject_wait_failure(self, on: bool):
+        """Test hook: make every dependency wait of the step unreachable
+        (FP64 / FP32 batches); the next steps report CGL_ETIMEOUT."""
+        check(load().cgl_batch_inject_wait_failure(self.handle, 1 if on else 0), "cgl_batch_inject_wait_failure")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -146,6 +146,45 @@ def test_full_512_instance_workload_every_instance_within_bound():
         assert not bad, (prec, bad[:8], len(bad))
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dependency_wait_timeout_is_reported_and_batch_recovers(prec):
+    """Failure detection without a GPU fault: with the injected wait failure
+    every item of a later mode pass waits for a count that is never reached,
+    gives up after a short bounded spin, and the launch ends; the step reports
+    CGL_ETIMEOUT and the context stays usable, so the same batch with normal
+    waits then reproduces an untouched batch's result bit for bit."""
+    probs, fields = mixed_instances()
+    with nat.Batch(probs, 0.01, "lawson4", prec) as b:
+        u = b.pack(fields)
+        b.inject_wait_failure(True)
+        b.step(u, 2)
+        torch.cuda.synchronize()
+        assert b.device_status() == nat.CGL_ETIMEOUT
+        assert b.device_status() == nat.CGL_OK  # reading clears it
+        b.inject_wait_failure(False)
+        v = b.pack(fields)
+        b.step(v, 3)
+        torch.cuda.synchronize()
+        assert b.device_status() == nat.CGL_OK
+        got = b.unpack(v)
+    with nat.Batch(probs, 0.01, "lawson4", prec) as fresh:
+        w = fresh.pack(fields)
+        fresh.step(w, 3)
+        torch.cuda.synchronize()
+        assert fresh.device_status() == nat.CGL_OK
+        want = fresh.unpack(w)
+    for G, W in zip(got, want):
+        assert G.tobytes() == W.tobytes()
+
+
+def test_wait_failure_injection_rejects_tensor_core_batches():
+    probs, _ = mixed_instances()
+    with nat.Batch(probs, 0.01, "lawson4", "bf16x3") as b:
+        with pytest.raises(nat.CglError) as ei:
+            b.inject_wait_failure(True)
+        assert ei.value.status == nat.CGL_EUNSUPPORTED
+
+
 def test_autotuner_returns_admissible_tiles_and_caches(tmp_path, monkeypatch):
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("CGL_AUTOTUNE_CACHE", str(cache))
