@@ -355,7 +355,7 @@ int cgl_autotune_mode_tile(int n, int contiguous, int precision, int nrhs, int* 
  * accumulation; weight gradients in FP32 from the unrounded values; FP32
  * masters, Adam on the masters.  The paper has no learned part; this
  * follows the fine method (the plain integrator at a smaller step) as the
- * training target and as the judge of the corrected error.
+ * training target and as the reference for the corrected error.
  *
  * Field arguments are complex64 device arrays [P][H][W] (W fastest, the
  * layout of a 2D plan field with n_1 = W); `params` is float [P][5]

@@ -1,7 +1,7 @@
 """Learned corrector of a coarse exponential step, trained on trajectories of
 the fine method (2D periodic cubic CGL, 128 x 128, (-10,10)^2).
 
-  fine   : Lawson4 (eq. lawson4), complex128, tau_f = 0.002   (training target and judge)
+  fine   : Lawson4 (eq. lawson4), complex128, tau_f = 0.002   (training target and reference)
   coarse : Lawson4, complex128, tau_c = 0.016 = 8 tau_f
   corrected coarse step: u_{n+1} = C(u_n) + N(x_n)  (cgl_corrector_*)
 
