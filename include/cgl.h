@@ -205,6 +205,15 @@ int cgl_step_host(cgl_plan* plan, void* u_host, int64_t nsteps, void* stream);
 int cgl_plan_destroy(cgl_plan* plan);
 
 /*
+ * Fault injection for tests (the paper has no counterpart): after `after`
+ * more device allocations by plans, batches and correctors (process-wide),
+ * the next one fails as if cudaMalloc had, and the call that made it
+ * returns CGL_ENOMEM after freeing what it had allocated; the injection is
+ * then disarmed.  after = -1 disarms it.  Errors: EINVAL (after < -1).
+ */
+int cgl_inject_alloc_failure(long long after);
+
+/*
  * Apply one linear flow exp(c tau K) to the device field u in place
  * (eq. Tucker / Sec. 3.2), for c equal to one of the plan's factor values
  * (1 or 0.5; EINVAL otherwise).  Asynchronous on `stream`.

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -479,7 +480,22 @@ double norm1(const std::vector<double2>& A, int n) {
   return best;
 }
 
+// Allocations left before the injected failure (-1: none armed).
+static std::atomic<long long> g_alloc_countdown{-1};
+
+bool injected_alloc_failure() {
+  long long c = g_alloc_countdown.load();
+  while (c >= 0) {
+    if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+  }
+  return false;
+}
+
 int dev_alloc(cgl_plan* p, void** ptr, size_t bytes) {
+  if (injected_alloc_failure()) {
+    *ptr = nullptr;
+    return fail(CGL_ENOMEM, "cudaMalloc: injected allocation failure");
+  }
   cudaError_t e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
   if (e != cudaSuccess) {
     *ptr = nullptr;
@@ -1089,6 +1105,12 @@ int plan_create_impl(cgl_plan** out, int d, const int64_t* n, const int* bc, con
 }  // namespace cgl
 
 extern "C" {
+
+int cgl_inject_alloc_failure(long long after) {
+  if (after < -1) return fail(CGL_EINVAL, "after must be >= -1");
+  g_alloc_countdown.store(after);
+  return CGL_OK;
+}
 
 int cgl_plan_create(cgl_plan** out, int d, const int64_t* n, const int* bc, const double* lo, const double* hi,
                     double a1, double b1, double a2, double a3, double b3, double a4, double b4, double tau,

@@ -231,6 +231,10 @@ void free_batch(cgl_batch* b) {
 }
 
 int batch_alloc(cgl_batch* b, void** ptr, size_t bytes) {
+  if (injected_alloc_failure()) {
+    *ptr = nullptr;
+    return fail(CGL_ENOMEM, "cudaMalloc: injected allocation failure");
+  }
   cudaError_t e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
   if (e != cudaSuccess) {
     *ptr = nullptr;

@@ -217,6 +217,10 @@ struct cgl_corrector {
 namespace {
 
 int corr_alloc(cgl_corrector* c, void** p, size_t bytes) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return fail(CGL_ENOMEM, "cudaMalloc: injected allocation failure");
+  }
   cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
   if (e != cudaSuccess) {
     *p = nullptr;

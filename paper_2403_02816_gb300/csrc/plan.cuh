@@ -14,6 +14,10 @@ namespace cgl {
 // Records `msg` as the calling thread's last error and returns `status`.
 int fail(int status, const std::string& msg);
 
+// Fault injection (cgl_inject_alloc_failure): true when the library's
+// device allocation about to be made is the one set to fail.
+bool injected_alloc_failure();
+
 enum { BUF_U = 0, BUF_W0 = 1, BUF_W1 = 2, BUF_W2 = 3, NBUF = 4 };
 constexpr int FAC_K = -1;   // the Runge-Kutta sweeps apply K, not an exponential
 constexpr int FAC_K2 = -2;  // ... the coupled system's v field (advection -a0)

@@ -103,6 +103,7 @@ def load() -> ctypes.CDLL:
         "cgl_batch_last_device_status": (I, [P, VP]),
         "cgl_batch_destroy": (I, [P]),
         "cgl_batch_inject_wait_failure": (I, [P, I]),
+        "cgl_inject_alloc_failure": (I, [ctypes.c_longlong]),
         "cgl_autotune_mode_tile": (I, [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "cgl_corrector_create": (I, [ctypes.POINTER(P), I, I, I, I, I, ctypes.c_uint64, VP]),
         "cgl_corrector_num_params": (I, [P, ctypes.POINTER(I64)]),
@@ -328,6 +329,12 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def inject_alloc_failure(after: int):
+    """Test hook: the (after + 1)-th device allocation from now by a plan,
+    batch or corrector fails with CGL_ENOMEM; -1 disarms."""
+    check(load().cgl_inject_alloc_failure(int(after)), "cgl_inject_alloc_failure")
 
 
 def to_device(U, dtype, device="cuda"):

@@ -185,6 +185,46 @@ def test_wait_failure_injection_rejects_tensor_core_batches():
         assert ei.value.status == nat.CGL_EUNSUPPORTED
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16x3"])
+def test_batch_allocation_failure_is_reported_and_cleaned_up(prec):
+    """Each device allocation of a batch's creation (its instances' plans and
+    its own tables) fails in turn: CGL_ENOMEM every time, free device memory
+    back at its level, and the batch made afterwards matches single plans."""
+    probs, fields = mixed_instances()
+    probs, fields = probs[:3], fields[:3]
+    with nat.Batch(probs, 0.01, "lawson4", prec):  # set-up kernels loaded, tiles tuned
+        pass
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    k = 0
+    while True:
+        nat.inject_alloc_failure(k)
+        try:
+            b = nat.Batch(probs, 0.01, "lawson4", prec)
+        except nat.CglError as e:
+            assert e.status == nat.CGL_ENOMEM, e
+            k += 1
+            assert k < 2000
+            continue
+        nat.inject_alloc_failure(-1)
+        b.close()
+        break
+    assert k >= 3, k
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    with nat.Batch(probs, 0.01, "lawson4", prec) as b:
+        u = b.pack(fields)
+        b.step(u, 2)
+        torch.cuda.synchronize()
+        assert b.device_status() == nat.CGL_OK
+        got = b.unpack(u)
+    for p, U0, G in zip(probs, fields, got):
+        with nat.Plan(p, 0.01, "lawson4", prec) as plan:
+            v = nat.to_device(U0, torch.complex64)
+            plan.step(v, 2)
+            assert O.rel_l2(G, nat.from_device(v)) <= 1e-6
+
+
 def test_autotuner_returns_admissible_tiles_and_caches(tmp_path, monkeypatch):
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("CGL_AUTOTUNE_CACHE", str(cache))

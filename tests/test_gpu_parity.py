@@ -295,6 +295,38 @@ def test_workload_3d_periodic_longer_run_small_grid():
 
 # ------------------------------------------------------------ API behaviour
 
+def test_allocation_failure_at_each_allocation_is_reported_and_cleaned_up():
+    """Failure injection on the host: each device allocation of a plan's
+    creation fails in turn; every attempt returns CGL_ENOMEM after freeing
+    what it had allocated (free device memory back at its level), and a plan
+    made afterwards steps as the oracle does."""
+    w = I.workload_2d_dirichlet(32)
+    U0 = I.u0_2d_dirichlet(w)
+    for prec in ("f64", "bf16x3"):
+        with nat.Plan(w.prob, w.tau, "lawson4", prec):  # loads the set-up kernels once
+            pass
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        k = 0
+        while True:
+            nat.inject_alloc_failure(k)
+            try:
+                plan = nat.Plan(w.prob, w.tau, "lawson4", prec)
+            except nat.CglError as e:
+                assert e.status == nat.CGL_ENOMEM, e
+                k += 1
+                assert k < 500
+                continue
+            nat.inject_alloc_failure(-1)
+            plan.close()
+            break
+        assert k >= 3, (prec, k)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, prec
+        got = run_gpu(w.prob, U0, w.tau, 5, "lawson4", prec)
+        check(got, O.integrate(oprob(w.prob), U0, w.tau, 5, "lawson4"), prec, "after injected failures")
+
+
 def test_step_host_matches_device_step():
     w = I.workload_2d_dirichlet(32)
     U0 = I.u0_2d_dirichlet(w)
