@@ -197,18 +197,20 @@ def test_batch_allocation_failure_is_reported_and_cleaned_up(prec):
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     k = 0
-    while True:
-        nat.inject_alloc_failure(k)
-        try:
-            b = nat.Batch(probs, 0.01, "lawson4", prec)
-        except nat.CglError as e:
-            assert e.status == nat.CGL_ENOMEM, e
-            k += 1
-            assert k < 2000
-            continue
+    try:
+        while True:
+            nat.inject_alloc_failure(k)
+            try:
+                b = nat.Batch(probs, 0.01, "lawson4", prec)
+            except nat.CglError as e:
+                assert e.status == nat.CGL_ENOMEM, e
+                k += 1
+                assert k < 2000
+                continue
+            b.close()
+            break
+    finally:
         nat.inject_alloc_failure(-1)
-        b.close()
-        break
     assert k >= 3, k
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0

@@ -308,18 +308,20 @@ def test_allocation_failure_at_each_allocation_is_reported_and_cleaned_up():
         torch.cuda.synchronize()
         free0 = torch.cuda.mem_get_info()[0]
         k = 0
-        while True:
-            nat.inject_alloc_failure(k)
-            try:
-                plan = nat.Plan(w.prob, w.tau, "lawson4", prec)
-            except nat.CglError as e:
-                assert e.status == nat.CGL_ENOMEM, e
-                k += 1
-                assert k < 500
-                continue
+        try:
+            while True:
+                nat.inject_alloc_failure(k)
+                try:
+                    plan = nat.Plan(w.prob, w.tau, "lawson4", prec)
+                except nat.CglError as e:
+                    assert e.status == nat.CGL_ENOMEM, e
+                    k += 1
+                    assert k < 500
+                    continue
+                plan.close()
+                break
+        finally:
             nat.inject_alloc_failure(-1)
-            plan.close()
-            break
         assert k >= 3, (prec, k)
         torch.cuda.synchronize()
         assert torch.cuda.mem_get_info()[0] == free0, prec
