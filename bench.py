@@ -107,10 +107,11 @@ def measured_peaks():
         return {}
 
 
-def timed_steps(step_fn, K, chunk, warmup, flush, stream):
+def timed_steps(step_fn, K, chunk, warmup, flush, stream, each=None):
     """ms per time step: `warmup` (at least 3) untimed calls of one step, then
     K calls of `chunk` steps, each bracketed by CUDA events on `stream` with
-    L2 flushed (outside the events) before it."""
+    L2 flushed (outside the events) before it.  `each` (a list), if given,
+    receives every timed call's ms per time step, so that an outlier shows."""
     import torch
     for _ in range(max(warmup, 3)):
         step_fn(1)
@@ -123,7 +124,10 @@ def timed_steps(step_fn, K, chunk, warmup, flush, stream):
         step_fn(chunk)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms += e0.elapsed_time(e1)
+        t = e0.elapsed_time(e1)
+        ms += t
+        if each is not None:
+            each.append(t / chunk)
     return ms / (K * chunk)
 
 
@@ -142,8 +146,10 @@ def neumann256_study(dev, flush, K, warmup, chunk, t1_steps, n=256, precisions=(
         dt = torch.complex128 if prec in ("f64", "f64tc") else torch.complex64
         with nat.Plan(w.prob, w.tau, "lawson4", prec) as plan:
             u = nat.to_device(U0, dt, dev)
-            ms = timed_steps(lambda k: plan.step(u, k), K if prec != "f64" else 1, chunk, warmup, flush, stream)
+            each = []
+            ms = timed_steps(lambda k: plan.step(u, k), K if prec != "f64" else 1, chunk, warmup, flush, stream, each)
             res[prec] = {"grid_pt_steps_per_s": N / (ms / 1e3), "ms_per_time_step": ms,
+                         "ms_per_time_step_each_call": each,
                          "launches_per_step": plan.info()["launches_per_step"]}
             prof[prec] = plan.profile(u, 1)
             v = nat.to_device(U0, dt, dev)
@@ -219,9 +225,11 @@ def batch512_study(dev, flush, K, warmup, chunk, t1_steps, precisions=("bf16x3",
         with nat.Batch(probs, 0.01, "lawson4", prec) as b:
             create_s = time.perf_counter() - t0
             u = b.pack(fields, dev)
+            each = []
             ms = timed_steps(lambda k: b.step(u, k), K if prec != "f64" else max(1, K // 2), chunk, warmup, flush,
-                             stream)
+                             stream, each)
             res[prec] = {"grid_pt_steps_per_s": total / (ms / 1e3), "ms_per_time_step": ms,
+                         "ms_per_time_step_each_call": each,
                          "create_s": create_s, "launches_per_step": b.launches_per_step,
                          "achieved_tflops": flops_step / (ms / 1e3) / 1e12}
             v = b.pack(fields, dev)

@@ -45,3 +45,41 @@ def test_traffic_is_null_once_a_source_changes(tmp_path, monkeypatch):
     assert bench.profiled_traffic("k.md", ["a.cu", "b.cuh"]) is None
     assert bench.profiled_traffic("missing.md", ["a.cu"]) is None
 
+
+
+def test_timed_steps_reports_each_call(monkeypatch):
+    """timed_steps on a fake clock: the mean over the timed calls per time
+    step, and every call's own figure in `each` (an outlier stays visible)."""
+    import torch
+
+    clock = {"t": 0.0}
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            self.t = None
+
+        def record(self, stream=None):
+            self.t = clock["t"]
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    class FakeFlush:
+        def fill_(self, v):
+            clock["t"] += 100.0  # outside the events
+
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    calls = []
+
+    def step(k):
+        calls.append(k)
+        # 2 ms per time step, the third timed call 10x slower
+        clock["t"] += (20.0 if len(calls) == 3 + 3 else 2.0) * k
+
+    each = []
+    ms = bench.timed_steps(step, 4, 5, 3, FakeFlush(), None, each)
+    assert calls == [1, 1, 1, 5, 5, 5, 5]
+    assert each == [2.0, 2.0, 20.0, 2.0]
+    assert abs(ms - (2.0 + 2.0 + 20.0 + 2.0) / 4) < 1e-12
+    assert bench.timed_steps(step, 1, 5, 3, FakeFlush(), None) == 2.0
