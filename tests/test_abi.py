@@ -100,6 +100,14 @@ def test_batch_validation_before_any_cuda_call(lib):
     assert lib.cgl_autotune_mode_tile(1, 1, 0, 1, None, None) == nat.CGL_EINVAL
 
 
+def test_fault_injection_hooks_validate_their_arguments(lib):
+    assert lib.cgl_batch_inject_wait_failure(None, 1) == nat.CGL_EINVAL
+    assert lib.cgl_inject_alloc_failure(-2) == nat.CGL_EINVAL
+    # arming and disarming the allocation failure touches no device
+    assert lib.cgl_inject_alloc_failure(3) == nat.CGL_OK
+    assert lib.cgl_inject_alloc_failure(-1) == nat.CGL_OK
+
+
 def coupled_create(**kw):
     base = dict(d=2, n=[70, 35], lo=[0.0, 0.0], hi=[70.0, 35.0], a0=-0.4, a1=0.125, b1=0.5, a2=-0.9, a3=1.0,
                 b3=0.8, a4=-0.1, b4=-0.6, a5=0.5, tau=0.01, scheme=nat.CGL_SPLIT4, precision=nat.CGL_F64)
